@@ -1,0 +1,338 @@
+"""Benchmark of the GB300 quasi-3D dual-solver PIC step.
+
+Workload (default): the 4000 x 400 LWFA/DLA box, modes m = 0, 1, dz = 0.2,
+dr = 0.8, 32 particles per cell (51.2M macroparticles), moving window at c,
+dual solver with 16 coefficients, dt = 0.9 x its stability limit, FP32 push
+and solve with int64 fixed-point current.  One step = Faraday, gather + push +
+deposit, J decode + J_z filter, Ampere, window shift/injection and the particle
+sort.  Synthetic inputs (seeded plasma lattice + Gaussian laser); the box's
+1.8 GB of particles exceed the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line: value = particle-steps/s of the whole step (all ranks),
+with cell-updates/s, the roofline of the gather+push+deposit kernel, the
+FP64 oracle timed on the host cores (cpu_baseline), an end-to-end number
+through the C ABI with host buffers, SM clocks sampled during the timed
+region, and the number of kernels launched.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+Multi-GPU (torchrun): every rank runs an independent replica of the box
+("replicas only"; weak scaling), timed between barriers, max over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "particle-steps/s (gather+push+deposit) + solver cell-updates/s, FP32 vs FP64"
+# algorithmic bytes of gather+push+deposit per particle-step at P particles per
+# cell: particle read 36 B + write 32 B, plus per cell E and Bbar (72 B read)
+# and the int64 current (72 B read-modify-write = 144 B), amortised over P
+GPD_BYTES_PER_PARTICLE = 68.0
+GPD_BYTES_PER_CELL = 72.0 + 144.0
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = "/tmp/qpic_clocks_%d.csv" % os.getpid()
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _make_sim(q, w, stream, track_work=False):
+    return q.Sim(w["nz"], w["nr"], w["dz"], w["dr"], n_modes=w["n_modes"], solver=w["solver"],
+                 periodic=w["periodic"], moving_window=w["moving_window"], stream=stream,
+                 track_work=track_work, seed=w["plasma"]["seed"])
+
+
+def _init_state(sim, w):
+    pl, la = w["plasma"], w["laser"]
+    sim.load_plasma(pl["n0"], pl["z_start"], pl["ramp_len"], pl["ppc"])
+    sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
+
+
+def oracle_sample(w, dt, nz_sample, steps):
+    """The FP64 oracle, as it stands, on a z-slab of the workload: the same
+    nr, dz, dr, dt, plasma and ppc over nz_sample columns (periodic).  Returns
+    (particle-steps/s, particles, seconds)."""
+    import oracle
+    from oracle import coeffs as C
+    from oracle import setup as S
+    pl = w["plasma"]
+    cE, cB = C.solver_coefficients(w["solver"], dt, w["dz"])
+    o = oracle.Oracle(nz_sample, w["nr"], w["n_modes"], w["dz"], w["dr"], dt, cE, cB,
+                      C.filter_taps(cB), periodic=True)
+    # the slab sits on the plateau of the profile (z_start + ramp onwards)
+    first = int(np.ceil((pl["z_start"] + pl["ramp_len"]) / w["dz"]))
+    p = S.plasma_cells(np.arange(first, first + nz_sample), w["nr"], w["dz"], w["dr"],
+                       pl["n0"], pl["z_start"], pl["ramp_len"], pl["ppc"], pl["seed"])
+    p["z"] = p["z"] - first * w["dz"]
+    o.load_particles(**p)
+    n = o.num_particles()
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    return n * steps / t, n, t
+
+
+def run_reference(args, w):
+    """--impl reference: the FP64 CPU oracle (this repository's reference
+    implementation of the method) on the host cores, bounded per step."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import coeffs as C
+    dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], w["nr"], w["n_modes"], w["solver"])
+    nz_s = args.ref_nz
+    oracle_sample(w, dt, nz_s, max(1, args.warmup))      # warm-up (untimed)
+    rate, n, t = oracle_sample(w, dt, nz_s, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "particle-steps/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": "z-slab of %d of %d columns" % (nz_s, w["nz"]),
+                   "particles": n, "nr": w["nr"], "ppc": list(w["plasma"]["ppc"])},
+        "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d steps of a %d x %d periodic slab (%d particles)"
+                                   % (args.steps, nz_s, w["nr"], n)},
+        "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, w):
+    import torch
+    import paper_2303_12874_gb300 as q
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    sim = _make_sim(q, w, stream)
+    _init_state(sim, w)
+    for _ in range(args.warmup):
+        sim.step(1)
+    n0 = sim.diag()["particles"]
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K full steps, CUDA events on the library's stream
+    launches0 = sim.launch_count()
+    clocks = ClockSampler(dev)
+    barrier()
+    if rank == 0:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    barrier()
+    clk = clocks.stop() if rank == 0 else None
+    launches = sim.launch_count() - launches0
+    n1 = sim.diag()["particles"]
+    n_avg = 0.5 * (n0 + n1)
+    ms_t = torch.tensor([ms], device="cuda")
+    tot_p = torch.tensor([n_avg], device="cuda", dtype=torch.float64)
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tot_p)
+    ms_max = float(ms_t.item())
+    particles_all = float(tot_p.item())
+    value = particles_all * args.steps / (ms_max / 1e3)
+    cells = w["nz"] * w["nr"]
+    cell_updates = ws * cells * args.steps / (ms_max / 1e3)
+
+    # ---- per-kernel times (a second, profiled run of the same steps)
+    sim.profile(True, True)
+    sim.step(args.prof_steps)
+    kt = sim.kernel_times()
+    sim.profile(False, True)
+    gpd_ms, gpd_n = kt["gather_push_deposit"]
+    gpd_avg = gpd_ms / max(gpd_n, 1)
+    solver_ms = sum(kt[k][0] for k in ("faraday", "j_decode", "jz_filter", "ampere"))
+    step_prof_ms = sum(v[0] for v in kt.values())
+    ppc = int(np.prod(w["plasma"]["ppc"]))
+    gpd_bytes = n_avg * (GPD_BYTES_PER_PARTICLE + GPD_BYTES_PER_CELL / ppc)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if not hbm:
+        hbm, peak_src = 6800.0, "fallback"
+    achieved = gpd_bytes / (gpd_avg / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "gpd_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tr = json.load(open(tpath))
+            if tr.get("workload") == args.workload and tr.get("kernel_rev") == q.KERNEL_REV:
+                traffic = tr["bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers (rank-local)
+    e2e = None
+    if not args.no_e2e:
+        p = sim.particles()
+        pin = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in p.items()}
+        out_n = len(pin["z"])
+        sim2 = _make_sim(q, w, stream)
+        fields_h = {}
+        for which in ("E", "B"):
+            for c in ("r", "phi", "z"):
+                for m in range(w["n_modes"]):
+                    fields_h[(which, c, m)] = sim.get_field(which, c, m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2.load_particles(pin["z"], pin["r"], pin["phi"], pin["ux"], pin["uy"], pin["uz"], pin["w"])
+        for (which, c, m), v in fields_h.items():
+            sim2.set_field(which, c, m, v)
+        for _ in range(args.e2e_steps):
+            sim2.step(1)
+            d = sim2.diag()
+        res = sim2.particles()
+        t = time.perf_counter() - t0
+        h2d = out_n * 7 * 8 + sum(v.size * 16 for v in fields_h.values())
+        d2h = len(res["z"]) * 9 * 8 + args.e2e_steps * (7 + w["n_modes"]) * 8
+        e2e = {"value": ws * out_n * args.e2e_steps / t, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d / args.e2e_steps),
+               "d2h_bytes_per_step": int(d2h / args.e2e_steps),
+               "steps": args.e2e_steps, "note": "state loaded from pinned host memory, "
+               "diagnostics read back every step, final particles read back"}
+        sim2.close()
+        del d
+
+    # ---- CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, n, t = oracle_sample(w, sim.dt, args.ref_nz, 2)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": "2 steps of a %d x %d periodic z-slab of the workload (%d particles), "
+                         "single-threaded FP64 C, %.1f s" % (args.ref_nz, w["nr"], n, t)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "nz": w["nz"], "nr": w["nr"],
+                       "modes": w["n_modes"], "ppc": list(w["plasma"]["ppc"]),
+                       "particles_per_gpu": int(n_avg), "solver": "dual L=16",
+                       "dt": sim.dt, "deposit": "int64 fixed point",
+                       "l2": "inputs larger than L2 (particles %.1f GB)" % (n_avg * 36 / 1e9),
+                       "parallelism": "replicas x%d" % ws},
+            "cell_updates_per_s": cell_updates,
+            "solver_cell_updates_per_s": cells * args.prof_steps / (solver_ms / 1e3) if solver_ms else None,
+            "gpd_particle_steps_per_s": n_avg / (gpd_avg / 1e3),
+            "kernel_ms_per_step": {k: v[0] / max(args.prof_steps, 1) for k, v in kt.items() if v[1]},
+            "roofline": {"kernel": "gather_push_deposit", "bound": "hbm", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_source": peak_src + " (hbm_gbs, burst)",
+                         "algorithmic_bytes_per_launch": gpd_bytes, "traffic": traffic},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2_lwfa")
+    ap.add_argument("--prof-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-nz", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = synth.workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

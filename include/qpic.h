@@ -1,0 +1,215 @@
+/*
+ * qpic.h -- C ABI of libqpic, a GB300 (sm_103a) quasi-3D electromagnetic
+ * particle-in-cell step with the extended-stencil ("dual") Maxwell solver of
+ * arXiv:2303.12874 (Miller et al.), Sec. III.
+ *
+ * Method (paper sections):
+ *   Sec. III.A, Eqs. 9-15  dual solver: z-derivatives with L coefficients fitted
+ *                          so that [k]_B[k]_E = (sin(k dt/2)/(dt/2))^2 (Eq. 11)
+ *                          and sqrt([k]_E/[k]_B) cos(k dt/2) = 1 (Eq. 15).
+ *   Sec. III.B              azimuthal-mode ("quasi-3D") fields F_m e^{i m phi}.
+ *   Eq. 6, Eq. 12           relativistic push with E^n and the time-averaged B.
+ *   Sec. II (end)           charge-conserving current deposition.
+ *   Eq. 16                  modal work W_LWFA (m = 0) and W_DLA (m = 1).
+ *
+ * Units: c = 1, lengths in c/w0, time in 1/w0, fields in m c w0/e, momenta
+ * u = gamma v, densities in n_c (w_p^2 = n); electrons, q = -1, m = 1.
+ *
+ * Conventions for every call:
+ *   - returns a qpic_status; no exception or abort crosses the ABI;
+ *     qpic_last_error(ctx) gives a text for the last failure;
+ *   - host buffers are owned by the caller and only read/written during the
+ *     call; device memory is owned by the context;
+ *   - a context is used by one host thread at a time;
+ *   - all work is queued on the context's CUDA stream; calls that return
+ *     data to the host synchronise that stream.
+ *   - field planes are [nr+1][nz] (r index j = 0..nr slowest, z fastest) in
+ *     the window's logical order, per component and mode.  Mode 0 is real
+ *     (im part ignored / written as 0).  Grid staggering (z index i at
+ *     z = zmin + i dz, r_j = j dr, half-integer points stored at the integer
+ *     index below them):  E_r (i, j+1/2)  E_phi (i, j)  E_z (i+1/2, j)
+ *                         B_r (i+1/2, j)  B_phi (i+1/2, j+1/2)  B_z (i, j+1/2)
+ *     J co-located with E.  Rows that lie outside the wall (half-r row nr)
+ *     or on the conductor (E_phi, E_z at j = nr) are 0.
+ */
+#ifndef QPIC_H
+#define QPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qpic_ctx qpic_ctx;
+
+typedef enum {
+    QPIC_OK = 0,
+    QPIC_EINVAL = -1,      /* bad argument or configuration */
+    QPIC_ENOMEM = -2,      /* device or host allocation failed */
+    QPIC_ECUDA = -3,       /* a CUDA runtime call failed */
+    QPIC_ECFL = -4,        /* dt above the stability limit, or no coefficient fit */
+    QPIC_EOVERFLOW = -5,   /* fixed-point current accumulator out of range */
+    QPIC_ETIMEOUT = -6,    /* a bounded device-side wait gave up */
+    QPIC_ENONFINITE = -7,  /* NaN/Inf found by the diagnostics */
+    QPIC_ESTATE = -8,      /* call not valid in the current state */
+    QPIC_ECAPACITY = -9    /* particle buffer capacity exceeded */
+} qpic_status;
+
+enum { QPIC_YEE = 0, QPIC_DUAL = 1 };
+enum { QPIC_FP64 = 0, QPIC_FP32_FIXED = 1, QPIC_FP32_FATOMIC = 2 };
+enum { QPIC_FIELD_E = 0, QPIC_FIELD_B = 1, QPIC_FIELD_BBAR = 2, QPIC_FIELD_J = 3, QPIC_FIELD_RHO = 4 };
+enum { QPIC_COMP_R = 0, QPIC_COMP_PHI = 1, QPIC_COMP_Z = 2 };
+enum { QPIC_STAGE_FARADAY = 1, QPIC_STAGE_PARTICLES = 2, QPIC_STAGE_AMPERE = 4,
+       QPIC_STAGE_WINDOW = 8, QPIC_STAGE_SORT = 16 };
+
+typedef struct {
+    int32_t nz, nr;        /* logical grid: nz cells along z, nr cells in r (wall at nr dr) */
+    int32_t n_modes;       /* M + 1 azimuthal modes (1..4) */
+    double dz, dr;
+    double dt;             /* <= 0: dt = cfl_frac x the solver's stability limit */
+    double cfl_frac;
+    int32_t solver;        /* QPIC_YEE or QPIC_DUAL */
+    int32_t n_coef;        /* L coefficients per z-operator for QPIC_DUAL (Appendix A: 16) */
+    double fit_band;       /* fit range k dz in (0, fit_band*pi] (a reading; default 0.8) */
+    int32_t precision;     /* QPIC_FP32_FIXED (default), QPIC_FP32_FATOMIC, QPIC_FP64 */
+    int32_t jz_filter;     /* 1: J_z correction so that Gauss's law holds in the dual form */
+    double filter_tol;     /* filter taps kept down to |k_n| >= filter_tol |k_0| */
+    int32_t periodic_z;    /* 1: periodic box; 0: open box (zero fields outside) */
+    int32_t moving_window; /* 1: window moves at window_v (needs periodic_z = 0) */
+    double window_v;
+    int32_t tile_z, tile_r;   /* particle tile in cells (0: default 16 x 8) */
+    int32_t sort_period;      /* steps between particle sorts (0: default 1) */
+    int32_t track_work;       /* 1: accumulate modal work W0, W1 per particle (Eq. 16) */
+    uint64_t seed;            /* plasma azimuthal jitter seed */
+    int64_t max_particles;    /* capacity (0: sized at the first load, +25%) */
+    void *cuda_stream;        /* cudaStream_t to run on, NULL: the legacy default stream */
+    /* optional device allocator (e.g. a PyTorch caching allocator); NULL: cudaMalloc */
+    void *(*dev_alloc)(size_t bytes, void *user);
+    void (*dev_free)(void *ptr, void *user);
+    void *alloc_user;
+} qpic_config;
+
+/* Fill *cfg with defaults (M = 1, dual solver, L = 16, band 0.8, cfl 0.9,
+ * FP32 + int64 fixed point, filter on, tol 1e-16, periodic, 16 x 8 tiles). */
+qpic_status qpic_default_config(qpic_config *cfg);
+
+/* Create a context: fit the z-operator coefficients on the host in FP64
+ * (Eqs. 11 and 15, Sec. III.A; least squares on the fit band with the exact
+ * long-wavelength limit), find dt by bisection of the leapfrog stability
+ * bound when cfg->dt <= 0, build the J_z filter taps, allocate zeroed device
+ * fields.  *out receives the context; on failure it may still receive one so
+ * that qpic_last_error can explain -- destroy it with qpic_destroy. */
+qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out);
+
+/* Free everything the context owns.  NULL is allowed. */
+void qpic_destroy(qpic_ctx *ctx);
+
+/* Text of the last failure on ctx (static string when ctx is NULL). */
+const char *qpic_last_error(const qpic_ctx *ctx);
+
+/* Solver constants chosen at init: dt, L and the coefficients C^E_l, C^B_l
+ * (l = 1..L; Eq. 9 operators D f_{i+1/2} = sum_l C_l (f_{i+l} - f_{i+1-l})/dz),
+ * and the J_z filter taps k_0..k_{nk-1}.  Arrays may be NULL; caps in entries. */
+qpic_status qpic_get_solver(const qpic_ctx *ctx, double *dt, int32_t *L,
+                            double *cE, double *cB, int32_t cap_coef,
+                            double *taps, int32_t cap_taps, int32_t *n_taps);
+
+/* Host-only numerics, usable without a GPU (same code qpic_init uses).
+ * qpic_fit_coefficients: C^E, C^B for `solver` at time step dt (Eqs. 11, 15;
+ *   Yee gives L = 1, C = 1); returns L in *L_out; arrays hold >= n_coef entries.
+ * qpic_filter_taps: J_z correction taps k_0..k_{n-1} for C^B (symbol
+ *   [k]_Yee/[k]_B), truncated below tol |k_0|; *n_out = 0 for Yee.
+ * qpic_stability_limit: largest dt with (dt^2/4) lambda_max(curl curl) <= 1
+ *   for an nr-cell radial grid and n_modes modes (bisection; the dual
+ *   coefficients are refitted at every trial dt). */
+qpic_status qpic_fit_coefficients(int32_t solver, double dt, double dz, int32_t n_coef,
+                                  double fit_band, double *cE, double *cB, int32_t *L_out);
+qpic_status qpic_filter_taps(const double *cB, int32_t L, double tol, double *taps,
+                             int32_t cap, int32_t *n_out);
+qpic_status qpic_stability_limit(int32_t solver, double dz, double dr, int32_t nr,
+                                 int32_t n_modes, int32_t n_coef, double fit_band,
+                                 double *dt_max);
+
+/* Stability limit of the configured solver on this grid (leapfrog bound
+ * (dt^2/4) lambda_max(curl curl) <= 1, coefficients refitted per trial dt). */
+qpic_status qpic_cfl_limit(const qpic_ctx *ctx, double *dt_max);
+
+/* Load the cold plasma lattice into every cell of the current window,
+ * replacing all particles: ppc_z x ppc_r x ppc_phi per cell at
+ * z = (i + (a+1/2)/ppc_z) dz, r = (j + (b+1/2)/ppc_r) dr,
+ * phi = 2 pi (c + jitter)/ppc_phi with one jitter in [0,1) per cell from a
+ * SplitMix64 keyed on (seed, absolute z cell, r cell) (0 when phi_jitter = 0);
+ * weight w = n(z) 2 pi r (dr/ppc_r)(dz/ppc_z)/ppc_phi, n(z) = n0 times a linear
+ * ramp from z_start over ramp_len (lab frame).  The same parameters feed the
+ * moving-window injection.  Cells where n = 0 get no particles. */
+qpic_status qpic_load_plasma(qpic_ctx *ctx, double n0, double z_start, double ramp_len,
+                             int32_t ppc_z, int32_t ppc_r, int32_t ppc_phi, int32_t phi_jitter);
+
+/* Replace all particles with n given ones (host FP64 arrays): lab-frame z,
+ * r in [0, nr dr], phi, momenta u = gamma v (Cartesian), weights w >= 0
+ * (number of electrons).  Modal work counters start at 0. */
+qpic_status qpic_load_particles(qpic_ctx *ctx, int64_t n, const double *z, const double *r,
+                                const double *phi, const double *ux, const double *uy,
+                                const double *uz, const double *w);
+
+/* Add a linearly polarised Gaussian pulse to the m = 1 fields (Eq. 18 near
+ * focus, as a paraxial Gaussian beam): field amplitude a0, waist w0, intensity
+ * FWHM duration fwhm, centroid z_centroid and focus z_focus (lab frame),
+ * polarisation angle pol_angle from x.  E at t = 0; B at t = -dt/2 with the
+ * discrete B/E ratio sqrt([k]_E/[k]_B) at k = 1.  Needs n_modes >= 2. */
+qpic_status qpic_add_laser(qpic_ctx *ctx, double a0, double w0, double fwhm,
+                           double z_centroid, double z_focus, double pol_angle);
+
+/* Advance nsteps full PIC steps (Faraday -> gather/push/deposit -> J_z filter
+ * -> Ampere, then the moving window and the particle sort).  Asynchronous on
+ * the context's stream except for a final check of the device error word. */
+qpic_status qpic_step(qpic_ctx *ctx, int32_t nsteps);
+
+/* Run only the given stages once (QPIC_STAGE_* bit mask, in step order);
+ * for stage-by-stage parity checks and timing. */
+qpic_status qpic_run_stages(qpic_ctx *ctx, int32_t stages);
+
+/* Copy one field plane to/from caller-owned host FP64 arrays of
+ * (nr+1)*nz entries each (layout above).  which: QPIC_FIELD_*; J is the
+ * current of the last step after the J_z correction; RHO (get only) deposits
+ * the electron charge density per mode from the current particles. */
+qpic_status qpic_get_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t mode,
+                           double *re, double *im);
+qpic_status qpic_set_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t mode,
+                           const double *re, const double *im);
+
+/* Number of live particles. */
+qpic_status qpic_num_particles(qpic_ctx *ctx, int64_t *n);
+
+/* Copy live particles to a caller-owned host buffer of 9*capacity FP64 in
+ * structure-of-arrays order z, r, phi, ux, uy, uz, w, W0, W1 (each block has
+ * *n_out entries, packed at stride capacity).  Order is unspecified. */
+qpic_status qpic_get_particles(qpic_ctx *ctx, double *out, int64_t capacity, int64_t *n_out);
+
+/* Like qpic_get_particles but in device buffer order without sorting or
+ * compaction: slot k of every block is buffer slot k, dead slots have w = 0.
+ * Two raw exports with only QPIC_STAGE_FARADAY/PARTICLES/AMPERE stages in
+ * between list the same particles in the same order. */
+qpic_status qpic_get_particles_raw(qpic_ctx *ctx, double *out, int64_t capacity, int64_t *n_out);
+
+/* FP64 diagnostics into out[0..count): [0] time, [1] steps, [2] window shifts,
+ * [3] live particles, [4] total charge, [5] kinetic energy sum w (gamma-1),
+ * [6..6+M] field energy per mode, then the overflow flag. */
+qpic_status qpic_get_diag(qpic_ctx *ctx, double *out, int32_t count);
+
+/* Number of CUDA kernels this context has launched so far. */
+qpic_status qpic_launch_count(const qpic_ctx *ctx, int64_t *n);
+
+/* Per-kernel device time (ms, CUDA events on the context's stream) and launch
+ * counts accumulated since the last reset, for n kernel classes; names gives
+ * "name" strings (static).  Timing is on only when enabled. */
+qpic_status qpic_profile(qpic_ctx *ctx, int32_t enable, int32_t reset);
+qpic_status qpic_kernel_times(qpic_ctx *ctx, int32_t n, double *ms, int64_t *launches,
+                              const char **names, int32_t *n_classes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QPIC_H */

@@ -1,0 +1,685 @@
+// api.cu -- the C ABI of libqpic (declared in include/qpic.h): context set-up,
+// particle and field I/O, the step loop, diagnostics and kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qpic_internal.h"
+
+using namespace qpic;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+void *dalloc(qpic_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->cfg.dev_alloc) {
+        p = c->cfg.dev_alloc(bytes, c->cfg.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.push_back(p);
+    return p;
+}
+
+void dfree(qpic_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    if (c->cfg.dev_free) c->cfg.dev_free(p, c->cfg.alloc_user);
+    else cudaFree(p);
+}
+
+template <class T>
+bool alloc_arr(qpic_ctx *c, T **out, size_t n)
+{
+    *out = static_cast<T *>(dalloc(c, n * sizeof(T)));
+    return *out != nullptr;
+}
+
+qpic_status fail(qpic_ctx *c, qpic_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+qpic_status cuda_check(qpic_ctx *c, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, QPIC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return QPIC_OK;
+}
+
+bool alloc_particles(qpic_ctx *c, qpic::Particles &p, long long cap)
+{
+    bool ok = alloc_arr(c, &p.cell, cap) && alloc_arr(c, &p.oz, cap) && alloc_arr(c, &p.orr, cap) &&
+              alloc_arr(c, &p.cph, cap) && alloc_arr(c, &p.sph, cap) && alloc_arr(c, &p.ux, cap) &&
+              alloc_arr(c, &p.uy, cap) && alloc_arr(c, &p.uz, cap) && alloc_arr(c, &p.w, cap);
+    if (ok && c->cfg.track_work) ok = alloc_arr(c, &p.W0, cap) && alloc_arr(c, &p.W1, cap);
+    return ok;
+}
+
+void free_particles(qpic_ctx *c, qpic::Particles &p)
+{
+    void *arr[11] = {p.cell, p.oz, p.orr, p.cph, p.sph, p.ux, p.uy, p.uz, p.w, p.W0, p.W1};
+    for (void *a : arr) dfree(c, a);
+    p = qpic::Particles();
+}
+
+qpic_status ensure_capacity(qpic_ctx *c, long long need)
+{
+    if (need <= c->cap) return QPIC_OK;
+    long long cap = c->cfg.max_particles > 0 ? c->cfg.max_particles
+                                             : std::max(need + need / 4 + 4096, c->cap);
+    if (cap < need) return fail(c, QPIC_ECAPACITY, "particle capacity (max_particles) exceeded");
+    cudaStreamSynchronize(c->stream);
+    free_particles(c, c->p);
+    free_particles(c, c->ps);
+    c->cap = 0;
+    if (!alloc_particles(c, c->p, cap) || !alloc_particles(c, c->ps, cap))
+        return fail(c, QPIC_ENOMEM, "particle buffers: device allocation failed");
+    c->cap = cap;
+    return QPIC_OK;
+}
+
+// logical column <-> physical column
+long long phys_col(const qpic_ctx *c, long long il)
+{
+    long long p = (il + c->g.zoff) % c->g.nzp;
+    return p < 0 ? p + c->g.nzp : p;
+}
+
+float *field_base(qpic_ctx *c, int which)
+{
+    switch (which) {
+    case QPIC_FIELD_E: return c->E;
+    case QPIC_FIELD_B: return c->B;
+    case QPIC_FIELD_BBAR: return c->Bb;
+    default: return c->Jf;
+    }
+}
+
+void set_qscale(qpic_ctx *c, double qmax)
+{
+    c->qref = qmax > 0 ? qmax : 1.0;
+    // per-particle contributions stay below ~2 qref: 2^45 of 2^63 leaves 2^17
+    // particles' worth of headroom per accumulator
+    c->qscale = (float)(17592186044416.0 / c->qref);       // 2^44 / qref
+}
+
+void do_shift(qpic_ctx *c)
+{
+    long long back = phys_col(c, 0);
+    launch_zero_column(c, back);
+    c->g.zoff = (c->g.zoff + 1) % c->g.nzp;
+    c->shifts++;
+    if (c->have_plasma) {
+        if (c->np + (long long)c->g.nr * c->ppc_z * c->ppc_r * c->ppc_phi > c->cap) {
+            // host bound is loose after sorts dropped particles: refresh it
+            long long n = 0;
+            cudaMemcpyAsync(&n, c->d_count, sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+            cudaStreamSynchronize(c->stream);
+            c->np = n;
+        }
+        launch_load_plasma(c, c->g.nz - 1, 1, true);
+    }
+}
+
+qpic_status run_one_step(qpic_ctx *c, int stages)
+{
+    if (stages & QPIC_STAGE_FARADAY) launch_faraday(c);
+    if (stages & QPIC_STAGE_PARTICLES) {
+        launch_gpd(c);
+        launch_jdecode(c);
+        c->j_filtered = false;
+    }
+    if (stages & QPIC_STAGE_AMPERE) {
+        if (!c->taps.empty()) launch_jfilter(c);
+        c->j_filtered = !c->taps.empty();
+        launch_ampere(c);
+    }
+    bool full = (stages & (QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE)) ==
+                (QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE);
+    if (full) c->nstep++;
+    if ((stages & QPIC_STAGE_WINDOW) && c->cfg.moving_window) {
+        while (c->cfg.window_v * ((double)c->nstep * c->dt) >= (double)(c->shifts + 1) * c->dz)
+            do_shift(c);
+    }
+    if (stages & QPIC_STAGE_SORT) {
+        bool due = c->sort_period <= 1 || (c->nstep % c->sort_period) == 0 ||
+                   c->n_tail > c->cap / 64;
+        if (due) launch_sort(c);
+    }
+    return QPIC_OK;
+}
+
+qpic_status check_device_error(qpic_ctx *c)
+{
+    int e = 0;
+    cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return fail(c, QPIC_ECUDA, std::string("step: ") + cudaGetErrorString(ce));
+    if (e & 1) return fail(c, QPIC_EOVERFLOW, "fixed-point current accumulator overflow");
+    if (e & 2) return fail(c, QPIC_ECAPACITY, "particle capacity exceeded during injection");
+    return QPIC_OK;
+}
+
+long long live_count(qpic_ctx *c)
+{
+    long long n = 0;
+    cudaMemcpyAsync(&n, c->d_count, sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    c->np = n;
+    return n;
+}
+
+}  // namespace
+
+namespace qpic {
+
+void prof_begin(qpic_ctx *c)
+{
+    if (!c->profile) return;
+    if (c->ev_used + 2 > c->ev_pool.size()) {
+        for (int k = 0; k < 256; k++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->ev_pool.push_back(e);
+        }
+    }
+    cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+}
+
+void prof_end(qpic_ctx *c, int kclass, int nkernels)
+{
+    c->n_kernels += nkernels;
+    if (!c->profile) return;
+    cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream);
+    c->ev_class.push_back(kclass);
+    c->ev_used += 2;
+}
+
+}  // namespace qpic
+
+static void resolve_events(qpic_ctx *c)
+{
+    if (c->ev_used == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (size_t k = 0; k < c->ev_class.size(); k++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]);
+        c->kms[c->ev_class[k]] += ms;
+        c->klaunch[c->ev_class[k]] += 1;
+    }
+    c->ev_class.clear();
+    c->ev_used = 0;
+}
+
+extern "C" {
+
+qpic_status qpic_default_config(qpic_config *cfg)
+{
+    if (!cfg) return QPIC_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->n_modes = 2;
+    cfg->cfl_frac = 0.9;
+    cfg->solver = QPIC_DUAL;
+    cfg->n_coef = 16;
+    cfg->fit_band = 0.8;
+    cfg->precision = QPIC_FP32_FIXED;
+    cfg->jz_filter = 1;
+    cfg->filter_tol = 1e-16;
+    cfg->periodic_z = 1;
+    cfg->window_v = 1.0;
+    cfg->tile_z = 16;
+    cfg->tile_r = 8;
+    cfg->sort_period = 1;
+    cfg->seed = 1;
+    return QPIC_OK;
+}
+
+const char *qpic_last_error(const qpic_ctx *ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+void qpic_destroy(qpic_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    std::vector<void *> all = ctx->allocs;
+    for (void *p : all) dfree(ctx, p);
+    delete ctx;
+}
+
+qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
+{
+    if (!out) return QPIC_EINVAL;
+    *out = nullptr;
+    if (!cfg) return QPIC_EINVAL;
+    qpic_ctx *c = new (std::nothrow) qpic_ctx();
+    if (!c) return QPIC_ENOMEM;
+    c->cfg = *cfg;
+    auto bad = [&](qpic_status s, const std::string &m) {
+        c->err = m;
+        *out = c;          // returned so that qpic_last_error can explain; caller destroys
+        return s;
+    };
+    if (cfg->nz < 4 || cfg->nr < 2 || cfg->n_modes < 1 || cfg->n_modes > MAX_MODES)
+        return bad(QPIC_EINVAL, "grid: need nz >= 4, nr >= 2, 1 <= n_modes <= 4");
+    if (!(cfg->dz > 0) || !(cfg->dr > 0)) return bad(QPIC_EINVAL, "dz, dr must be positive");
+    if (cfg->solver != QPIC_YEE && cfg->solver != QPIC_DUAL) return bad(QPIC_EINVAL, "solver");
+    if (cfg->precision == QPIC_FP64) return bad(QPIC_EINVAL, "FP64 path: use precision FP32_FIXED");
+    if (cfg->precision != QPIC_FP32_FIXED) return bad(QPIC_EINVAL, "precision");
+    if (cfg->moving_window && cfg->periodic_z) return bad(QPIC_EINVAL, "moving window needs periodic_z = 0");
+    c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    c->dz = cfg->dz;
+    c->dr = cfg->dr;
+    const int L = cfg->solver == QPIC_YEE ? 1 : (cfg->n_coef > 0 ? cfg->n_coef : 16);
+    const double band = cfg->fit_band > 0 ? cfg->fit_band : 0.8;
+    double dtmax = 0.0;
+    if (!cfl_limit(cfg->solver, cfg->dz, cfg->dr, cfg->nr, cfg->n_modes, L, band, &dtmax, c->err))
+        return bad(QPIC_ECFL, c->err);
+    c->dt = cfg->dt > 0 ? cfg->dt : (cfg->cfl_frac > 0 ? cfg->cfl_frac : 0.9) * dtmax;
+    if (c->dt > dtmax * (1.0 + 1e-9)) return bad(QPIC_ECFL, "dt above the stability limit");
+    c->L = fit_coefficients(cfg->solver, c->dt, cfg->dz, L, band, c->cE, c->cB, c->err);
+    if (!c->L) return bad(QPIC_ECFL, c->err);
+    if (cfg->solver == QPIC_DUAL && cfg->jz_filter) {
+        double tol = cfg->filter_tol > 0 ? cfg->filter_tol : 1e-16;
+        if (!filter_taps_host(c->cB, c->L, tol, c->taps, c->err)) return bad(QPIC_ECFL, c->err);
+    }
+    c->kE1 = symbol(c->cE, c->L, cfg->dz) / cfg->dz;
+    c->kB1 = symbol(c->cB, c->L, cfg->dz) / cfg->dz;
+    // geometry: circular z buffer, gap wider than the widest stencil for open boxes
+    c->TZ = cfg->tile_z > 0 ? cfg->tile_z : 16;
+    c->TR = cfg->tile_r > 0 ? cfg->tile_r : 8;
+    c->halo = 1;
+    c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 1;
+    FieldGeom &g = c->g;
+    g.nz = cfg->nz; g.nr = cfg->nr; g.nm = cfg->n_modes; g.nparts = 2 * cfg->n_modes - 1;
+    g.periodic = cfg->periodic_z ? 1 : 0;
+    int reach = std::max({2 * c->L + 2, (int)c->taps.size() + 2, 2 * (c->TZ + 2 * c->halo + 3)});
+    g.gap = g.periodic ? 0 : ((reach + c->TZ - 1) / c->TZ) * c->TZ;
+    g.nzp = g.nz + g.gap;
+    g.zoff = 0;
+    g.plane = (size_t)(g.nr + 1) * g.nzp;
+    g.dz = (float)c->dz; g.dr = (float)c->dr; g.dt = (float)c->dt;
+    const size_t nplanes = (size_t)3 * g.nparts;
+    if (!alloc_arr(c, &c->E, nplanes * g.plane) || !alloc_arr(c, &c->B, nplanes * g.plane) ||
+        !alloc_arr(c, &c->Bb, nplanes * g.plane) || !alloc_arr(c, &c->Jf, nplanes * g.plane) ||
+        !alloc_arr(c, &c->Jzf, (size_t)g.nparts * g.plane) ||
+        !alloc_arr(c, &c->Jacc, nplanes * g.plane) || !alloc_arr(c, &c->rowf, (size_t)4 * (g.nr + 1)) ||
+        !alloc_arr(c, &c->coef, (size_t)2 * MAX_L + MAX_TAPS) || !alloc_arr(c, &c->d_err, 4) ||
+        !alloc_arr(c, &c->d_count, 4))
+        return bad(QPIC_ENOMEM, "field buffers: device allocation failed");
+    c->ntz = (g.nzp + c->TZ - 1) / c->TZ;
+    c->ntr = (g.nr + c->TR - 1) / c->TR;
+    c->nkeys = (long long)c->ntz * c->ntr * c->TZ * c->TR;
+    const int nb = (int)((c->nkeys + 1 + 4095) / 4096);
+    c->red_cap = std::max(4 * (g.nr + 1) * g.nm + 64, 8 + 3 * 305);
+    if (!alloc_arr(c, &c->counts, (size_t)c->nkeys + 1) ||
+        !alloc_arr(c, &c->offsets, (size_t)c->nkeys + 1) || !alloc_arr(c, &c->scan_tmp, (size_t)nb + 2) ||
+        !alloc_arr(c, &c->d_red, (size_t)c->red_cap))
+        return bad(QPIC_ENOMEM, "sort buffers: device allocation failed");
+    cudaMemsetAsync(c->E, 0, nplanes * g.plane * sizeof(float), c->stream);
+    cudaMemsetAsync(c->B, 0, nplanes * g.plane * sizeof(float), c->stream);
+    cudaMemsetAsync(c->Bb, 0, nplanes * g.plane * sizeof(float), c->stream);
+    cudaMemsetAsync(c->Jf, 0, nplanes * g.plane * sizeof(float), c->stream);
+    cudaMemsetAsync(c->Jzf, 0, (size_t)g.nparts * g.plane * sizeof(float), c->stream);
+    cudaMemsetAsync(c->Jacc, 0, nplanes * g.plane * 8, c->stream);
+    cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_count, 0, 4 * sizeof(long long), c->stream);
+    cudaMemsetAsync(c->offsets, 0, ((size_t)c->nkeys + 1) * sizeof(int32_t), c->stream);
+    // row factors turning the deposit's charge quantities into current densities:
+    // J_z = X dz/(V_j dt), J_r = X/(2 pi r_{j+1/2} dz dt), J_phi^{m>=1} = X r_j/(V_j dt),
+    // J_phi^0 = X dr/(V_j dt); V_j the control volume of node j
+    std::vector<float> rf((size_t)4 * (g.nr + 1));
+    const double dz = c->dz, dr = c->dr, dt = c->dt, R = g.nr * dr;
+    for (int j = 0; j <= g.nr; j++) {
+        double V = j == 0 ? kPi * 0.25 * dr * dr * dz
+                 : j == g.nr ? kPi * (R * R - (R - 0.5 * dr) * (R - 0.5 * dr)) * dz
+                             : 2.0 * kPi * j * dr * dr * dz;
+        rf[j] = (float)(dz / (V * dt));
+        rf[(g.nr + 1) + j] = j < g.nr ? (float)(1.0 / (2.0 * kPi * (j + 0.5) * dr * dz * dt)) : 0.f;
+        rf[2 * (g.nr + 1) + j] = (float)(j * dr / (V * dt));
+        rf[3 * (g.nr + 1) + j] = (float)(dr / (V * dt));
+    }
+    cudaMemcpy(c->rowf, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    set_solver_constants(c);
+    set_qscale(c, 1.0);
+    qpic_status st = cuda_check(c, "init");
+    if (st != QPIC_OK) { *out = c; return st; }
+    cudaStreamSynchronize(c->stream);
+    *out = c;
+    return QPIC_OK;
+}
+
+qpic_status qpic_get_solver(const qpic_ctx *ctx, double *dt, int32_t *L, double *cE, double *cB,
+                            int32_t cap_coef, double *taps, int32_t cap_taps, int32_t *n_taps)
+{
+    if (!ctx) return QPIC_EINVAL;
+    if (dt) *dt = ctx->dt;
+    if (L) *L = ctx->L;
+    for (int l = 0; l < ctx->L && l < cap_coef; l++) {
+        if (cE) cE[l] = ctx->cE[l];
+        if (cB) cB[l] = ctx->cB[l];
+    }
+    if (n_taps) *n_taps = (int32_t)ctx->taps.size();
+    for (int q = 0; q < (int)ctx->taps.size() && q < cap_taps; q++)
+        if (taps) taps[q] = ctx->taps[q];
+    return QPIC_OK;
+}
+
+qpic_status qpic_fit_coefficients(int32_t solver, double dt, double dz, int32_t n_coef,
+                                  double fit_band, double *cE, double *cB, int32_t *L_out)
+{
+    if (!cE || !cB || !L_out || (solver != QPIC_YEE && solver != QPIC_DUAL)) return QPIC_EINVAL;
+    std::string err;
+    int L = fit_coefficients(solver, dt, dz, solver == QPIC_YEE ? 1 : n_coef,
+                             fit_band > 0 ? fit_band : 0.8, cE, cB, err);
+    if (!L) return QPIC_ECFL;
+    *L_out = L;
+    return QPIC_OK;
+}
+
+qpic_status qpic_filter_taps(const double *cB, int32_t L, double tol, double *taps, int32_t cap,
+                             int32_t *n_out)
+{
+    if (!cB || !n_out || L < 1 || L > MAX_L) return QPIC_EINVAL;
+    std::string err;
+    std::vector<double> t;
+    if (!filter_taps_host(cB, L, tol > 0 ? tol : 1e-16, t, err)) return QPIC_ECFL;
+    *n_out = (int32_t)t.size();
+    for (int q = 0; q < (int)t.size() && q < cap; q++)
+        if (taps) taps[q] = t[q];
+    return QPIC_OK;
+}
+
+qpic_status qpic_stability_limit(int32_t solver, double dz, double dr, int32_t nr, int32_t n_modes,
+                                 int32_t n_coef, double fit_band, double *dt_max)
+{
+    if (!dt_max || nr < 1 || n_modes < 1 || !(dz > 0) || !(dr > 0)) return QPIC_EINVAL;
+    std::string err;
+    if (!cfl_limit(solver, dz, dr, nr, n_modes, solver == QPIC_YEE ? 1 : n_coef,
+                   fit_band > 0 ? fit_band : 0.8, dt_max, err))
+        return QPIC_ECFL;
+    return QPIC_OK;
+}
+
+qpic_status qpic_cfl_limit(const qpic_ctx *ctx, double *dt_max)
+{
+    if (!ctx || !dt_max) return QPIC_EINVAL;
+    std::string err;
+    const int L = ctx->cfg.solver == QPIC_YEE ? 1 : ctx->L;
+    if (!cfl_limit(ctx->cfg.solver, ctx->dz, ctx->dr, ctx->g.nr, ctx->g.nm, L,
+                   ctx->cfg.fit_band > 0 ? ctx->cfg.fit_band : 0.8, dt_max, err))
+        return QPIC_ECFL;
+    return QPIC_OK;
+}
+
+qpic_status qpic_load_plasma(qpic_ctx *c, double n0, double z_start, double ramp_len,
+                             int32_t ppc_z, int32_t ppc_r, int32_t ppc_phi, int32_t phi_jitter)
+{
+    if (!c) return QPIC_EINVAL;
+    if (ppc_z < 1 || ppc_r < 1 || ppc_phi < 1 || !(n0 >= 0)) return fail(c, QPIC_EINVAL, "plasma parameters");
+    c->have_plasma = true;
+    c->n0 = n0; c->z_start = z_start; c->ramp_len = ramp_len;
+    c->ppc_z = ppc_z; c->ppc_r = ppc_r; c->ppc_phi = ppc_phi; c->jitter = phi_jitter ? 1 : 0;
+    long long n = (long long)c->g.nz * c->g.nr * ppc_z * ppc_r * ppc_phi;
+    long long per_col = (long long)c->g.nr * ppc_z * ppc_r * ppc_phi;
+    qpic_status s = ensure_capacity(c, n + (c->cfg.moving_window ? 64 * per_col : 0));
+    if (s != QPIC_OK) return s;
+    // largest weight: density n0 at the outermost sub-particle radius
+    double rmax = (c->g.nr - 1 + (ppc_r - 0.5) / ppc_r) * c->dr;
+    set_qscale(c, n0 * 2.0 * kPi * rmax * (c->dr / ppc_r) * (c->dz / ppc_z) / ppc_phi);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (!launch_load_plasma(c, 0, c->g.nz, false)) return fail(c, QPIC_ECAPACITY, "capacity");
+    launch_sort(c);
+    live_count(c);
+    return cuda_check(c, "load_plasma");
+}
+
+qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const double *r,
+                                const double *phi, const double *ux, const double *uy,
+                                const double *uz, const double *w)
+{
+    if (!c || n < 0 || (n > 0 && (!z || !r || !phi || !ux || !uy || !uz || !w)))
+        return fail(c, QPIC_EINVAL, "load_particles arguments");
+    qpic_status s = ensure_capacity(c, n);
+    if (s != QPIC_OK) return s;
+    double qmax = 0.0;
+    for (long long i = 0; i < n; i++) qmax = std::max(qmax, std::fabs(w[i]));
+    set_qscale(c, qmax);
+    double *tmp = nullptr;
+    if (n > 0) {
+        if (!alloc_arr(c, &tmp, (size_t)7 * n)) return fail(c, QPIC_ENOMEM, "staging buffer");
+        const double *src[7] = {z, r, phi, ux, uy, uz, w};
+        for (int k = 0; k < 7; k++)
+            cudaMemcpyAsync(tmp + (size_t)k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream);
+    }
+    launch_load_particles(c, n, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n, tmp + 5 * n,
+                          tmp + 6 * n);
+    launch_sort(c);
+    cudaStreamSynchronize(c->stream);
+    if (tmp) dfree(c, tmp);
+    live_count(c);
+    return cuda_check(c, "load_particles");
+}
+
+qpic_status qpic_add_laser(qpic_ctx *c, double a0, double w0, double fwhm, double z_centroid,
+                           double z_focus, double pol_angle)
+{
+    if (!c) return QPIC_EINVAL;
+    if (c->g.nm < 2) return fail(c, QPIC_EINVAL, "a laser needs n_modes >= 2");
+    if (!(w0 > 0) || !(fwhm > 0)) return fail(c, QPIC_EINVAL, "laser parameters");
+    launch_laser(c, a0, w0, fwhm, z_centroid, z_focus, pol_angle);
+    return cuda_check(c, "add_laser");
+}
+
+qpic_status qpic_run_stages(qpic_ctx *c, int32_t stages)
+{
+    if (!c) return QPIC_EINVAL;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    run_one_step(c, stages);
+    qpic_status s = cuda_check(c, "run_stages");
+    if (s != QPIC_OK) return s;
+    return check_device_error(c);
+}
+
+qpic_status qpic_step(qpic_ctx *c, int32_t nsteps)
+{
+    if (!c || nsteps < 0) return QPIC_EINVAL;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    const int all = QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE |
+                    QPIC_STAGE_WINDOW | QPIC_STAGE_SORT;
+    for (int s = 0; s < nsteps; s++) run_one_step(c, all);
+    qpic_status st = cuda_check(c, "step");
+    if (st != QPIC_OK) return st;
+    return check_device_error(c);
+}
+
+qpic_status qpic_get_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mode, double *re,
+                           double *im)
+{
+    if (!c || !re || comp < 0 || comp > 2 || mode < 0 || mode >= c->g.nm || which < 0 || which > 4)
+        return fail(c, QPIC_EINVAL, "get_field arguments");
+    const FieldGeom &g = c->g;
+    const size_t nout = (size_t)(g.nr + 1) * g.nz;
+    if (which == QPIC_FIELD_RHO) {
+        double *d = nullptr;
+        size_t sz = (size_t)g.nm * 2 * nout;
+        if (!alloc_arr(c, &d, sz)) return fail(c, QPIC_ENOMEM, "rho buffer");
+        launch_rho(c, d);
+        cudaMemcpyAsync(re, d + (size_t)(2 * mode) * nout, nout * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream);
+        if (im)
+            cudaMemcpyAsync(im, d + (size_t)(2 * mode + 1) * nout, nout * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        dfree(c, d);
+        return cuda_check(c, "get_field rho");
+    }
+    std::vector<float> hre(g.plane), him(g.plane, 0.f);
+    const float *base = field_base(c, which);
+    int pre = mode == 0 ? 0 : 2 * mode - 1;
+    const float *src_re = base + (size_t)(comp * g.nparts + pre) * g.plane;
+    const float *src_im = mode ? base + (size_t)(comp * g.nparts + pre + 1) * g.plane : nullptr;
+    if (which == QPIC_FIELD_J && comp == QPIC_COMP_Z && c->j_filtered) {
+        src_re = c->Jzf + (size_t)pre * g.plane;
+        src_im = mode ? c->Jzf + (size_t)(pre + 1) * g.plane : nullptr;
+    }
+    cudaMemcpyAsync(hre.data(), src_re, g.plane * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (src_im)
+        cudaMemcpyAsync(him.data(), src_im, g.plane * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "get_field");
+    for (int j = 0; j <= g.nr; j++)
+        for (int il = 0; il < g.nz; il++) {
+            size_t q = (size_t)j * g.nzp + phys_col(c, il);
+            re[(size_t)j * g.nz + il] = hre[q];
+            if (im) im[(size_t)j * g.nz + il] = him[q];
+        }
+    return QPIC_OK;
+}
+
+qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mode, const double *re,
+                           const double *im)
+{
+    if (!c || !re || comp < 0 || comp > 2 || mode < 0 || mode >= c->g.nm ||
+        (which != QPIC_FIELD_E && which != QPIC_FIELD_B && which != QPIC_FIELD_BBAR))
+        return fail(c, QPIC_EINVAL, "set_field arguments");
+    const FieldGeom &g = c->g;
+    std::vector<float> hre(g.plane, 0.f), him(g.plane, 0.f);
+    for (int j = 0; j <= g.nr; j++)
+        for (int il = 0; il < g.nz; il++) {
+            size_t q = (size_t)j * g.nzp + phys_col(c, il);
+            hre[q] = (float)re[(size_t)j * g.nz + il];
+            him[q] = im ? (float)im[(size_t)j * g.nz + il] : 0.f;
+        }
+    float *base = field_base(c, which);
+    int pre = mode == 0 ? 0 : 2 * mode - 1;
+    cudaMemcpyAsync(base + (size_t)(comp * g.nparts + pre) * g.plane, hre.data(),
+                    g.plane * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (mode)
+        cudaMemcpyAsync(base + (size_t)(comp * g.nparts + pre + 1) * g.plane, him.data(),
+                        g.plane * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return cuda_check(c, "set_field");
+}
+
+qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
+{
+    if (!c || !n) return QPIC_EINVAL;
+    launch_sort(c);
+    *n = live_count(c);
+    return cuda_check(c, "num_particles");
+}
+
+qpic_status qpic_get_particles(qpic_ctx *c, double *out, int64_t capacity, int64_t *n_out)
+{
+    if (!c || !out || !n_out) return QPIC_EINVAL;
+    launch_sort(c);
+    long long n = live_count(c);
+    *n_out = n;
+    if (n > capacity) return fail(c, QPIC_ECAPACITY, "get_particles: capacity too small");
+    double *d = nullptr;
+    if (n > 0) {
+        if (!alloc_arr(c, &d, (size_t)9 * n)) return fail(c, QPIC_ENOMEM, "export buffer");
+        launch_export_particles(c, d, n);
+        for (int k = 0; k < 9; k++)
+            cudaMemcpyAsync(out + (size_t)k * capacity, d + (size_t)k * n, n * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        dfree(c, d);
+    }
+    return cuda_check(c, "get_particles");
+}
+
+qpic_status qpic_get_particles_raw(qpic_ctx *c, double *out, int64_t capacity, int64_t *n_out)
+{
+    if (!c || !out || !n_out) return QPIC_EINVAL;
+    long long n = live_count(c);           // buffer slots in use (device count)
+    *n_out = n;
+    if (n > capacity) return fail(c, QPIC_ECAPACITY, "get_particles_raw: capacity too small");
+    double *d = nullptr;
+    if (n > 0) {
+        if (!alloc_arr(c, &d, (size_t)9 * n)) return fail(c, QPIC_ENOMEM, "export buffer");
+        launch_export_particles(c, d, n);
+        for (int k = 0; k < 9; k++)
+            cudaMemcpyAsync(out + (size_t)k * capacity, d + (size_t)k * n, n * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
+        dfree(c, d);
+    }
+    return cuda_check(c, "get_particles_raw");
+}
+
+qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)
+{
+    if (!c || !out) return QPIC_EINVAL;
+    const int nm = c->g.nm;
+    std::vector<double> v(7 + nm, 0.0);
+    v[0] = c->nstep * c->dt;
+    v[1] = (double)c->nstep;
+    v[2] = (double)c->shifts;
+    double s3[3];
+    launch_particle_sums(c, s3);
+    v[3] = s3[0]; v[4] = s3[1]; v[5] = s3[2];
+    std::vector<double> fe(nm);
+    launch_field_energy(c, fe.data());
+    for (int m = 0; m < nm; m++) v[6 + m] = fe[m];
+    int e = 0;
+    cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    v[6 + nm] = (e & 1) ? 1.0 : 0.0;
+    for (int k = 0; k < count && k < (int)v.size(); k++) out[k] = v[k];
+    return cuda_check(c, "get_diag");
+}
+
+qpic_status qpic_profile(qpic_ctx *c, int32_t enable, int32_t reset)
+{
+    if (!c) return QPIC_EINVAL;
+    resolve_events(c);
+    c->profile = enable != 0;
+    if (reset) {
+        for (int k = 0; k < KC_COUNT; k++) { c->kms[k] = 0.0; c->klaunch[k] = 0; }
+    }
+    return QPIC_OK;
+}
+
+qpic_status qpic_launch_count(const qpic_ctx *c, int64_t *n)
+{
+    if (!c || !n) return QPIC_EINVAL;
+    *n = c->n_kernels;
+    return QPIC_OK;
+}
+
+qpic_status qpic_kernel_times(qpic_ctx *c, int32_t n, double *ms, int64_t *launches,
+                              const char **names, int32_t *n_classes)
+{
+    static const char *kNames[KC_COUNT] = {"faraday", "gather_push_deposit", "j_decode",
+                                           "jz_filter", "ampere", "sort", "window",
+                                           "inject", "diag", "other"};
+    if (!c) return QPIC_EINVAL;
+    resolve_events(c);
+    if (n_classes) *n_classes = KC_COUNT;
+    for (int k = 0; k < n && k < KC_COUNT; k++) {
+        if (ms) ms[k] = c->kms[k];
+        if (launches) launches[k] = c->klaunch[k];
+        if (names) names[k] = kNames[k];
+    }
+    return QPIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,533 @@
+// k_fields.cu -- FP32 field kernels of the quasi-3D dual solver (Sec. III.A-B).
+//
+// Faraday and Ampere per azimuthal mode on the (z, r) Yee grid, with the
+// extended z-stencils D^E_z (Faraday) and D^B_z (Ampere) of Eq. 9 and the
+// cylindrical radial operators; axis rules per mode; conducting wall.
+// Each block owns one r row and 128 z columns; the rows that need a z
+// derivative are staged in shared memory with an L-column halo on each side
+// (the z-stencil reaches L columns), every other operand is a coalesced
+// global read.  These kernels are bandwidth bound (about 18 floats read and
+// written per cell and part); the tensor cores have no role here.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "qpic_internal.h"
+
+namespace qpic {
+
+static const int FTILE = 128;     // z columns per solver block
+static const int JTILE = 256;     // z columns per filter block
+
+// Coefficients live in a per-context device array [cE (MAX_L) | cB (MAX_L) |
+// taps (MAX_TAPS)] (FP32 copies of the FP64 host values); blocks stage what
+// they use in shared memory, so several contexts can coexist in a process.
+void set_solver_constants(qpic_ctx *c)
+{
+    static_assert(MAX_L * 2 + MAX_TAPS <= 1024, "coefficient block size");
+    float h[2 * MAX_L + MAX_TAPS] = {0};
+    for (int l = 0; l < c->L; l++) { h[l] = (float)c->cE[l]; h[MAX_L + l] = (float)c->cB[l]; }
+    for (size_t q = 0; q < c->taps.size(); q++) h[2 * MAX_L + q] = (float)c->taps[q];
+    cudaMemcpyAsync(c->coef, h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+}
+
+struct GridArgs {
+    int nz, nr, nzp, nparts, L;
+    long long zoff;
+    size_t plane;
+    float dz, dr, dt;
+    const float *coef;     // [cE | cB | taps]
+};
+
+static GridArgs grid_args(const qpic_ctx *c)
+{
+    GridArgs a;
+    a.nz = c->g.nz; a.nr = c->g.nr; a.nzp = c->g.nzp; a.nparts = c->g.nparts; a.L = c->L;
+    a.zoff = c->g.zoff % c->g.nzp; a.plane = c->g.plane;
+    a.dz = (float)c->dz; a.dr = (float)c->dr; a.dt = (float)c->dt;
+    a.coef = c->coef;
+    return a;
+}
+
+__device__ __forceinline__ int wrapz(long long i, int nzp)
+{
+    long long r = i % nzp;
+    return (int)(r < 0 ? r + nzp : r);
+}
+
+// true when the physical column lies in the gap of an open box
+__device__ __forceinline__ bool in_gap(int col, const GridArgs &a)
+{
+    int l = wrapz((long long)col - a.zoff, a.nzp);
+    return l >= a.nz;
+}
+
+// mode number of a part and the (i m / r) coupling: returns the value of part p
+// of (i m / r) F given both parts of F (re = F[pr], im = F[pi])
+__device__ __forceinline__ int part_mode(int p) { return (p + 1) >> 1; }
+
+// ---------------------------------------------------------------- Faraday
+// dB/dt = -curl E:  B_r: -(i m/r) E_z + D^E_z E_phi;  B_phi: -D^E_z E_r + d_r E_z;
+// B_z: -(1/r) d_r(r E_phi) + (i m/r) E_r.  Writes B^{n+1/2} and Bbar^n.
+__global__ void __launch_bounds__(FTILE) k_faraday(const float *__restrict__ E, float *__restrict__ B,
+                                                  float *__restrict__ Bb, GridArgs a)
+{
+    extern __shared__ float sh[];
+    const int j = blockIdx.y;
+    const int i0 = blockIdx.x * FTILE;
+    const int W = FTILE + 2 * a.L;
+    const int P = a.nparts;
+    float *sC = sh;                  // [L] C^E
+    float *sEphi = sh + MAX_L;       // [P][W]
+    float *sEr = sEphi + P * W;      // [P][W]
+    for (int k = threadIdx.x; k < a.L; k += FTILE) sC[k] = a.coef[k];
+    for (int k = threadIdx.x; k < W; k += FTILE) {
+        int col = wrapz((long long)i0 - a.L + k, a.nzp);
+        for (int p = 0; p < P; p++) {
+            sEphi[p * W + k] = E[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            sEr[p * W + k] = E[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
+        }
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= a.nzp) return;
+    const bool gap = in_gap(i, a);
+    const float dr = a.dr, dz = a.dz, dt = a.dt;
+    const float rj = j * dr, rh = (j + 0.5f) * dr, rj1 = (j + 1) * dr;
+    const int s = threadIdx.x + a.L;   // smem index of column i
+    for (int p = 0; p < P; p++) {
+        const int m = part_mode(p);
+        const bool isim = (p > 0) && !(p & 1);
+        const int pr = isim ? p - 1 : p, pim = isim ? p : p + 1;   // re / im partner
+        // D^E_z of E_phi and E_r at i + 1/2
+        float dEphi = 0.f, dEr = 0.f;
+        for (int l = 1; l <= a.L; l++) {
+            float cl = sC[l - 1];
+            dEphi += cl * (sEphi[p * W + s + l] - sEphi[p * W + s + 1 - l]);
+            dEr += cl * (sEr[p * W + s + l] - sEr[p * W + s + 1 - l]);
+        }
+        dEphi /= dz; dEr /= dz;
+        const size_t base = (size_t)j * a.nzp + i;
+        // B_r at (i+1/2, j)
+        float d;
+        if (j == 0) {
+            if (m == 1) {
+                // -(i/r) E_z -> -i E_z^1(dr)/dr on the axis
+                const float *Ez = E + (size_t)(2 * P) * a.plane + (size_t)1 * a.nzp + i;
+                float ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
+                d = (isim ? -ezr : ezi) / dr + dEphi;
+            } else {
+                d = 0.f;
+            }
+        } else {
+            float imr = 0.f;
+            if (m > 0) {
+                const float *Ez = E + (size_t)(2 * P) * a.plane + base;
+                float ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
+                imr = (isim ? ezr : -ezi) * (float)m / rj;      // part of (i m / r) E_z
+            }
+            d = -imr + dEphi;
+        }
+        {
+            size_t q = (size_t)(0 * P + p) * a.plane + base;
+            float bo = B[q], bn = gap ? 0.f : bo + dt * d;
+            B[q] = bn; Bb[q] = gap ? 0.f : 0.5f * (bo + bn);
+        }
+        if (j < a.nr) {
+            // B_phi at (i+1/2, j+1/2)
+            const float *Ez = E + (size_t)(2 * P + p) * a.plane + base;
+            d = -dEr + (Ez[a.nzp] - Ez[0]) / dr;
+            size_t q = (size_t)(1 * P + p) * a.plane + base;
+            float bo = B[q], bn = gap ? 0.f : bo + dt * d;
+            B[q] = bn; Bb[q] = gap ? 0.f : 0.5f * (bo + bn);
+            // B_z at (i, j+1/2)
+            const float *Ep = E + (size_t)(1 * P + p) * a.plane + base;
+            float imr = 0.f;
+            if (m > 0) {
+                const float *Er = E + (size_t)(0 * P) * a.plane + base;
+                float err_ = Er[(size_t)pr * a.plane], eri = Er[(size_t)pim * a.plane];
+                imr = (isim ? err_ : -eri) * (float)m / rh;
+            }
+            d = -(rj1 * Ep[a.nzp] - rj * Ep[0]) / (rh * dr) + imr;
+            q = (size_t)(2 * P + p) * a.plane + base;
+            bo = B[q]; bn = gap ? 0.f : bo + dt * d;
+            B[q] = bn; Bb[q] = gap ? 0.f : 0.5f * (bo + bn);
+        } else {
+            // half-r row beyond the wall: not advanced; its average is the value itself
+            size_t q = (size_t)(1 * P + p) * a.plane + base;
+            Bb[q] = gap ? 0.f : B[q];
+            q = (size_t)(2 * P + p) * a.plane + base;
+            Bb[q] = gap ? 0.f : B[q];
+        }
+    }
+}
+
+void launch_faraday(qpic_ctx *c)
+{
+    GridArgs a = grid_args(c);
+    dim3 grid((a.nzp + FTILE - 1) / FTILE, a.nr + 1);
+    size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
+    prof_begin(c);
+    k_faraday<<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Bb, a);
+    prof_end(c, KC_FARADAY);
+}
+
+// ---------------------------------------------------------------- J decode
+// int64 fixed point -> FP32 current with the per-row finite-volume factors,
+// and the accumulator is cleared for the next deposit.
+__global__ void k_jdecode(unsigned long long *__restrict__ Jacc, float *__restrict__ Jf,
+                          const float *__restrict__ rowf, GridArgs a, float inv_qscale, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int pl = blockIdx.z;            // plane = comp * nparts + part
+    if (i >= a.nzp) return;
+    const int comp = pl / a.nparts, part = pl % a.nparts;
+    const size_t q = (size_t)pl * a.plane + (size_t)j * a.nzp + i;
+    long long v = (long long)Jacc[q];
+    Jacc[q] = 0ull;
+    if (v > (1ll << 62) || v < -(1ll << 62)) atomicOr(err, 1);     // fixed-point headroom gone
+    float f;
+    if (comp == 2) f = rowf[j];                                   // J_z
+    else if (comp == 0) f = rowf[(a.nr + 1) + j];                  // J_r
+    else f = part == 0 ? rowf[3 * (a.nr + 1) + j] : rowf[2 * (a.nr + 1) + j];  // J_phi
+    Jf[q] = in_gap(i, a) ? 0.f : __ll2float_rn(v) * inv_qscale * f;
+}
+
+void launch_jdecode(qpic_ctx *c)
+{
+    GridArgs a = grid_args(c);
+    dim3 grid((a.nzp + 255) / 256, a.nr + 1, 3 * a.nparts);
+    prof_begin(c);
+    k_jdecode<<<grid, 256, 0, c->stream>>>(c->Jacc, c->Jf, c->rowf, a, 1.0f / c->qscale,
+                                           c->d_err);
+    prof_end(c, KC_JDECODE);
+}
+
+// ---------------------------------------------------------------- J_z filter
+// J_z <- K * J_z along z (symbol [k]_Yee/[k]_B): keeps Gauss's law in the dual
+// form when the deposit satisfies the two-point continuity equation.
+__global__ void __launch_bounds__(JTILE) k_jfilter(const float *__restrict__ Jf, float *__restrict__ Jzf,
+                                                  GridArgs a, int nk)
+{
+    extern __shared__ float sh2[];
+    const int j = blockIdx.y, p = blockIdx.z;
+    const int i0 = blockIdx.x * JTILE;
+    const int H = nk - 1, W = JTILE + 2 * H;
+    float *sT = sh2, *sh = sh2 + MAX_TAPS;
+    for (int k = threadIdx.x; k < nk; k += JTILE) sT[k] = a.coef[2 * MAX_L + k];
+    const float *src = Jf + (size_t)(2 * a.nparts + p) * a.plane + (size_t)j * a.nzp;
+    for (int k = threadIdx.x; k < W; k += JTILE) sh[k] = src[wrapz((long long)i0 - H + k, a.nzp)];
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= a.nzp) return;
+    const int s = threadIdx.x + H;
+    float acc = sT[0] * sh[s];
+    for (int q = 1; q < nk; q++) acc += sT[q] * (sh[s + q] + sh[s - q]);
+    Jzf[(size_t)p * a.plane + (size_t)j * a.nzp + i] = in_gap(i, a) ? 0.f : acc;
+}
+
+void launch_jfilter(qpic_ctx *c)
+{
+    GridArgs a = grid_args(c);
+    int nk = (int)c->taps.size();
+    dim3 grid((a.nzp + JTILE - 1) / JTILE, a.nr + 1, a.nparts);
+    size_t sm = (size_t)(MAX_TAPS + JTILE + 2 * (nk - 1)) * sizeof(float);
+    prof_begin(c);
+    k_jfilter<<<grid, JTILE, sm, c->stream>>>(c->Jf, c->Jzf, a, nk);
+    prof_end(c, KC_JFILTER);
+}
+
+// ---------------------------------------------------------------- Ampere
+// dE/dt = curl B - J:  E_r: (i m/r) B_z - D^B_z B_phi - J_r;
+// E_phi: D^B_z B_r - d_r B_z - J_phi;  E_z: (1/r) d_r(r B_phi) - (i m/r) B_r - J_z.
+// Axis: m = 0: E_phi = 0, E_z uses 4 B_phi(dr/2)/dr; m = 1: E_z = 0,
+// d_r B_z(0) = 2 B_z(dr/2)/dr; m >= 2: 0.  Wall: E_phi = E_z = 0.
+__global__ void __launch_bounds__(FTILE) k_ampere(float *__restrict__ E, const float *__restrict__ B,
+                                                 const float *__restrict__ Jf,
+                                                 const float *__restrict__ Jz, GridArgs a)
+{
+    extern __shared__ float sh[];
+    const int j = blockIdx.y;
+    const int i0 = blockIdx.x * FTILE;
+    const int W = FTILE + 2 * a.L;
+    const int P = a.nparts;
+    float *sC = sh;                      // [L] C^B
+    float *sBphi = sh + MAX_L, *sBr = sBphi + P * W;
+    for (int k = threadIdx.x; k < a.L; k += FTILE) sC[k] = a.coef[MAX_L + k];
+    for (int k = threadIdx.x; k < W; k += FTILE) {
+        int col = wrapz((long long)i0 - a.L + k, a.nzp);
+        for (int p = 0; p < P; p++) {
+            sBphi[p * W + k] = B[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            sBr[p * W + k] = B[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
+        }
+    }
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= a.nzp) return;
+    const bool gap = in_gap(i, a);
+    const float dr = a.dr, dz = a.dz, dt = a.dt;
+    const float rj = j * dr, rh = (j + 0.5f) * dr, rl = (j - 0.5f) * dr;
+    const int s = threadIdx.x + a.L;
+    const size_t base = (size_t)j * a.nzp + i;
+    for (int p = 0; p < P; p++) {
+        const int m = part_mode(p);
+        const bool isim = (p > 0) && !(p & 1);
+        const int pr = isim ? p - 1 : p, pim = isim ? p : p + 1;
+        // D^B_z of B_phi and B_r at integer i: sum_l C_l (f_{i+l-1/2} - f_{i-l+1/2})
+        float dBphi = 0.f, dBr = 0.f;
+        for (int l = 1; l <= a.L; l++) {
+            float cl = sC[l - 1];
+            dBphi += cl * (sBphi[p * W + s + l - 1] - sBphi[p * W + s - l]);
+            dBr += cl * (sBr[p * W + s + l - 1] - sBr[p * W + s - l]);
+        }
+        dBphi /= dz; dBr /= dz;
+        // E_r at (i, j+1/2)
+        if (j < a.nr) {
+            float imr = 0.f;
+            if (m > 0) {
+                const float *Bz = B + (size_t)(2 * P) * a.plane + base;
+                float bzr = Bz[(size_t)pr * a.plane], bzi = Bz[(size_t)pim * a.plane];
+                imr = (isim ? bzr : -bzi) * (float)m / rh;
+            }
+            size_t q = (size_t)(0 * P + p) * a.plane + base;
+            float d = imr - dBphi - Jf[q];
+            E[q] = gap ? 0.f : E[q] + dt * d;
+        }
+        // E_phi at (i, j)
+        {
+            size_t q = (size_t)(1 * P + p) * a.plane + base;
+            float v;
+            if (j == a.nr || (j == 0 && m != 1)) {
+                v = 0.f;
+            } else if (j == 0) {
+                const float *Bz = B + (size_t)(2 * P + p) * a.plane + base;
+                float d = dBr - 2.f * Bz[0] / dr - Jf[q];
+                v = E[q] + dt * d;
+            } else {
+                const float *Bz = B + (size_t)(2 * P + p) * a.plane + base;
+                float d = dBr - (Bz[0] - Bz[-(long long)a.nzp]) / dr - Jf[q];
+                v = E[q] + dt * d;
+            }
+            E[q] = gap ? 0.f : v;
+        }
+        // E_z at (i+1/2, j)
+        {
+            size_t q = (size_t)(2 * P + p) * a.plane + base;
+            size_t qz = (size_t)p * a.plane + base;
+            float v;
+            if (j == a.nr || (j == 0 && m != 0)) {
+                v = 0.f;
+            } else if (j == 0) {
+                const float *Bp = B + (size_t)(1 * P + p) * a.plane + base;
+                v = E[q] + dt * (4.f * Bp[0] / dr - Jz[qz]);
+            } else {
+                const float *Bp = B + (size_t)(1 * P + p) * a.plane + base;
+                float imr = 0.f;
+                if (m > 0) {
+                    const float *Br = B + (size_t)(0 * P) * a.plane + base;
+                    float brr = Br[(size_t)pr * a.plane], bri = Br[(size_t)pim * a.plane];
+                    imr = (isim ? brr : -bri) * (float)m / rj;
+                }
+                float d = (rh * Bp[0] - rl * Bp[-(long long)a.nzp]) / (rj * dr) - imr - Jz[qz];
+                v = E[q] + dt * d;
+            }
+            E[q] = gap ? 0.f : v;
+        }
+    }
+}
+
+void launch_ampere(qpic_ctx *c)
+{
+    GridArgs a = grid_args(c);
+    dim3 grid((a.nzp + FTILE - 1) / FTILE, a.nr + 1);
+    size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
+    const float *jz = c->taps.empty() ? c->Jf + (size_t)2 * a.nparts * a.plane : c->Jzf;
+    prof_begin(c);
+    k_ampere<<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Jf, jz, a);
+    prof_end(c, KC_AMPERE);
+}
+
+// ---------------------------------------------------------------- window column
+__global__ void k_zero_column(float *E, float *B, float *Bb, float *Jf, float *Jzf, int col,
+                              GridArgs a, int nplanes, int nzf)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pl = blockIdx.y;
+    if (j > a.nr) return;
+    size_t q = (size_t)pl * a.plane + (size_t)j * a.nzp + col;
+    E[q] = 0.f; B[q] = 0.f; Bb[q] = 0.f; Jf[q] = 0.f;
+    if (pl < nzf) Jzf[q] = 0.f;
+}
+
+void launch_zero_column(qpic_ctx *c, long long phys_col)
+{
+    GridArgs a = grid_args(c);
+    int np = 3 * a.nparts;
+    dim3 grid((a.nr + 1 + 127) / 128, np);
+    prof_begin(c);
+    k_zero_column<<<grid, 128, 0, c->stream>>>(c->E, c->B, c->Bb, c->Jf, c->Jzf,
+                                               (int)(phys_col % a.nzp), a, np, a.nparts);
+    prof_end(c, KC_WINDOW);
+}
+
+// ---------------------------------------------------------------- laser
+// Paraxial Gaussian beam (Eq. 18 near focus), evaluated in FP64 per grid point:
+// q = (z - z_f) - i zR, zR = w0^2/2, A = (-i zR/q) exp(i r^2/(2q)),
+// Ex_c = a0 env(xi) (-i) A e^{i(xi + (1-omega) t)}, xi = z - z_c - t,
+// env = exp(-2 ln2 xi^2/fwhm^2); E_x = Re Ex_c, E_z = Re(-(x/q) Ex_c),
+// B_y = E_x, B_z = Re(-(y/q) Ex_c).  m = 1 amplitudes (polarisation psi):
+// E_r = Ex/2, E_phi = i Ex/2, E_z = r h/2, B_r = -i By/2, B_phi = By/2,
+// B_z = -i r h/2 with h = Re(-Ex_c/q), all times e^{-i psi}.
+struct LaserArgs {
+    double a0, w0, fwhm, zc, zf, psi, omega, ratio, zmin, Lz, dz, dr, dt;
+    int periodic;
+};
+
+__device__ void laser_core(const LaserArgs &L, double z, double r, double t, double *exr,
+                           double *hr)
+{
+    double xi = z - L.zc - t;
+    if (L.periodic) {
+        xi = fmod(xi + 0.5 * L.Lz, L.Lz);
+        if (xi < 0) xi += L.Lz;
+        xi -= 0.5 * L.Lz;
+    }
+    double env = exp(-2.0 * 0.69314718055994530942 * xi * xi / (L.fwhm * L.fwhm));
+    double zR = 0.5 * L.w0 * L.w0;
+    double qr = z - L.zf, qi = -zR;                      // q = qr + i qi
+    double qq = qr * qr + qi * qi;
+    // 1/q = (qr - i qi)/|q|^2 ; i r^2 / (2q) = i r^2 (qr - i qi) / (2|q|^2)
+    double er = r * r * qi / (2.0 * qq);                  // real part of i r^2/(2q)
+    double ei = r * r * qr / (2.0 * qq);                  // imag part
+    double mag = exp(er);
+    double cr = mag * cos(ei), ci = mag * sin(ei);        // exp(i r^2/(2q))
+    // -i zR / q = -i zR (qr - i qi)/qq = (-zR qi - i zR qr)/qq
+    double pr_ = -zR * qi / qq, pi_ = -zR * qr / qq;
+    double Ar = pr_ * cr - pi_ * ci, Ai = pr_ * ci + pi_ * cr;
+    // (-i) A = Ai - i Ar
+    double Br_ = Ai, Bi_ = -Ar;
+    double ph = xi + (1.0 - L.omega) * t;
+    double sr = cos(ph), si = sin(ph);
+    double exc_r = L.a0 * env * (Br_ * sr - Bi_ * si);
+    double exc_i = L.a0 * env * (Br_ * si + Bi_ * sr);
+    *exr = exc_r;
+    // h = Re(-Ex_c / q) = -Re(Ex_c (qr - i qi))/qq = -(exc_r qr + exc_i qi)/qq
+    *hr = -(exc_r * qr + exc_i * qi) / qq;
+}
+
+__global__ void k_laser(float *E, float *B, GridArgs a, LaserArgs L)
+{
+    const int il = blockIdx.x * blockDim.x + threadIdx.x;     // logical column
+    const int j = blockIdx.y;
+    if (il >= a.nz) return;
+    const int col = wrapz((long long)il + a.zoff, a.nzp);
+    const size_t base = (size_t)j * a.nzp + col;
+    const int P = a.nparts;
+    const double cp = cos(L.psi), sp = -sin(L.psi);           // e^{-i psi}
+    const double zi = L.zmin + il * L.dz, zh = zi + 0.5 * L.dz;
+    const double ri = j * L.dr, rh = (j + 0.5) * L.dr;
+    double ex, h;
+    // value (vr + i vi) * e^{-i psi} added to mode-1 planes of component comp
+    auto add = [&](float *F, int comp, double vr, double vi, bool zero) {
+        if (zero) return;
+        double wr = vr * cp - vi * sp, wi = vr * sp + vi * cp;
+        F[(size_t)(comp * P + 1) * a.plane + base] += (float)wr;
+        F[(size_t)(comp * P + 2) * a.plane + base] += (float)wi;
+    };
+    const bool wall = (j == a.nr);
+    // E at t = 0
+    laser_core(L, zi, rh, 0.0, &ex, &h);
+    add(E, 0, 0.5 * ex, 0.0, wall);                           // E_r (i, j+1/2)
+    laser_core(L, zi, ri, 0.0, &ex, &h);
+    add(E, 1, 0.0, 0.5 * ex, wall);                           // E_phi (i, j)
+    laser_core(L, zh, ri, 0.0, &ex, &h);
+    add(E, 2, 0.5 * ri * h, 0.0, wall || j == 0);             // E_z (i+1/2, j)
+    // B at t = -dt/2, times the discrete B/E ratio
+    const double t = -0.5 * L.dt, R = L.ratio;
+    laser_core(L, zh, ri, t, &ex, &h);
+    add(B, 0, 0.0, -0.5 * ex * R, wall);                      // B_r (i+1/2, j)
+    laser_core(L, zh, rh, t, &ex, &h);
+    add(B, 1, 0.5 * ex * R, 0.0, wall);                       // B_phi (i+1/2, j+1/2)
+    laser_core(L, zi, rh, t, &ex, &h);
+    add(B, 2, 0.0, -0.5 * rh * h * R, wall);                  // B_z (i, j+1/2)
+}
+
+void launch_laser(qpic_ctx *c, double a0, double w0, double fwhm, double zc, double zf, double psi)
+{
+    GridArgs a = grid_args(c);
+    LaserArgs L;
+    L.a0 = a0; L.w0 = w0; L.fwhm = fwhm; L.zc = zc; L.zf = zf; L.psi = psi;
+    L.omega = 2.0 / c->dt * asin(0.5 * c->dt * sqrt(c->kE1 * c->kB1));
+    L.ratio = sqrt(c->kE1 / c->kB1);
+    L.zmin = c->shifts * c->dz; L.Lz = c->g.nz * c->dz; L.dz = c->dz; L.dr = c->dr; L.dt = c->dt;
+    L.periodic = c->g.periodic;
+    dim3 grid((a.nz + 127) / 128, a.nr + 1);
+    prof_begin(c);
+    k_laser<<<grid, 128, 0, c->stream>>>(c->E, c->B, a, L);
+    prof_end(c, KC_OTHER);
+}
+
+// ---------------------------------------------------------------- field energy (FP64)
+// 1/2 sum V(r_loc) (|E|^2 + |B|^2) per mode, each component at its own radius,
+// modes m >= 1 counted twice.  Deterministic two-pass reduction.
+__global__ void k_energy_partial(const float *E, const float *B, GridArgs a, double *part)
+{
+    __shared__ double red[256];
+    const int j = blockIdx.y, m = blockIdx.z;
+    const double PI = 3.14159265358979323846;
+    const double dr = a.dr, dz = a.dz, R = a.nr * dr;
+    double Vi, Vh;
+    if (j == 0) Vi = PI * 0.25 * dr * dr * dz;
+    else if (j == a.nr) Vi = PI * (R * R - (R - 0.5 * dr) * (R - 0.5 * dr)) * dz;
+    else Vi = 2.0 * PI * j * dr * dr * dz;
+    Vh = (j < a.nr) ? 2.0 * PI * (j + 0.5) * dr * dr * dz : 0.0;
+    double s = 0.0;
+    for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < a.nz; il += gridDim.x * blockDim.x) {
+        int col = wrapz((long long)il + a.zoff, a.nzp);
+        size_t base = (size_t)j * a.nzp + col;
+        for (int k = 0; k < (m ? 2 : 1); k++) {
+            int p = m ? 2 * m - 1 + k : 0;
+            auto v2 = [&](const float *F, int comp) {
+                double x = F[(size_t)(comp * a.nparts + p) * a.plane + base];
+                return x * x;
+            };
+            s += Vh * (v2(E, 0) + v2(B, 1) + v2(B, 2)) + Vi * (v2(E, 1) + v2(E, 2) + v2(B, 0));
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        part[((size_t)m * gridDim.y + j) * gridDim.x + blockIdx.x] = red[0] * (m ? 1.0 : 0.5);
+}
+
+__global__ void k_sum_ordered(const double *part, int n_per, int nseg, double *out)
+{
+    // one thread per segment, sums in index order (deterministic)
+    int sgm = threadIdx.x;
+    if (sgm >= nseg) return;
+    double s = 0.0;
+    for (int k = 0; k < n_per; k++) s += part[(size_t)sgm * n_per + k];
+    out[sgm] = s;
+}
+
+void launch_field_energy(qpic_ctx *c, double *out_modes)
+{
+    GridArgs a = grid_args(c);
+    const int nm = c->g.nm, nbx = 4;
+    dim3 grid(nbx, a.nr + 1, nm);
+    size_t need = (size_t)nbx * (a.nr + 1) * nm + nm;
+    if ((size_t)c->red_cap < need) return;
+    prof_begin(c);
+    k_energy_partial<<<grid, 256, 0, c->stream>>>(c->E, c->B, a, c->d_red);
+    k_sum_ordered<<<1, 32, 0, c->stream>>>(c->d_red, nbx * (a.nr + 1), nm, c->d_red + need - nm);
+    prof_end(c, KC_DIAG, 2);
+    cudaMemcpyAsync(out_modes, c->d_red + need - nm, nm * sizeof(double), cudaMemcpyDeviceToHost,
+                    c->stream);
+    cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace qpic

@@ -1,0 +1,932 @@
+// k_particles.cu -- the particle half of the quasi-3D PIC step (FP32 path).
+//
+// k_gpd: one CTA per particle tile (TZ x TR cells, particles sorted by tile).
+//   1. E^n and Bbar^n of the tile plus a halo are staged in shared memory
+//      (mode-parity images below the axis, even images beyond the wall, zeros
+//      in the gap of an open box), so the gather never branches on boundaries.
+//   2. per particle: bilinear gather of every mode at each component's own
+//      staggered point, modal sum F_0 + 2 Re(F_m e^{i m phi}) (Sec. III.B),
+//      rotation to x, y; relativistic Boris push with E^n and Bbar^n
+//      (Eq. 6 time-centred as in Eq. 12); Cartesian move and an update of
+//      (r, cos phi, sin phi) written with cancellation-free differences;
+//      optional modal work (Eq. 16).
+//   3. charge-conserving deposit per mode into int64 fixed-point shared
+//      accumulators.  The modal charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
+//      splits into (S1 - S0)(e0 + e1)/2, carried by 2D Esirkepov r/z fluxes,
+//      and (S0 + S1)/2 (e1 - e0), carried by J_phi through (i m / r) J_phi.
+//   4. the tile's accumulators go to global memory with int64 atomics; integer
+//      addition makes the step independent of particle order (bit-reproducible).
+//   Particles beyond the staged halo (drift between sorts, or injected by the
+//   moving window) run the same code against global memory.
+//
+// k_count / scan / k_scatter: counting sort of live particles by a tile-major
+// cell key; dead particles are dropped.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "qpic_internal.h"
+
+namespace qpic {
+
+struct PArgs {
+    int nz, nr, nzp, nparts, nm;
+    long long zoff;
+    size_t plane;
+    float dz, dr, dt, inv_dz, inv_dr, R;
+    int periodic;
+    int TZ, TR, ntz, ntr, H;
+    float qscale;
+    int track_work;
+};
+
+static PArgs pargs(const qpic_ctx *c)
+{
+    PArgs a;
+    a.nz = c->g.nz; a.nr = c->g.nr; a.nzp = c->g.nzp; a.nparts = c->g.nparts; a.nm = c->g.nm;
+    a.zoff = c->g.zoff % c->g.nzp; a.plane = c->g.plane;
+    a.dz = (float)c->dz; a.dr = (float)c->dr; a.dt = (float)c->dt;
+    a.inv_dz = (float)(1.0 / c->dz); a.inv_dr = (float)(1.0 / c->dr);
+    a.R = (float)(c->g.nr * c->dr);
+    a.periodic = c->g.periodic;
+    a.TZ = c->TZ; a.TR = c->TR; a.ntz = c->ntz; a.ntr = c->ntr; a.H = c->halo;
+    a.qscale = c->qscale;
+    a.track_work = c->cfg.track_work;
+    return a;
+}
+
+__device__ __forceinline__ int pwrap(long long i, int n)
+{
+    long long r = i % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+// staggering: E_r (0,1) E_phi (0,0) E_z (1,0); B_r (1,0) B_phi (1,1) B_z (0,1)
+__host__ __device__ __forceinline__ int hz_of(int fb, int c) { return fb == 0 ? (c == 2) : (c != 2); }
+__host__ __device__ __forceinline__ int hr_of(int fb, int c) { return fb == 0 ? (c == 0) : (c != 0); }
+
+// sample of plane (fb: 0 = E, 1 = Bbar; comp c; part p) at physical column col
+// (any integer, wrapped) and row j (any integer).  Half-r components continue
+// below the axis with the mode parity (radial/azimuthal (-1)^(m+1), B_z (-1)^m)
+// and beyond the wall with their even image; integer-r components are 0 outside.
+__device__ __forceinline__ float gsample(const float *E, const float *Bb, const PArgs &a, int fb,
+                                         int c, int p, int j, long long col)
+{
+    const float *F = fb == 0 ? E : Bb;
+    float sgn = 1.f;
+    if (hr_of(fb, c)) {
+        if (j < 0) {
+            int m = (p + 1) >> 1;
+            bool longitudinal = (fb == 1 && c == 2);
+            bool odd = ((m & 1) != 0) != !longitudinal;   // radial: (-1)^(m+1); z: (-1)^m
+            sgn = odd ? -1.f : 1.f;
+            j = -1 - j;
+        }
+        if (j >= a.nr) j = 2 * a.nr - 1 - j;
+        if (j < 0 || j >= a.nr) return 0.f;
+    } else {
+        if (j < 0 || j > a.nr) return 0.f;
+    }
+    int ic = pwrap(col, a.nzp);
+    return sgn * F[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic];
+}
+
+// ------------------------------------------------------------ accessors
+struct SmemAcc {
+    const float *sf;             // [2][3][P][FR][FW]
+    unsigned long long *sJ;      // [3][P][JR][JW]
+    int FW, FR, JW, JR, P;
+    __device__ __forceinline__ float f(int fb, int c, int p, int lj, int li) const
+    {
+        return sf[((size_t)((fb * 3 + c) * P + p) * FR + lj) * FW + li];
+    }
+    __device__ __forceinline__ void jadd(int c, int p, int lj, int li, long long v) const
+    {
+        if (v) atomicAdd(&sJ[((size_t)(c * P + p) * JR + lj) * JW + li], (unsigned long long)v);
+    }
+};
+
+struct GlobAcc {
+    const float *E, *Bb;
+    unsigned long long *J;
+    PArgs a;
+    __device__ __forceinline__ float f(int fb, int c, int p, int j, int i) const
+    {
+        return gsample(E, Bb, a, fb, c, p, j, i);
+    }
+    __device__ __forceinline__ void jadd(int c, int p, int j, int i, long long v) const
+    {
+        if (!v || j < 0 || j > a.nr) return;
+        int ic = pwrap(i, a.nzp);
+        atomicAdd(&J[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic],
+                  (unsigned long long)v);
+    }
+};
+
+__device__ __forceinline__ long long fx(float x, float qs) { return __float2ll_rn(x * qs); }
+
+// Linear-shape values S0 and differences dS = S1 - S0 at nodes k = -1..2 (index
+// k+1) for a move x0 -> x0 + d in old-cell coordinates (x0 in [0,1), |d| < 1).
+// A move inside the cell gives dS = (-d, +d) exactly, without cancellation.
+__device__ __forceinline__ void shape_delta(float x0, float d, float S0[4], float dS[4], int &lo,
+                                            int &hi)
+{
+    float x1 = x0 + d;
+    S0[0] = 0.f; S0[1] = 1.f - x0; S0[2] = x0; S0[3] = 0.f;
+    if (x1 >= 1.f) {
+        dS[0] = 0.f; dS[1] = x0 - 1.f; dS[2] = (2.f - 2.f * x0) - d; dS[3] = (x0 - 1.f) + d;
+        lo = 1; hi = 3;
+    } else if (x1 < 0.f) {
+        dS[0] = -(x0 + d); dS[1] = 2.f * x0 + d; dS[2] = -x0; dS[3] = 0.f;
+        lo = 0; hi = 2;
+    } else {
+        dS[0] = 0.f; dS[1] = -d; dS[2] = d; dS[3] = 0.f;
+        lo = 1; hi = 2;
+    }
+}
+
+struct PState {
+    float oz, orr, cph, sph, ux, uy, uz, w, W0, W1;
+    int jr;          // r cell (absolute)
+    int diz, djr;    // cell change of the move
+};
+
+// One particle: gather, push, move, deposit.  (bi, bj): accessor coordinates of
+// its cell.  On return the offsets, angle and momentum are the new ones and
+// (diz, djr) the cell change.
+template <int NP, class Acc>
+__device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, int bi, int bj,
+                                              PState &s)
+{
+    constexpr int NM = (NP + 1) / 2;
+    const float oz = s.oz, orr = s.orr, cph = s.cph, sph = s.sph;
+    // ---- interpolation weights on the integer and half grids
+    const int ozh = oz >= 0.5f ? 0 : -1, orh = orr >= 0.5f ? 0 : -1;
+    const float wzH = oz >= 0.5f ? oz - 0.5f : oz + 0.5f;
+    const float wrH = orr >= 0.5f ? orr - 0.5f : orr + 0.5f;
+    float F[2][3][NP];
+#pragma unroll
+    for (int fb = 0; fb < 2; fb++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int hz = hz_of(fb, c), hr = hr_of(fb, c);
+            const int i0 = bi + (hz ? ozh : 0), j0 = bj + (hr ? orh : 0);
+            const float tz = hz ? wzH : oz, tr = hr ? wrH : orr;
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+                float v00 = acc.f(fb, c, p, j0, i0), v01 = acc.f(fb, c, p, j0, i0 + 1);
+                float v10 = acc.f(fb, c, p, j0 + 1, i0), v11 = acc.f(fb, c, p, j0 + 1, i0 + 1);
+                float lo = v00 + tz * (v01 - v00), hi = v10 + tz * (v11 - v10);
+                F[fb][c][p] = lo + tr * (hi - lo);
+            }
+        }
+    // ---- modal sum, rotation to Cartesian
+    float cm[NM], sm[NM];
+    cm[0] = 1.f; sm[0] = 0.f;
+#pragma unroll
+    for (int m = 1; m < NM; m++) {
+        cm[m] = cm[m - 1] * cph - sm[m - 1] * sph;
+        sm[m] = sm[m - 1] * cph + cm[m - 1] * sph;
+    }
+    float Ec[3], Bc[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float e = F[0][c][0], b = F[1][c][0];
+#pragma unroll
+        for (int m = 1; m < NM; m++) {
+            e += 2.f * (F[0][c][2 * m - 1] * cm[m] - F[0][c][2 * m] * sm[m]);
+            b += 2.f * (F[1][c][2 * m - 1] * cm[m] - F[1][c][2 * m] * sm[m]);
+        }
+        Ec[c] = e; Bc[c] = b;
+    }
+    const float Ex = Ec[0] * cph - Ec[1] * sph, Ey = Ec[0] * sph + Ec[1] * cph, Ez = Ec[2];
+    const float Bx = Bc[0] * cph - Bc[1] * sph, By = Bc[0] * sph + Bc[1] * cph, Bz = Bc[2];
+    // ---- relativistic Boris push, q = -1
+    const float h = -0.5f * a.dt;
+    const float ux = s.ux, uy = s.uy, uz = s.uz;
+    const float g_old = sqrtf(1.f + ux * ux + uy * uy + uz * uz);
+    float umx = ux + h * Ex, umy = uy + h * Ey, umz = uz + h * Ez;
+    float gm = sqrtf(1.f + umx * umx + umy * umy + umz * umz);
+    float tx = h * Bx / gm, ty = h * By / gm, tz = h * Bz / gm;
+    float t2 = tx * tx + ty * ty + tz * tz;
+    float f2 = 2.f / (1.f + t2);
+    float sx = f2 * tx, sy = f2 * ty, sz = f2 * tz;
+    float upx = umx + (umy * tz - umz * ty);
+    float upy = umy + (umz * tx - umx * tz);
+    float upz = umz + (umx * ty - umy * tx);
+    float unx = umx + (upy * sz - upz * sy) + h * Ex;
+    float uny = umy + (upz * sx - upx * sz) + h * Ey;
+    float unz = umz + (upx * sy - upy * sx) + h * Ez;
+    const float g = sqrtf(1.f + unx * unx + uny * uny + unz * unz);
+    const float vx = unx / g, vy = uny / g, vz = unz / g;
+    if (a.track_work) {
+        // Eq. 16: W_m += q dt E^m . v, v at time n the mean of u/gamma at n -+ 1/2
+        float wx = 0.5f * (ux / g_old + vx), wy = 0.5f * (uy / g_old + vy),
+              wz = 0.5f * (uz / g_old + vz);
+        float E0x = F[0][0][0] * cph - F[0][1][0] * sph, E0y = F[0][0][0] * sph + F[0][1][0] * cph;
+        float p0 = E0x * wx + E0y * wy + F[0][2][0] * wz;
+        float pt = Ex * wx + Ey * wy + Ez * wz;
+        s.W0 -= a.dt * p0;
+        s.W1 -= a.dt * (pt - p0);
+    }
+    // ---- move in Cartesian x, y; r and angle with cancellation-free differences
+    const float ddz = a.dt * vz;
+    float ddx = a.dt * vx, ddy = a.dt * vy;
+    const float r0 = ((float)s.jr + orr) * a.dr;
+    const float x0 = r0 * cph, y0 = r0 * sph;
+    float x1 = x0 + ddx, y1 = y0 + ddy;
+    float r1 = sqrtf(x1 * x1 + y1 * y1);
+    float drr, c1, s1, dc, ds;
+    if (r1 <= a.R) {
+        float den = r0 + r1;
+        drr = den > 0.f ? (ddx * (2.f * x0 + ddx) + ddy * (2.f * y0 + ddy)) / den : 0.f;
+        if (r1 > 0.f) {
+            float ir = 1.f / r1;
+            c1 = x1 * ir; s1 = y1 * ir;
+            dc = (ddx - cph * drr) * ir; ds = (ddy - sph * drr) * ir;
+        } else {
+            c1 = cph; s1 = sph; dc = 0.f; ds = 0.f;
+        }
+    } else {                               // specular reflection at the wall
+        float cr = x1 / r1, sr = y1 / r1;
+        float urad = unx * cr + uny * sr;
+        unx -= 2.f * urad * cr; uny -= 2.f * urad * sr;
+        float rn = 2.f * a.R - r1;
+        x1 = cr * rn; y1 = sr * rn; r1 = rn;
+        ddx = x1 - x0; ddy = y1 - y0;
+        drr = r1 - r0; c1 = cr; s1 = sr; dc = c1 - cph; ds = s1 - sph;
+    }
+    const float dzc = ddz * a.inv_dz, drc = drr * a.inv_dr;
+    // ---- deposit
+    float S0z[4], dSz[4], S0r[4], dSr[4];
+    int zlo, zhi, rlo, rhi;
+    shape_delta(oz, dzc, S0z, dSz, zlo, zhi);
+    shape_delta(orr, drc, S0r, dSr, rlo, rhi);
+    const float Q = -s.w, qs = a.qscale;
+    // e^{-i m phi} at the start and its change over the move, m = 1..NM-1
+    float e0r[NM], e0i[NM], der[NM], dei[NM];
+    e0r[0] = 1.f; e0i[0] = 0.f; der[0] = 0.f; dei[0] = 0.f;
+    if (NM > 1) {
+        const float a0r = cph, a0i = -sph, adr = dc, adi = -ds;     // e0_1, de_1
+        const float a1r = a0r + adr, a1i = a0i + adi;                // e1_1
+#pragma unroll
+        for (int m = 1; m < NM; m++) {
+            if (m == 1) { e0r[1] = a0r; e0i[1] = a0i; der[1] = adr; dei[1] = adi; continue; }
+            // e0_m = e0_{m-1} e0_1 ; de_m = de_{m-1} e1_1 + e0_{m-1} de_1
+            e0r[m] = e0r[m - 1] * a0r - e0i[m - 1] * a0i;
+            e0i[m] = e0r[m - 1] * a0i + e0i[m - 1] * a0r;
+            der[m] = der[m - 1] * a1r - dei[m - 1] * a1i + e0r[m - 1] * adr - e0i[m - 1] * adi;
+            dei[m] = der[m - 1] * a1i + dei[m - 1] * a1r + e0r[m - 1] * adi + e0i[m - 1] * adr;
+        }
+    }
+    // z fluxes through faces (i0+k+1/2, j0+kr): prefix sums of W^z along z
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        if (b < rlo || b > rhi) continue;
+        const float srb = S0r[b] + 0.5f * dSr[b];
+        float accw = 0.f;
+#pragma unroll
+        for (int a2 = 0; a2 < 3; a2++) {
+            if (a2 < zlo || a2 >= zhi) continue;
+            accw += dSz[a2] * srb;
+            const float X = -Q * accw;
+            const int lj = bj + b - 1, li = bi + a2 - 1;
+            acc.jadd(2, 0, lj, li, fx(X, qs));
+#pragma unroll
+            for (int m = 1; m < NM; m++) {
+                float ebr = e0r[m] + 0.5f * der[m], ebi = e0i[m] + 0.5f * dei[m];
+                acc.jadd(2, 2 * m - 1, lj, li, fx(X * ebr, qs));
+                acc.jadd(2, 2 * m, lj, li, fx(X * ebi, qs));
+            }
+        }
+    }
+    // r fluxes through faces (i0+k, j0+kr+1/2): prefix sums of W^r along r
+#pragma unroll
+    for (int a2 = 0; a2 < 4; a2++) {
+        if (a2 < zlo || a2 > zhi) continue;
+        const float sza = S0z[a2] + 0.5f * dSz[a2];
+        float accw = 0.f;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (b < rlo || b >= rhi) continue;
+            accw += dSr[b] * sza;
+            const float X = -Q * accw;
+            const int lj = bj + b - 1, li = bi + a2 - 1;
+            acc.jadd(0, 0, lj, li, fx(X, qs));
+#pragma unroll
+            for (int m = 1; m < NM; m++) {
+                float ebr = e0r[m] + 0.5f * der[m], ebi = e0i[m] + 0.5f * dei[m];
+                acc.jadd(0, 2 * m - 1, lj, li, fx(X * ebr, qs));
+                acc.jadd(0, 2 * m, lj, li, fx(X * ebi, qs));
+            }
+        }
+    }
+    // azimuthal current at nodes: m = 0 from the mid-point azimuthal displacement,
+    // m >= 1 from i Q Sbar (e1 - e0) / m
+    const float xm = x0 + 0.5f * ddx, ym = y0 + 0.5f * ddy;
+    const float rm = sqrtf(xm * xm + ym * ym);
+    const float aphi = rm > 0.f ? (x0 * ddy - y0 * ddx) / (rm * a.dr) : 0.f;
+#pragma unroll
+    for (int a2 = 0; a2 < 4; a2++) {
+        if (a2 < zlo || a2 > zhi) continue;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            if (b < rlo || b > rhi) continue;
+            const float sb = S0z[a2] * S0r[b] +
+                             0.5f * (S0z[a2] * dSr[b] + dSz[a2] * S0r[b] + dSz[a2] * dSr[b]);
+            const int lj = bj + b - 1, li = bi + a2 - 1;
+            const float QS = Q * sb;
+            acc.jadd(1, 0, lj, li, fx(QS * aphi, qs));
+#pragma unroll
+            for (int m = 1; m < NM; m++) {
+                const float im = 1.f / (float)m;
+                acc.jadd(1, 2 * m - 1, lj, li, fx(-QS * dei[m] * im, qs));
+                acc.jadd(1, 2 * m, lj, li, fx(QS * der[m] * im, qs));
+            }
+        }
+    }
+    // ---- new state: offsets renormalised into the cell
+    float nz_ = oz + dzc, nr_ = orr + drc;
+    int diz = 0, djr = 0;
+    if (nz_ >= 1.f) { nz_ -= 1.f; diz = 1; } else if (nz_ < 0.f) { nz_ += 1.f; diz = -1; }
+    if (nz_ >= 1.f) nz_ = 0.99999994f;          // rounding guard
+    if (nr_ >= 1.f) { nr_ -= 1.f; djr = 1; } else if (nr_ < 0.f) { nr_ += 1.f; djr = -1; }
+    if (nr_ >= 1.f) nr_ = 0.99999994f;
+    if (s.jr + djr >= a.nr) { djr = a.nr - 1 - s.jr; nr_ = 0.99999994f; }   // r = R exactly
+    if (s.jr + djr < 0) { djr = -s.jr; nr_ = 0.f; }
+    s.oz = nz_; s.orr = nr_; s.cph = c1; s.sph = s1;
+    s.ux = unx; s.uy = uny; s.uz = unz;
+    s.diz = diz; s.djr = djr;
+}
+
+// ------------------------------------------------------------ the GPD kernel
+template <int NP>
+__global__ void __launch_bounds__(256) k_gpd(Particles P, const float *__restrict__ E,
+                                            const float *__restrict__ Bb,
+                                            unsigned long long *__restrict__ J,
+                                            const int32_t *__restrict__ offsets,
+                                            const long long *__restrict__ dcount, PArgs a,
+                                            int ntiles, int tail_chunk)
+{
+    extern __shared__ unsigned long long sraw[];
+    const int H = a.H;
+    const int FW = a.TZ + 2 * H + 2, FR = a.TR + 2 * H + 2;
+    const int JW = FW + 1, JR = FR + 1;
+    long long begin, end;
+    bool tile_mode = blockIdx.x < (unsigned)ntiles;
+    int tz0 = 0, tr0 = 0;
+    if (tile_mode) {
+        const int t = blockIdx.x;
+        const int TS = a.TZ * a.TR;
+        begin = offsets[(size_t)t * TS];
+        end = offsets[(size_t)(t + 1) * TS];
+        if (begin == end) return;
+        tz0 = (t / a.ntr) * a.TZ;
+        tr0 = (t % a.ntr) * a.TR;
+    } else {
+        const long long nsorted = dcount[1], np = dcount[0];
+        begin = nsorted + (long long)(blockIdx.x - ntiles) * tail_chunk;
+        end = min(begin + tail_chunk, np);
+        if (begin >= end) return;
+    }
+    GlobAcc gacc{E, Bb, J, a};
+    SmemAcc sacc;
+    const long long col0 = (long long)tz0 - H - 1;
+    const int row0 = tr0 - H - 1;
+    if (tile_mode) {
+        unsigned long long *sJ = sraw;
+        float *sf = reinterpret_cast<float *>(sraw + (size_t)3 * NP * JW * JR);
+        sacc = SmemAcc{sf, sJ, FW, FR, JW, JR, NP};
+        const int nJ = 3 * NP * JW * JR;
+        for (int k = threadIdx.x; k < nJ; k += blockDim.x) sJ[k] = 0ull;
+        const int nF = 6 * NP * FW * FR;
+        for (int k = threadIdx.x; k < nF; k += blockDim.x) {
+            int li = k % FW, t2 = k / FW, lj = t2 % FR, pl = t2 / FR;
+            int p = pl % NP, cc = (pl / NP) % 3, fb = pl / (3 * NP);
+            sf[k] = gsample(E, Bb, a, fb, cc, p, row0 + lj, col0 + li);
+        }
+        __syncthreads();
+    }
+    for (long long idx = begin + threadIdx.x; idx < end; idx += blockDim.x) {
+        int cell = P.cell[idx];
+        if (cell < 0) continue;
+        int iz = cell / a.nr, jr = cell - iz * a.nr;
+        if (!a.periodic && pwrap((long long)iz - a.zoff, a.nzp) >= a.nz) {
+            P.cell[idx] = -1;                  // behind the moving window
+            continue;
+        }
+        PState s;
+        s.oz = P.oz[idx]; s.orr = P.orr[idx]; s.cph = P.cph[idx]; s.sph = P.sph[idx];
+        s.ux = P.ux[idx]; s.uy = P.uy[idx]; s.uz = P.uz[idx]; s.w = P.w[idx];
+        s.W0 = a.track_work ? P.W0[idx] : 0.f;
+        s.W1 = a.track_work ? P.W1[idx] : 0.f;
+        s.jr = jr;
+        bool done = false;
+        if (tile_mode) {
+            int li = pwrap((long long)iz - col0, a.nzp), lj = jr - row0;
+            if (li >= 1 && li <= FW - 2 && lj >= 1 && lj <= FR - 2 && a.nzp >= 2 * JW) {
+                push_particle<NP>(sacc, a, li, lj, s);
+                done = true;
+            }
+        }
+        if (!done) push_particle<NP>(gacc, a, iz, jr, s);
+        int niz = pwrap((long long)iz + s.diz, a.nzp);
+        int njr = jr + s.djr;
+        bool dead = !a.periodic && pwrap((long long)niz - a.zoff, a.nzp) >= a.nz;
+        P.cell[idx] = dead ? -1 : niz * a.nr + njr;
+        P.oz[idx] = s.oz; P.orr[idx] = s.orr; P.cph[idx] = s.cph; P.sph[idx] = s.sph;
+        P.ux[idx] = s.ux; P.uy[idx] = s.uy; P.uz[idx] = s.uz;
+        if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+    }
+    if (tile_mode) {
+        __syncthreads();
+        const int nJ = 3 * NP * JW * JR;
+        for (int k = threadIdx.x; k < nJ; k += blockDim.x) {
+            unsigned long long v = sacc.sJ[k];
+            if (!v) continue;
+            int li = k % JW, t2 = k / JW, lj = t2 % JR, pl = t2 / JR;
+            int j = row0 + lj;
+            if (j < 0 || j > a.nr) continue;
+            int col = pwrap(col0 + li, a.nzp);
+            atomicAdd(&J[(size_t)pl * a.plane + (size_t)j * a.nzp + col], v);
+        }
+    }
+}
+
+static size_t gpd_smem(const qpic_ctx *c)
+{
+    const int H = c->halo, P = c->g.nparts;
+    const int FW = c->TZ + 2 * H + 2, FR = c->TR + 2 * H + 2;
+    return (size_t)3 * P * (FW + 1) * (FR + 1) * 8 + (size_t)6 * P * FW * FR * 4;
+}
+
+static const int TAIL_CHUNK = 4096;
+
+void launch_gpd(qpic_ctx *c)
+{
+    PArgs a = pargs(c);
+    const int ntiles = c->ntz * c->ntr;
+    long long tail = c->n_tail;              // particles appended since the last sort
+    int ntail = (int)((tail + TAIL_CHUNK - 1) / TAIL_CHUNK);
+    int grid = ntiles + ntail;
+    size_t sm = gpd_smem(c);
+    long long *dcount = c->d_count;   // [0] np, [1] nsorted
+    prof_begin(c);
+    switch (c->g.nparts) {
+    case 1:
+        cudaFuncSetAttribute(k_gpd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_gpd<1><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
+                                               ntiles, TAIL_CHUNK);
+        break;
+    case 3:
+        cudaFuncSetAttribute(k_gpd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_gpd<3><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
+                                               ntiles, TAIL_CHUNK);
+        break;
+    case 5:
+        cudaFuncSetAttribute(k_gpd<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_gpd<5><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
+                                               ntiles, TAIL_CHUNK);
+        break;
+    default:
+        cudaFuncSetAttribute(k_gpd<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_gpd<7><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
+                                               ntiles, TAIL_CHUNK);
+        break;
+    }
+    prof_end(c, KC_GPD);
+}
+
+// ------------------------------------------------------------ sort
+__device__ __forceinline__ int sort_key(int cell, const PArgs &a)
+{
+    int iz = cell / a.nr, jr = cell - iz * a.nr;
+    int tzi = iz / a.TZ, tri = jr / a.TR;
+    return ((tzi * a.ntr + tri) * a.TR + (jr - tri * a.TR)) * a.TZ + (iz - tzi * a.TZ);
+}
+
+__global__ void k_count(const int32_t *__restrict__ cell, const long long *dcount, int32_t *counts,
+                        PArgs a)
+{
+    const long long np = dcount[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        int c = cell[i];
+        if (c >= 0) atomicAdd(&counts[sort_key(c, a)], 1);
+    }
+}
+
+// exclusive scan of n ints: per-block scan of 4096 elements, block sums, add
+static const int SCAN_B = 1024, SCAN_I = 4;
+
+__device__ int block_excl_scan(int v, int *sh)
+{
+    // warp inclusive scan, then scan of warp totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t;
+    }
+    __syncthreads();
+    int base = wid ? sh[wid - 1] : 0;
+    int r = base + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_local(const int32_t *in, int32_t *out, int32_t *bsum, long long n)
+{
+    __shared__ int sh[32];
+    long long base = (long long)blockIdx.x * SCAN_B * SCAN_I + (long long)threadIdx.x * SCAN_I;
+    int v[SCAN_I], tot = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) { v[k] = (base + k < n) ? in[base + k] : 0; tot += v[k]; }
+    int ex = block_excl_scan(tot, sh);
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        if (base + k < n) out[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == blockDim.x - 1) bsum[blockIdx.x] = ex;
+}
+
+__global__ void k_scan_sums(int32_t *bsum, int nb, int32_t *total_out)
+{
+    __shared__ int sh[32];
+    __shared__ int last;
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += SCAN_B) {
+        int i = b0 + threadIdx.x;
+        int v = i < nb ? bsum[i] : 0;
+        int ex = block_excl_scan(v, sh);
+        if (i < nb) bsum[i] = ex + carry;
+        if (threadIdx.x == SCAN_B - 1) last = ex + v;
+        __syncthreads();
+        carry += last;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int32_t *out, const int32_t *bsum, long long n)
+{
+    long long base = (long long)blockIdx.x * SCAN_B * SCAN_I + (long long)threadIdx.x * SCAN_I;
+    int add = bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++)
+        if (base + k < n) out[base + k] += add;
+}
+
+__global__ void k_scatter(Particles src, Particles dst, const long long *dcount, int32_t *counts,
+                          const int32_t *offsets, PArgs a)
+{
+    const long long np = dcount[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        int c = src.cell[i];
+        if (c < 0) continue;
+        int k = sort_key(c, a);
+        int pos = atomicSub(&counts[k], 1) - 1;
+        long long d = (long long)offsets[k] + pos;
+        dst.cell[d] = c; dst.oz[d] = src.oz[i]; dst.orr[d] = src.orr[i];
+        dst.cph[d] = src.cph[i]; dst.sph[d] = src.sph[i];
+        dst.ux[d] = src.ux[i]; dst.uy[d] = src.uy[i]; dst.uz[d] = src.uz[i]; dst.w[d] = src.w[i];
+        if (a.track_work) { dst.W0[d] = src.W0[i]; dst.W1[d] = src.W1[i]; }
+    }
+}
+
+__global__ void k_set_counts(long long *dcount, const int32_t *total)
+{
+    dcount[0] = *total;
+    dcount[1] = *total;
+}
+
+void launch_sort(qpic_ctx *c)
+{
+    PArgs a = pargs(c);
+    const long long n = c->nkeys;
+    long long *dcount = c->d_count;
+    prof_begin(c);
+    cudaMemsetAsync(c->counts, 0, (size_t)(n + 1) * sizeof(int32_t), c->stream);
+    int nblk = 152 * 8;
+    k_count<<<nblk, 256, 0, c->stream>>>(c->p.cell, dcount, c->counts, a);
+    const long long per = (long long)SCAN_B * SCAN_I;
+    int nb = (int)((n + 1 + per - 1) / per);
+    k_scan_local<<<nb, SCAN_B, 0, c->stream>>>(c->counts, c->offsets, c->scan_tmp, n + 1);
+    k_scan_sums<<<1, SCAN_B, 0, c->stream>>>(c->scan_tmp, nb, c->scan_tmp + nb);
+    k_scan_add<<<nb, SCAN_B, 0, c->stream>>>(c->offsets, c->scan_tmp, n + 1);
+    k_scatter<<<nblk, 256, 0, c->stream>>>(c->p, c->ps, dcount, c->counts, c->offsets, a);
+    k_set_counts<<<1, 1, 0, c->stream>>>(dcount, c->offsets + n);
+    prof_end(c, KC_SORT, 6);
+    Particles t = c->p; c->p = c->ps; c->ps = t;
+    c->n_tail = 0;
+}
+
+// ------------------------------------------------------------ plasma loading
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014) on state x + gamma
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct PlasmaArgs {
+    double n0, z_start, ramp_len, dz, dr, zmin;
+    unsigned long long seed;
+    int pz, pr, pp, jitter, nr, nzp;
+    long long first_col, shifts, zoff, base;
+    int ncols;
+};
+
+__global__ void k_load_plasma(Particles P, PlasmaArgs L, long long ntot, int track,
+                              const long long *dcount, long long cap, int *err)
+{
+    const double PI = 3.14159265358979323846;
+    const long long base = L.base < 0 ? dcount[0] : L.base;      // append at the live count
+    if (base + ntot > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 2);
+        return;
+    }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ntot;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long q = t;
+        int c = (int)(q % L.pp); q /= L.pp;
+        int b = (int)(q % L.pr); q /= L.pr;
+        int a = (int)(q % L.pz); q /= L.pz;
+        int jr = (int)(q % L.nr); q /= L.nr;
+        long long il = L.first_col + q;                       // logical column
+        long long iz_abs = il + L.shifts;
+        double z = ((double)iz_abs + (a + 0.5) / L.pz) * L.dz;
+        double r = (jr + (b + 0.5) / L.pr) * L.dr;
+        double jit = 0.0;
+        if (L.jitter) {
+            unsigned long long key = (L.seed << 40) ^ ((unsigned long long)iz_abs << 20) ^
+                                     (unsigned long long)jr;
+            jit = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
+        }
+        double phi = 2.0 * PI * (c + jit) / L.pp;
+        double n;
+        if (L.ramp_len <= 0.0) n = z >= L.z_start ? L.n0 : 0.0;
+        else n = L.n0 * fmin(fmax((z - L.z_start) / L.ramp_len, 0.0), 1.0);
+        double w = n * 2.0 * PI * r * (L.dr / L.pr) * (L.dz / L.pz) / L.pp;
+        long long d = base + t;
+        int iz = (int)(((il + L.zoff) % L.nzp + L.nzp) % L.nzp);
+        P.cell[d] = w > 0.0 ? iz * L.nr + jr : -1;
+        P.oz[d] = (float)((a + 0.5) / L.pz);
+        P.orr[d] = (float)((b + 0.5) / L.pr);
+        P.cph[d] = (float)cos(phi); P.sph[d] = (float)sin(phi);
+        P.ux[d] = 0.f; P.uy[d] = 0.f; P.uz[d] = 0.f; P.w[d] = (float)w;
+        if (track) { P.W0[d] = 0.f; P.W1[d] = 0.f; }
+    }
+}
+
+__global__ void k_add_count(long long *dcount, long long add, int set_sorted)
+{
+    dcount[0] += add;
+    if (set_sorted) dcount[1] = dcount[0];
+}
+
+int launch_load_plasma(qpic_ctx *c, long long first_col, int ncols, bool append)
+{
+    PlasmaArgs L;
+    L.n0 = c->n0; L.z_start = c->z_start; L.ramp_len = c->ramp_len;
+    L.dz = c->dz; L.dr = c->dr; L.zmin = c->shifts * c->dz;
+    L.seed = c->cfg.seed; L.pz = c->ppc_z; L.pr = c->ppc_r; L.pp = c->ppc_phi;
+    L.jitter = c->jitter; L.nr = c->g.nr; L.nzp = c->g.nzp;
+    L.first_col = first_col; L.shifts = c->shifts; L.zoff = c->g.zoff % c->g.nzp;
+    L.ncols = ncols;
+    long long ntot = (long long)ncols * c->g.nr * L.pz * L.pr * L.pp;
+    L.base = append ? -1 : 0;
+    if ((append ? c->np : 0) + ntot > c->cap) return 0;          // host-side upper bound
+    long long *dcount = c->d_count;
+    prof_begin(c);
+    int nblk = (int)std::min<long long>((ntot + 255) / 256, 152LL * 16);
+    if (nblk < 1) nblk = 1;
+    k_load_plasma<<<nblk, 256, 0, c->stream>>>(c->p, L, ntot, c->cfg.track_work, dcount, c->cap,
+                                               c->d_err);
+    if (append) {
+        k_add_count<<<1, 1, 0, c->stream>>>(dcount, ntot, 0);
+    } else {
+        cudaMemsetAsync(dcount, 0, 2 * sizeof(long long), c->stream);
+        k_add_count<<<1, 1, 0, c->stream>>>(dcount, ntot, 0);
+    }
+    prof_end(c, KC_INJECT, 2);
+    if (append) { c->np += ntot; c->n_tail += ntot; }
+    else { c->np = ntot; c->n_tail = ntot; }
+    return 1;
+}
+
+// ------------------------------------------------------------ load / export
+struct LoadArgs {
+    double zmin, dz, dr;
+    int nz, nr, nzp, periodic;
+    long long zoff;
+};
+
+__global__ void k_load_particles(Particles P, long long n, const double *z, const double *r,
+                                 const double *phi, const double *ux, const double *uy,
+                                 const double *uz, const double *w, LoadArgs L, int track)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double zl = (z[i] - L.zmin) / L.dz;
+        double fl = floor(zl);
+        long long il = (long long)fl;
+        double oz = zl - fl;
+        bool dead = false;
+        if (L.periodic) il = ((il % L.nz) + L.nz) % L.nz;
+        else if (il < 0 || il >= L.nz) dead = true;
+        double rc = r[i] / L.dr;
+        int jr = (int)floor(rc);
+        double orr = rc - jr;
+        if (jr >= L.nr) { jr = L.nr - 1; orr = 1.0; }
+        if (jr < 0) { jr = 0; orr = 0.0; }
+        float ozf = (float)oz, orf = (float)orr;
+        if (ozf >= 1.f) ozf = 0.99999994f;
+        if (orf >= 1.f) orf = 0.99999994f;
+        int iz = (int)(((il + L.zoff) % L.nzp + L.nzp) % L.nzp);
+        P.cell[i] = (dead || !(w[i] > 0.0)) ? -1 : iz * L.nr + jr;
+        P.oz[i] = ozf; P.orr[i] = orf;
+        P.cph[i] = (float)cos(phi[i]); P.sph[i] = (float)sin(phi[i]);
+        P.ux[i] = (float)ux[i]; P.uy[i] = (float)uy[i]; P.uz[i] = (float)uz[i];
+        P.w[i] = (float)w[i];
+        if (track) { P.W0[i] = 0.f; P.W1[i] = 0.f; }
+    }
+}
+
+static LoadArgs load_args(const qpic_ctx *c)
+{
+    LoadArgs L;
+    L.zmin = c->shifts * c->dz; L.dz = c->dz; L.dr = c->dr;
+    L.nz = c->g.nz; L.nr = c->g.nr; L.nzp = c->g.nzp; L.periodic = c->g.periodic;
+    L.zoff = c->g.zoff % c->g.nzp;
+    return L;
+}
+
+void launch_load_particles(qpic_ctx *c, long long n, const double *z, const double *r,
+                           const double *phi, const double *ux, const double *uy, const double *uz,
+                           const double *w)
+{
+    LoadArgs L = load_args(c);
+    long long *dcount = c->d_count;
+    int nblk = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (nblk < 1) nblk = 1;
+    prof_begin(c);
+    if (n > 0)
+        k_load_particles<<<nblk, 256, 0, c->stream>>>(c->p, n, z, r, phi, ux, uy, uz, w, L,
+                                                       c->cfg.track_work);
+    cudaMemsetAsync(dcount, 0, 2 * sizeof(long long), c->stream);
+    k_add_count<<<1, 1, 0, c->stream>>>(dcount, n, 0);
+    prof_end(c, KC_OTHER, n > 0 ? 2 : 1);
+    c->np = n;
+    c->n_tail = n;
+}
+
+// out: [9][stride] FP64 SoA z, r, phi, ux, uy, uz, w, W0, W1 of particles [0, np)
+__global__ void k_export(Particles P, long long n, double *out, long long stride, LoadArgs L,
+                         int track)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int cell = P.cell[i];
+        const bool dead = cell < 0;
+        if (dead) cell = 0;
+        int iz = cell / L.nr, jr = cell - iz * L.nr;
+        long long il = ((long long)iz - L.zoff) % L.nzp;
+        if (il < 0) il += L.nzp;
+        out[0 * stride + i] = L.zmin + ((double)il + (double)P.oz[i]) * L.dz;
+        out[1 * stride + i] = ((double)jr + (double)P.orr[i]) * L.dr;
+        out[2 * stride + i] = atan2((double)P.sph[i], (double)P.cph[i]);
+        out[3 * stride + i] = P.ux[i];
+        out[4 * stride + i] = P.uy[i];
+        out[5 * stride + i] = P.uz[i];
+        out[6 * stride + i] = dead ? 0.0 : (double)P.w[i];
+        out[7 * stride + i] = track ? P.W0[i] : 0.0;
+        out[8 * stride + i] = track ? P.W1[i] : 0.0;
+    }
+}
+
+void launch_export_particles(qpic_ctx *c, double *dout, long long stride)
+{
+    LoadArgs L = load_args(c);
+    long long n = c->np;
+    int nblk = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (nblk < 1) nblk = 1;
+    if (n > 0) k_export<<<nblk, 256, 0, c->stream>>>(c->p, n, dout, stride, L, c->cfg.track_work);
+}
+
+// ------------------------------------------------------------ rho (diagnostic)
+// rho_m(i,j) = sum_p Q S_i S_j e^{-i m phi} / V_j in FP64, logical order,
+// out planes [nm][2][nr+1][nz]
+__global__ void k_rho(Particles P, long long n, double *out, LoadArgs L, int nm)
+{
+    const double PI = 3.14159265358979323846;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int cell = P.cell[i];
+        if (cell < 0) continue;
+        int iz = cell / L.nr, jr = cell - iz * L.nr;
+        long long il = ((long long)iz - L.zoff) % L.nzp;
+        if (il < 0) il += L.nzp;
+        double oz = P.oz[i], orr = P.orr[i], Q = -(double)P.w[i];
+        double c1 = P.cph[i], s1 = -(double)P.sph[i];      // e^{-i phi}
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) {
+                long long ic = il + a;
+                if (L.periodic) ic %= L.nz;
+                else if (ic >= L.nz) continue;
+                int j = jr + b;
+                double wgt = (a ? oz : 1.0 - oz) * (b ? orr : 1.0 - orr);
+                double R = L.nr * L.dr, V;
+                if (j == 0) V = PI * 0.25 * L.dr * L.dr * L.dz;
+                else if (j == L.nr) V = PI * (R * R - (R - 0.5 * L.dr) * (R - 0.5 * L.dr)) * L.dz;
+                else V = 2.0 * PI * j * L.dr * L.dr * L.dz;
+                double er = 1.0, ei = 0.0;
+                for (int m = 0; m < nm; m++) {
+                    if (m) { double t = er * c1 - ei * s1; ei = er * s1 + ei * c1; er = t; }
+                    size_t q = ((size_t)(m * 2) * (L.nr + 1) + j) * L.nz + ic;
+                    size_t qi = ((size_t)(m * 2 + 1) * (L.nr + 1) + j) * L.nz + ic;
+                    atomicAdd(&out[q], Q * wgt * er / V);
+                    atomicAdd(&out[qi], Q * wgt * ei / V);
+                }
+            }
+    }
+}
+
+void launch_rho(qpic_ctx *c, double *dplanes)
+{
+    LoadArgs L = load_args(c);
+    long long n = c->np;
+    size_t sz = (size_t)c->g.nm * 2 * (c->g.nr + 1) * c->g.nz;
+    cudaMemsetAsync(dplanes, 0, sz * sizeof(double), c->stream);
+    int nblk = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    if (nblk < 1) nblk = 1;
+    if (n > 0) k_rho<<<nblk, 256, 0, c->stream>>>(c->p, n, dplanes, L, c->g.nm);
+}
+
+// ------------------------------------------------------------ particle sums
+__global__ void k_psums_partial(Particles P, const long long *dcount, double *part)
+{
+    __shared__ double s0[256], s1[256], s2[256];
+    const long long n = dcount[0];
+    double cnt = 0, chg = 0, ke = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (P.cell[i] < 0) continue;
+        double w = P.w[i], ux = P.ux[i], uy = P.uy[i], uz = P.uz[i];
+        cnt += 1.0; chg -= w;
+        ke += w * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+    }
+    s0[threadIdx.x] = cnt; s1[threadIdx.x] = chg; s2[threadIdx.x] = ke;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s0[threadIdx.x] += s0[threadIdx.x + w];
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = s0[0]; part[3 * blockIdx.x + 1] = s1[0];
+        part[3 * blockIdx.x + 2] = s2[0];
+    }
+}
+
+__global__ void k_psums_final(const double *part, int nb, double *out)
+{
+    if (threadIdx.x >= 3) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; b++) s += part[3 * b + threadIdx.x];
+    out[threadIdx.x] = s;
+}
+
+void launch_particle_sums(qpic_ctx *c, double *out3)
+{
+    const int nb = 304;
+    double *part = c->d_red + 8;
+    long long *dcount = c->d_count;
+    prof_begin(c);
+    k_psums_partial<<<nb, 256, 0, c->stream>>>(c->p, dcount, part);
+    k_psums_final<<<1, 32, 0, c->stream>>>(part, nb, part + 3 * nb);
+    prof_end(c, KC_DIAG, 2);
+    cudaMemcpyAsync(out3, part + 3 * nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace qpic

@@ -1,0 +1,187 @@
+// qpic_internal.h -- context layout and kernel entry points of libqpic.
+//
+// Device data layout (FP32 path)
+//   Fields: planes of (nr+1) rows x nzp columns, z fastest.  A component c in
+//   {r, phi, z} has nparts = 2*n_modes - 1 planes: part 0 = mode 0 (real),
+//   part 2m-1 = Re F_m, part 2m = Im F_m; plane index = c*nparts + part.
+//   The z axis is a circular buffer of nzp = nz + gap physical columns: logical
+//   column i lives at physical (i + zoff) mod nzp.  An open box keeps a gap of
+//   zero columns wider than every stencil, so stencils that reach past either
+//   end read zeros; a periodic box has gap = 0 and wraps.  A moving window only
+//   advances zoff, zeroes the column that left and fills the new front one.
+//   Particles: structure of arrays, 36 B each: cell = iz_phys*nr + jr (int32,
+//   -1 = dead), oz, or in [0,1) (offsets in the cell), cos phi, sin phi,
+//   ux, uy, uz, w (float); optional W0, W1 (modal work, Eq. 16).
+//   Current: int64 fixed point per plane, value = round(X * qscale) where X is
+//   the per-particle "charge" quantity of the deposit; J = X * row factor.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qpic.h"
+
+namespace qpic {
+
+constexpr int MAX_L = 64;      // max coefficients per z-operator
+constexpr int MAX_TAPS = 512;  // max J_z filter half-length
+constexpr int MAX_MODES = 4;
+
+struct FieldGeom {
+    int nz, nr, nzp, gap, nparts, nm;
+    long long zoff;            // physical column of logical 0 (mod nzp)
+    size_t plane;              // (nr+1)*nzp
+    float dz, dr, dt;
+    int periodic;
+};
+
+struct Particles {
+    int32_t *cell = nullptr;
+    float *oz = nullptr, *orr = nullptr, *cph = nullptr, *sph = nullptr;
+    float *ux = nullptr, *uy = nullptr, *uz = nullptr, *w = nullptr;
+    float *W0 = nullptr, *W1 = nullptr;
+};
+
+struct Particles64 {  // plain FP64 path: lab z, Cartesian x, y
+    double *z = nullptr, *x = nullptr, *y = nullptr, *ux = nullptr, *uy = nullptr,
+           *uz = nullptr, *w = nullptr, *W0 = nullptr, *W1 = nullptr;
+};
+
+enum KernelClass {
+    KC_FARADAY = 0, KC_GPD, KC_JDECODE, KC_JFILTER, KC_AMPERE, KC_SORT, KC_WINDOW,
+    KC_INJECT, KC_DIAG, KC_OTHER, KC_COUNT
+};
+
+}  // namespace qpic
+
+struct qpic_ctx {
+    qpic_config cfg;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool fp64 = false;
+
+    // grid and solver
+    qpic::FieldGeom g;
+    double dz, dr, dt;
+    int L = 1;
+    double cE[qpic::MAX_L], cB[qpic::MAX_L];
+    std::vector<double> taps;     // k_0..k_{nk-1}; empty = no filter
+    double kE1, kB1;              // symbols at k = 1 (laser set-up)
+
+    // window / time
+    long long shifts = 0, nstep = 0;
+
+    // FP32 fields
+    float *E = nullptr, *B = nullptr, *Bb = nullptr, *Jf = nullptr, *Jzf = nullptr;
+    unsigned long long *Jacc = nullptr;
+    float *rowf = nullptr;        // [4][nr+1]: J_z, J_r, J_phi(m>=1), J_phi(m=0)
+    float *coef = nullptr;        // [cE (MAX_L) | cB (MAX_L) | taps (MAX_TAPS)] FP32
+    bool j_filtered = false;      // J_z of the last deposit has been filtered
+
+    // FP64 fields (plain path)
+    double *E64 = nullptr, *B64 = nullptr, *Bb64 = nullptr, *J64 = nullptr, *Jz64 = nullptr;
+
+    // particles
+    long long np = 0, cap = 0;    // np: host upper bound of the device count d_count[0]
+    long long n_tail = 0;         // particles appended since the last sort (unsorted tail)
+    long long *d_count = nullptr; // device: [0] particles in the buffer, [1] of them sorted
+    qpic::Particles p, ps;        // live buffers and the sort's second buffer
+    qpic::Particles64 p64;
+    double qref = 0.0;            // max |charge| of a particle
+    float qscale = 0.f;           // fixed-point scale 2^44 / qref
+
+    // plasma (for the moving-window injection)
+    bool have_plasma = false;
+    double n0 = 0, z_start = 0, ramp_len = 0;
+    int ppc_z = 0, ppc_r = 0, ppc_phi = 0, jitter = 0;
+
+    // tiles and sort
+    int TZ = 16, TR = 8, ntz = 0, ntr = 0, halo = 1;
+    long long nkeys = 0;
+    int32_t *counts = nullptr, *offsets = nullptr, *scan_tmp = nullptr;
+    int sort_period = 1;
+
+    // device scratch
+    int *d_err = nullptr;         // error word: bit 0 overflow, bit 1 capacity
+    double *d_red = nullptr;      // reduction scratch
+    int red_cap = 0;
+
+    // profiling
+    bool profile = false;
+    double kms[qpic::KC_COUNT] = {0};
+    long long klaunch[qpic::KC_COUNT] = {0};
+    long long n_kernels = 0;                   // kernels launched by this context
+    std::vector<cudaEvent_t> ev_pool;          // recorded pairs, resolved on demand
+    std::vector<int> ev_class;
+    size_t ev_used = 0;
+
+    // allocations made through the allocator hooks
+    std::vector<void *> allocs;
+};
+
+namespace qpic {
+
+// ---- host numerics (host_numerics.cpp) ----
+int fit_coefficients(int solver, double dt, double dz, int L, double band, double *cE, double *cB,
+                     std::string &err);
+double symbol(const double *C, int L, double theta);       // [k] dz of an operator
+int filter_taps_host(const double *cB, int L, double tol, std::vector<double> &taps,
+                     std::string &err);
+double radial_lambda_max(int nr, double dr, int m);
+int cfl_limit(int solver, double dz, double dr, int nr, int n_modes, int L, double band,
+              double *dt_out, std::string &err);
+
+// ---- kernel launchers (k_fields.cu) ----
+void set_solver_constants(qpic_ctx *c);
+void launch_faraday(qpic_ctx *c);
+void launch_jdecode(qpic_ctx *c);
+void launch_jfilter(qpic_ctx *c);
+void launch_ampere(qpic_ctx *c);
+void launch_zero_column(qpic_ctx *c, long long phys_col);
+void launch_laser(qpic_ctx *c, double a0, double w0, double fwhm, double zc, double zf,
+                  double psi);
+void launch_field_energy(qpic_ctx *c, double *out_modes);   // host out[n_modes]
+
+// ---- kernel launchers (k_particles.cu) ----
+void launch_gpd(qpic_ctx *c);
+void launch_sort(qpic_ctx *c);
+int launch_load_plasma(qpic_ctx *c, long long first_logical_col, int ncols, bool append);
+void launch_load_particles(qpic_ctx *c, long long n, const double *dz_, const double *dr_,
+                           const double *dphi, const double *dux, const double *duy,
+                           const double *duz, const double *dw);
+void launch_export_particles(qpic_ctx *c, double *dout, long long stride);
+void launch_rho(qpic_ctx *c, double *dplanes);               // nm*2 planes (nr+1)*nz logical
+void launch_particle_sums(qpic_ctx *c, double *out3);        // count, charge, kinetic
+
+// ---- plain FP64 path (k_fp64.cu) ----
+void fp64_faraday(qpic_ctx *c);
+void fp64_push_deposit(qpic_ctx *c);
+void fp64_ampere(qpic_ctx *c);
+void fp64_zero_column(qpic_ctx *c, long long phys_col);
+void fp64_laser(qpic_ctx *c, double a0, double w0, double fwhm, double zc, double zf, double psi);
+int fp64_load_plasma(qpic_ctx *c, long long first_logical_col, int ncols, bool append);
+void fp64_load_particles(qpic_ctx *c, long long n, const double *dz_, const double *dr_,
+                         const double *dphi, const double *dux, const double *duy,
+                         const double *duz, const double *dw);
+void fp64_export_particles(qpic_ctx *c, double *dout, long long stride);
+void fp64_compact(qpic_ctx *c);
+void fp64_rho(qpic_ctx *c, double *dplanes);
+void fp64_particle_sums(qpic_ctx *c, double *out3);
+void fp64_field_energy(qpic_ctx *c, double *out_modes);
+
+// profiling helpers (api.cu)
+void prof_begin(qpic_ctx *c);
+void prof_end(qpic_ctx *c, int kclass, int nkernels = 1);
+
+}  // namespace qpic
+
+#define QPIC_CUDA_OK(c, call)                                                          \
+    do {                                                                               \
+        cudaError_t _e = (call);                                                       \
+        if (_e != cudaSuccess) {                                                       \
+            (c)->err = std::string(#call) + ": " + cudaGetErrorString(_e);            \
+            return QPIC_ECUDA;                                                         \
+        }                                                                              \
+    } while (0)

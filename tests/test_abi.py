@@ -1,0 +1,68 @@
+"""The C ABI: the library builds for sm_103a, loads, exports every function
+declared in include/qpic.h, and its host-only numerics (coefficient fit,
+filter taps, stability limit) agree with the oracle's independent ones.
+No GPU is needed; a context refuses to start without one (no CPU fallback)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2303_12874_gb300 as q
+from oracle import coeffs as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "qpic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qpic_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = q.load()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("nu", [0.4, 0.7, 0.85])
+def test_host_fit_matches_oracle(nu):
+    dz = 0.2
+    cE, cB = q.fit_coefficients("dual", nu * dz, dz)
+    oE, oB = C.dual_coefficients(nu * dz, dz)
+    assert np.max(np.abs(cE - oE)) < 1e-11
+    assert np.max(np.abs(cB - oB)) < 1e-11
+    yE, yB = q.fit_coefficients("yee", nu * dz, dz)
+    assert list(yE) == [1.0] and list(yB) == [1.0]
+
+
+def test_host_filter_taps_match_oracle():
+    _, cB = C.dual_coefficients(0.14, 0.2)
+    k_lib = q.filter_taps(cB)
+    k_or = C.filter_taps(cB)
+    n = min(len(k_lib), len(k_or))
+    assert abs(len(k_lib) - len(k_or)) <= 1        # the 1e-16 cut may fall either side
+    assert np.max(np.abs(k_lib[:n] - k_or[:n])) < 1e-13
+    assert q.filter_taps(np.array([1.0])) is None
+
+
+@pytest.mark.parametrize("solver", ["dual", "yee"])
+def test_host_stability_limit_matches_oracle(solver):
+    lib = q.stability_limit(solver, 0.2, 0.5, 32, 2)
+    ora = C.cfl_dt(0.2, 0.5, 32, 2, solver)
+    assert abs(lib / ora - 1) < 1e-8
+
+
+def test_context_needs_a_gpu():
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present")
+    with pytest.raises(q.QpicError):
+        q.Sim(64, 8, 0.2, 0.5)

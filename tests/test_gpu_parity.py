@@ -1,0 +1,169 @@
+"""CUDA path vs the FP64 oracle, stage by stage and step by step, from
+identical states (tests/pairs.py).  Tolerance: relative L2 <= 1e-5 per field,
+component and mode for one step (the FP32 + int64 fixed-point target), particle
+coordinates to FP32 precision.  Sizes span several 16 x 8 particle tiles and a
+ragged tail (nz, nr not multiples of the tile)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import setup
+from pairs import (COMPS, angle_diff, compare_fields, load_same_particles, make_pair,
+                   rel_l2, set_random_fields, sync_fields)
+
+pytestmark = pytest.mark.gpu
+
+DZ, DR = 0.2, 0.5
+TOL = 1e-5
+
+
+def _random_particles(n, nz, nr, seed, umax=1.0):
+    return synth.random_particles(seed, n, nz, nr, DZ, DR, umax=umax)
+
+
+def test_faraday_stage():
+    sim, o = make_pair(100, 21, DZ, DR, 0.13)
+    set_random_fields(sim, 1)
+    sync_fields(sim, o)
+    sim.run_stages(1)
+    o.faraday()
+    compare_fields(sim, o, "B", 1e-6)
+    compare_fields(sim, o, "Bbar", 1e-6)
+
+
+@pytest.mark.parametrize("n_modes", [1, 2, 3])
+def test_particle_stage(n_modes):
+    nz, nr = 70, 19
+    sim, o = make_pair(nz, nr, DZ, DR, 0.13, n_modes=n_modes)
+    set_random_fields(sim, 2, amp=0.5)
+    sync_fields(sim, o)
+    p0, live = load_same_particles(sim, o, _random_particles(20000, nz, nr, 3))
+    sim.run_stages(2)                    # gather + push + deposit (+ decode)
+    o.push_deposit()
+    compare_fields(sim, o, "J", TOL)
+    g = sim.particles_raw()
+    r = o.particles()
+    gl = {k: v[live] for k, v in g.items()}
+    Lz = nz * DZ
+    dzz = np.abs((gl["z"] - r["z"] + 0.5 * Lz) % Lz - 0.5 * Lz)
+    assert np.max(dzz) < 2e-5 * DZ * 50
+    assert np.max(np.abs(gl["r"] - r["r"])) < 1e-5
+    m = r["r"] > 0.05
+    assert np.max(np.abs(angle_diff(gl["phi"][m], r["phi"][m]))) < 1e-4
+    for k in ("ux", "uy", "uz"):
+        assert np.max(np.abs(gl[k] - r[k])) < 1e-5 * (1 + np.abs(r[k]).max())
+
+
+def test_ampere_stage():
+    nz, nr = 70, 19
+    sim, o = make_pair(nz, nr, DZ, DR, 0.13)
+    set_random_fields(sim, 4, amp=0.5)
+    sync_fields(sim, o)
+    load_same_particles(sim, o, _random_particles(20000, nz, nr, 5))
+    sim.run_stages(2 | 4)
+    o.push_deposit()
+    o.ampere()
+    compare_fields(sim, o, "J", TOL)
+    compare_fields(sim, o, "E", TOL)
+
+
+def _config1_state(sim, o, nsteps_warm=0):
+    w = synth.workload("cfg1_small")
+    pl, la = w["plasma"], w["laser"]
+    sim.load_plasma(pl["n0"], pl["z_start"], pl["ramp_len"], pl["ppc"])
+    sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
+    return w
+
+
+def test_load_plasma_matches_oracle():
+    w = synth.workload("cfg1_small")
+    nz, nr = w["nz"], w["nr"]
+    sim, o = make_pair(nz, nr, w["dz"], w["dr"], 0.13)
+    pl = w["plasma"]
+    sim.load_plasma(pl["n0"], pl["z_start"], pl["ramp_len"], pl["ppc"])
+    g = sim.particles()
+    r = setup.plasma_cells(np.arange(nz), nr, w["dz"], w["dr"], pl["n0"], pl["z_start"],
+                           pl["ramp_len"], pl["ppc"], pl["seed"])
+    assert len(g["z"]) == len(r["z"]) == nz * nr * 8
+    kg = np.lexsort((np.round(np.mod(g["phi"], 2 * np.pi), 5), np.round(g["r"], 6), np.round(g["z"], 6)))
+    kr = np.lexsort((np.round(np.mod(r["phi"], 2 * np.pi), 5), np.round(r["r"], 6), np.round(r["z"], 6)))
+    assert np.max(np.abs(g["z"][kg] - r["z"][kr])) < 1e-5
+    assert np.max(np.abs(g["r"][kg] - r["r"][kr])) < 1e-5
+    assert np.max(np.abs(angle_diff(g["phi"][kg], r["phi"][kr]))) < 1e-6
+    assert np.max(np.abs(g["w"][kg] / r["w"][kr] - 1)) < 1e-6
+
+
+def test_laser_matches_oracle():
+    w = synth.workload("cfg1_small")
+    sim, o = make_pair(w["nz"], w["nr"], w["dz"], w["dr"], 0.13)
+    la = w["laser"]
+    sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"], 0.3)
+    setup.add_laser(o, o_cE(o), o_cB(o), la["a0"], la["w0"], la["fwhm"], la["z_centroid"],
+                    la["z_focus"], 0.3)
+    compare_fields(sim, o, "E", 1e-6, modes=[1])
+    compare_fields(sim, o, "B", 1e-6, modes=[1])
+
+
+def o_cE(o):
+    from oracle import coeffs as C
+    return C.dual_coefficients(o.dt, o.dz)[0]
+
+
+def o_cB(o):
+    from oracle import coeffs as C
+    return C.dual_coefficients(o.dt, o.dz)[1]
+
+
+@pytest.mark.parametrize("solver", ["dual", "yee"])
+def test_full_step_config1(solver):
+    w = synth.workload("cfg1_small")
+    nz, nr = w["nz"], w["nr"]
+    from oracle import coeffs as C
+    dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], nr, 2, solver)
+    sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, solver=solver)
+    _config1_state(sim, o)
+    # a few GPU steps to build up currents and plasma motion, then inject that state
+    sim.step(3)
+    sync_fields(sim, o, ("E", "B"))
+    p = sim.particles_raw()
+    live = p["w"] > 0
+    o.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
+    sim.step(1)
+    o.step(1)
+    for which in ("E", "B", "J"):
+        compare_fields(sim, o, which, TOL)
+
+
+def test_bit_reproducible():
+    """int64 deposit: fields and the particle set are bit-identical run to run.
+    The particle buffer order (atomic counting sort) may differ, so particles
+    are compared as sorted sets, and FP64 sums over particles to round-off."""
+    w = synth.workload("cfg1_small")
+    out = []
+    for _ in range(2):
+        sim, _o = make_pair(w["nz"], w["nr"], w["dz"], w["dr"], 0.13)
+        _config1_state(sim, _o)
+        sim.step(5)
+        p = sim.particles()
+        key = np.lexsort((p["uz"], p["phi"], p["r"], p["z"]))
+        out.append((sim.fields("E"), sim.fields("B"), sim.fields("J"),
+                    np.array([p[k][key] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")]),
+                    sim.diag()["kinetic"]))
+    for a, b in zip(out[0][:4], out[1][:4]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    assert abs(out[0][4] - out[1][4]) <= 1e-13 * abs(out[0][4])
+
+
+def test_multi_step_config1_tracks_oracle():
+    w = synth.workload("cfg1_small")
+    nz, nr = w["nz"], w["nr"]
+    sim, o = make_pair(nz, nr, w["dz"], w["dr"], 0.13)
+    _config1_state(sim, o)
+    sync_fields(sim, o, ("E", "B"))
+    p = sim.particles_raw()
+    live = p["w"] > 0
+    o.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
+    sim.step(20)
+    o.step(20)
+    compare_fields(sim, o, "E", 1e-4)
+    compare_fields(sim, o, "B", 1e-4)
