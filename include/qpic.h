@@ -80,7 +80,8 @@ typedef struct {
     int32_t moving_window; /* 1: window moves at window_v (needs periodic_z = 0) */
     double window_v;
     int32_t tile_z, tile_r;   /* particle tile in cells (0: default 16 x 8) */
-    int32_t sort_period;      /* steps between particle sorts (0: default 1) */
+    int32_t sort_period;      /* steps between particle sorts (0: default 2; a particle moves
+                                 < 1 cell per step, so 2 keeps every one inside its tile halo) */
     int32_t track_work;       /* 1: accumulate modal work W0, W1 per particle (Eq. 16) */
     uint64_t seed;            /* plasma azimuthal jitter seed */
     int64_t max_particles;    /* capacity (0: sized at the first load, +25%) */
@@ -92,7 +93,8 @@ typedef struct {
 } qpic_config;
 
 /* Fill *cfg with defaults (M = 1, dual solver, L = 16, band 0.8, cfl 0.9,
- * FP32 + int64 fixed point, filter on, tol 1e-16, periodic, 16 x 8 tiles). */
+ * FP32 + int64 fixed point, filter on, tol 1e-16, periodic, 16 x 8 tiles, sort
+ * every 2 steps). */
 qpic_status qpic_default_config(qpic_config *cfg);
 
 /* Create a context: fit the z-operator coefficients on the host in FP64

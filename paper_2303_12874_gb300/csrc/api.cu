@@ -112,9 +112,10 @@ float *field_base(qpic_ctx *c, int which)
 void set_qscale(qpic_ctx *c, double qmax)
 {
     c->qref = qmax > 0 ? qmax : 1.0;
-    // per-particle contributions stay below ~2 qref: 2^45 of 2^63 leaves 2^17
-    // particles' worth of headroom per accumulator
-    c->qscale = (float)(17592186044416.0 / c->qref);       // 2^44 / qref
+    // per-particle contributions stay below ~2 qref, i.e. 2^41 units: the
+    // exact FP32 split of the deposit handles up to 2^42, and int64 keeps
+    // 2^21 particles' worth of headroom per accumulator
+    c->qscale = (float)(1099511627776.0 / c->qref);        // 2^40 / qref
 }
 
 void do_shift(qpic_ctx *c)
@@ -243,7 +244,7 @@ qpic_status qpic_default_config(qpic_config *cfg)
     cfg->window_v = 1.0;
     cfg->tile_z = 16;
     cfg->tile_r = 8;
-    cfg->sort_period = 1;
+    cfg->sort_period = 2;
     cfg->seed = 1;
     return QPIC_OK;
 }
@@ -306,7 +307,7 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->TZ = cfg->tile_z > 0 ? cfg->tile_z : 16;
     c->TR = cfg->tile_r > 0 ? cfg->tile_r : 8;
     c->halo = 1;
-    c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 1;
+    c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 2;
     FieldGeom &g = c->g;
     g.nz = cfg->nz; g.nr = cfg->nr; g.nm = cfg->n_modes; g.nparts = 2 * cfg->n_modes - 1;
     g.periodic = cfg->periodic_z ? 1 : 0;

@@ -48,16 +48,17 @@ static GridArgs grid_args(const qpic_ctx *c)
     return a;
 }
 
-__device__ __forceinline__ int wrapz(long long i, int nzp)
+__device__ __forceinline__ int wrapz(int i, int nzp)
 {
-    long long r = i % nzp;
-    return (int)(r < 0 ? r + nzp : r);
+    int r = i % nzp;
+    return r < 0 ? r + nzp : r;
 }
 
 // true when the physical column lies in the gap of an open box
 __device__ __forceinline__ bool in_gap(int col, const GridArgs &a)
 {
-    int l = wrapz((long long)col - a.zoff, a.nzp);
+    int l = col - (int)a.zoff;          // col, zoff in [0, nzp)
+    l = l < 0 ? l + a.nzp : l;
     return l >= a.nz;
 }
 
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const float *__restrict__ E, 
     float *sEr = sEphi + P * W;      // [P][W]
     for (int k = threadIdx.x; k < a.L; k += FTILE) sC[k] = a.coef[k];
     for (int k = threadIdx.x; k < W; k += FTILE) {
-        int col = wrapz((long long)i0 - a.L + k, a.nzp);
+        int col = wrapz(i0 - a.L + k, a.nzp);
         for (int p = 0; p < P; p++) {
             sEphi[p * W + k] = E[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
             sEr[p * W + k] = E[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
@@ -190,7 +191,9 @@ __global__ void k_jdecode(unsigned long long *__restrict__ Jacc, float *__restri
     if (comp == 2) f = rowf[j];                                   // J_z
     else if (comp == 0) f = rowf[(a.nr + 1) + j];                  // J_r
     else f = part == 0 ? rowf[3 * (a.nr + 1) + j] : rowf[2 * (a.nr + 1) + j];  // J_phi
-    Jf[q] = in_gap(i, a) ? 0.f : __ll2float_rn(v) * inv_qscale * f;
+    // int64 -> float from two 32-bit halves (integer conversions stay off the FP64 pipe)
+    const float fv = __int2float_rn((int)(v >> 32)) * 4294967296.f + __uint2float_rn((unsigned)v);
+    Jf[q] = in_gap(i, a) ? 0.f : fv * inv_qscale * f;
 }
 
 void launch_jdecode(qpic_ctx *c)
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(JTILE) k_jfilter(const float *__restrict__ Jf,
     float *sT = sh2, *sh = sh2 + MAX_TAPS;
     for (int k = threadIdx.x; k < nk; k += JTILE) sT[k] = a.coef[2 * MAX_L + k];
     const float *src = Jf + (size_t)(2 * a.nparts + p) * a.plane + (size_t)j * a.nzp;
-    for (int k = threadIdx.x; k < W; k += JTILE) sh[k] = src[wrapz((long long)i0 - H + k, a.nzp)];
+    for (int k = threadIdx.x; k < W; k += JTILE) sh[k] = src[wrapz(i0 - H + k, a.nzp)];
     __syncthreads();
     const int i = i0 + threadIdx.x;
     if (i >= a.nzp) return;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(FTILE) k_ampere(float *__restrict__ E, const f
     float *sBphi = sh + MAX_L, *sBr = sBphi + P * W;
     for (int k = threadIdx.x; k < a.L; k += FTILE) sC[k] = a.coef[MAX_L + k];
     for (int k = threadIdx.x; k < W; k += FTILE) {
-        int col = wrapz((long long)i0 - a.L + k, a.nzp);
+        int col = wrapz(i0 - a.L + k, a.nzp);
         for (int p = 0; p < P; p++) {
             sBphi[p * W + k] = B[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
             sBr[p * W + k] = B[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
@@ -420,7 +423,7 @@ __global__ void k_laser(float *E, float *B, GridArgs a, LaserArgs L)
     const int il = blockIdx.x * blockDim.x + threadIdx.x;     // logical column
     const int j = blockIdx.y;
     if (il >= a.nz) return;
-    const int col = wrapz((long long)il + a.zoff, a.nzp);
+    const int col = wrapz(il + (int)a.zoff, a.nzp);
     const size_t base = (size_t)j * a.nzp + col;
     const int P = a.nparts;
     const double cp = cos(L.psi), sp = -sin(L.psi);           // e^{-i psi}
@@ -483,7 +486,7 @@ __global__ void k_energy_partial(const float *E, const float *B, GridArgs a, dou
     Vh = (j < a.nr) ? 2.0 * PI * (j + 0.5) * dr * dr * dz : 0.0;
     double s = 0.0;
     for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < a.nz; il += gridDim.x * blockDim.x) {
-        int col = wrapz((long long)il + a.zoff, a.nzp);
+        int col = wrapz(il + (int)a.zoff, a.nzp);
         size_t base = (size_t)j * a.nzp + col;
         for (int k = 0; k < (m ? 2 : 1); k++) {
             int p = m ? 2 * m - 1 + k : 0;

@@ -55,10 +55,10 @@ static PArgs pargs(const qpic_ctx *c)
     return a;
 }
 
-__device__ __forceinline__ int pwrap(long long i, int n)
+__device__ __forceinline__ int pwrap(int i, int n)
 {
-    long long r = i % n;
-    return (int)(r < 0 ? r + n : r);
+    int r = i % n;
+    return r < 0 ? r + n : r;
 }
 
 // staggering: E_r (0,1) E_phi (0,0) E_z (1,0); B_r (1,0) B_phi (1,1) B_z (0,1)
@@ -70,7 +70,7 @@ __host__ __device__ __forceinline__ int hr_of(int fb, int c) { return fb == 0 ? 
 // below the axis with the mode parity (radial/azimuthal (-1)^(m+1), B_z (-1)^m)
 // and beyond the wall with their even image; integer-r components are 0 outside.
 __device__ __forceinline__ float gsample(const float *E, const float *Bb, const PArgs &a, int fb,
-                                         int c, int p, int j, long long col)
+                                         int c, int p, int j, int col)
 {
     const float *F = fb == 0 ? E : Bb;
     float sgn = 1.f;
@@ -123,7 +123,33 @@ struct GlobAcc {
     }
 };
 
-__device__ __forceinline__ long long fx(float x, float qs) { return __float2ll_rn(x * qs); }
+// Exact round-to-nearest of a scaled contribution |v| < 2^42 into hi*2^20 + lo
+// (|lo| <= 2^19) using only FP32 adds: t + 1.5*2^23 has unit spacing, so its
+// bit pattern minus that of 1.5*2^23 is round(t).  (A float->int64 conversion
+// would run on the FP64 pipe, which is narrow on this part.)
+__device__ __forceinline__ void fx_split(float v, int &hi, int &lo)
+{
+    const float M = 12582912.0f;                       // 1.5 * 2^23
+    const float t = __fmul_rn(v, 9.5367431640625e-07f); // v * 2^-20 (exact)
+    const float tm = __fadd_rn(t, M);
+    hi = __float_as_int(tm) - 0x4B400000;
+    const float hf = __fsub_rn(tm, M);                  // round(t), exact
+    const float r = __fmaf_rn(-hf, 1048576.0f, v);      // v - hi * 2^20, exact
+    lo = __float_as_int(__fadd_rn(r, M)) - 0x4B400000;
+}
+
+__device__ __forceinline__ long long fx(float x, float qs)
+{
+    int hi, lo;
+    fx_split(x * qs, hi, lo);
+    return ((long long)hi << 20) + lo;
+}
+
+__device__ __forceinline__ int wrapn(int i, int n)      // for i in [-n, 2n)
+{
+    i = i < 0 ? i + n : i;
+    return i >= n ? i - n : i;
+}
 
 // Linear-shape values S0 and differences dS = S1 - S0 at nodes k = -1..2 (index
 // k+1) for a move x0 -> x0 + d in old-cell coordinates (x0 in [0,1), |d| < 1).
@@ -151,12 +177,20 @@ struct PState {
     int diz, djr;    // cell change of the move
 };
 
-// One particle: gather, push, move, deposit.  (bi, bj): accessor coordinates of
-// its cell.  On return the offsets, angle and momentum are the new ones and
-// (diz, djr) the cell change.
+// what the deposit needs from the move: old offsets, displacement in cells,
+// charge, e^{-i m phi} at the start and its change, and the m = 0 azimuthal
+// displacement (x0 dy - y0 dx)/(r_mid dr)
+template <int NM>
+struct DepIn {
+    float oz0, or0, dzc, drc, Q, aphi;
+    float e0r[NM], e0i[NM], der[NM], dei[NM];
+};
+
+// Gather, push and move one particle.  (bi, bj): accessor coordinates of its
+// cell.  On return s holds the new state and d the deposit inputs.
 template <int NP, class Acc>
-__device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, int bi, int bj,
-                                              PState &s)
+__device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi, int bj, PState &s,
+                                          DepIn<(NP + 1) / 2> &d)
 {
     constexpr int NM = (NP + 1) / 2;
     const float oz = s.oz, orr = s.orr, cph = s.cph, sph = s.sph;
@@ -204,10 +238,9 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
     // ---- relativistic Boris push, q = -1
     const float h = -0.5f * a.dt;
     const float ux = s.ux, uy = s.uy, uz = s.uz;
-    const float g_old = sqrtf(1.f + ux * ux + uy * uy + uz * uz);
     float umx = ux + h * Ex, umy = uy + h * Ey, umz = uz + h * Ez;
-    float gm = sqrtf(1.f + umx * umx + umy * umy + umz * umz);
-    float tx = h * Bx / gm, ty = h * By / gm, tz = h * Bz / gm;
+    float igm = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
+    float tx = h * Bx * igm, ty = h * By * igm, tz = h * Bz * igm;
     float t2 = tx * tx + ty * ty + tz * tz;
     float f2 = 2.f / (1.f + t2);
     float sx = f2 * tx, sy = f2 * ty, sz = f2 * tz;
@@ -217,12 +250,12 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
     float unx = umx + (upy * sz - upz * sy) + h * Ex;
     float uny = umy + (upz * sx - upx * sz) + h * Ey;
     float unz = umz + (upx * sy - upy * sx) + h * Ez;
-    const float g = sqrtf(1.f + unx * unx + uny * uny + unz * unz);
-    const float vx = unx / g, vy = uny / g, vz = unz / g;
+    const float ig = rsqrtf(1.f + unx * unx + uny * uny + unz * unz);
+    const float vx = unx * ig, vy = uny * ig, vz = unz * ig;
     if (a.track_work) {
         // Eq. 16: W_m += q dt E^m . v, v at time n the mean of u/gamma at n -+ 1/2
-        float wx = 0.5f * (ux / g_old + vx), wy = 0.5f * (uy / g_old + vy),
-              wz = 0.5f * (uz / g_old + vz);
+        const float igo = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
+        float wx = 0.5f * (ux * igo + vx), wy = 0.5f * (uy * igo + vy), wz = 0.5f * (uz * igo + vz);
         float E0x = F[0][0][0] * cph - F[0][1][0] * sph, E0y = F[0][0][0] * sph + F[0][1][0] * cph;
         float p0 = E0x * wx + E0y * wy + F[0][2][0] * wz;
         float pt = Ex * wx + Ey * wy + Ez * wz;
@@ -257,28 +290,59 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
         drr = r1 - r0; c1 = cr; s1 = sr; dc = c1 - cph; ds = s1 - sph;
     }
     const float dzc = ddz * a.inv_dz, drc = drr * a.inv_dr;
-    // ---- deposit
-    float S0z[4], dSz[4], S0r[4], dSr[4];
-    int zlo, zhi, rlo, rhi;
-    shape_delta(oz, dzc, S0z, dSz, zlo, zhi);
-    shape_delta(orr, drc, S0r, dSr, rlo, rhi);
-    const float Q = -s.w, qs = a.qscale;
-    // e^{-i m phi} at the start and its change over the move, m = 1..NM-1
-    float e0r[NM], e0i[NM], der[NM], dei[NM];
-    e0r[0] = 1.f; e0i[0] = 0.f; der[0] = 0.f; dei[0] = 0.f;
+    // ---- deposit inputs
+    d.oz0 = oz; d.or0 = orr; d.dzc = dzc; d.drc = drc; d.Q = -s.w;
+    d.e0r[0] = 1.f; d.e0i[0] = 0.f; d.der[0] = 0.f; d.dei[0] = 0.f;
     if (NM > 1) {
         const float a0r = cph, a0i = -sph, adr = dc, adi = -ds;     // e0_1, de_1
         const float a1r = a0r + adr, a1i = a0i + adi;                // e1_1
+        d.e0r[1] = a0r; d.e0i[1] = a0i; d.der[1] = adr; d.dei[1] = adi;
 #pragma unroll
-        for (int m = 1; m < NM; m++) {
-            if (m == 1) { e0r[1] = a0r; e0i[1] = a0i; der[1] = adr; dei[1] = adi; continue; }
+        for (int m = 2; m < NM; m++) {
             // e0_m = e0_{m-1} e0_1 ; de_m = de_{m-1} e1_1 + e0_{m-1} de_1
-            e0r[m] = e0r[m - 1] * a0r - e0i[m - 1] * a0i;
-            e0i[m] = e0r[m - 1] * a0i + e0i[m - 1] * a0r;
-            der[m] = der[m - 1] * a1r - dei[m - 1] * a1i + e0r[m - 1] * adr - e0i[m - 1] * adi;
-            dei[m] = der[m - 1] * a1i + dei[m - 1] * a1r + e0r[m - 1] * adi + e0i[m - 1] * adr;
+            d.e0r[m] = d.e0r[m - 1] * a0r - d.e0i[m - 1] * a0i;
+            d.e0i[m] = d.e0r[m - 1] * a0i + d.e0i[m - 1] * a0r;
+            d.der[m] = d.der[m - 1] * a1r - d.dei[m - 1] * a1i + d.e0r[m - 1] * adr - d.e0i[m - 1] * adi;
+            d.dei[m] = d.der[m - 1] * a1i + d.dei[m - 1] * a1r + d.e0r[m - 1] * adi + d.e0i[m - 1] * adr;
         }
     }
+    const float xm = x0 + 0.5f * ddx, ym = y0 + 0.5f * ddy;
+    const float rm = sqrtf(xm * xm + ym * ym);
+    d.aphi = rm > 0.f ? (x0 * ddy - y0 * ddx) / (rm * a.dr) : 0.f;
+    // ---- new state: offsets renormalised into the cell
+    float nz_ = oz + dzc, nr_ = orr + drc;
+    int diz = 0, djr = 0;
+    if (nz_ >= 1.f) { nz_ -= 1.f; diz = 1; } else if (nz_ < 0.f) { nz_ += 1.f; diz = -1; }
+    if (nz_ >= 1.f) nz_ = 0.99999994f;          // rounding guard
+    if (nr_ >= 1.f) { nr_ -= 1.f; djr = 1; } else if (nr_ < 0.f) { nr_ += 1.f; djr = -1; }
+    if (nr_ >= 1.f) nr_ = 0.99999994f;
+    if (s.jr + djr >= a.nr) { djr = a.nr - 1 - s.jr; nr_ = 0.99999994f; }   // r = R exactly
+    if (s.jr + djr < 0) { djr = -s.jr; nr_ = 0.f; }
+    s.oz = nz_; s.orr = nr_; s.cph = c1; s.sph = s1;
+    s.ux = unx; s.uy = uny; s.uz = unz;
+    s.diz = diz; s.djr = djr;
+}
+
+// True when the move stays inside its cell in z and r (the common case).
+template <int NM>
+__device__ __forceinline__ bool same_cell(const DepIn<NM> &d)
+{
+    const float xz = d.oz0 + d.dzc, xr = d.or0 + d.drc;
+    return xz >= 0.f && xz < 1.f && xr >= 0.f && xr < 1.f;
+}
+
+// Charge-conserving deposit of one move, any cell crossing (2D Esirkepov fluxes
+// times (e0+e1)/2 per mode, J_phi from the phase change), direct atomics.
+template <int NP, class Acc>
+__device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, int bi, int bj,
+                                                const DepIn<(NP + 1) / 2> &d)
+{
+    constexpr int NM = (NP + 1) / 2;
+    float S0z[4], dSz[4], S0r[4], dSr[4];
+    int zlo, zhi, rlo, rhi;
+    shape_delta(d.oz0, d.dzc, S0z, dSz, zlo, zhi);
+    shape_delta(d.or0, d.drc, S0r, dSr, rlo, rhi);
+    const float Q = d.Q, qs = a.qscale;
     // z fluxes through faces (i0+k+1/2, j0+kr): prefix sums of W^z along z
 #pragma unroll
     for (int b = 0; b < 4; b++) {
@@ -294,7 +358,7 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
             acc.jadd(2, 0, lj, li, fx(X, qs));
 #pragma unroll
             for (int m = 1; m < NM; m++) {
-                float ebr = e0r[m] + 0.5f * der[m], ebi = e0i[m] + 0.5f * dei[m];
+                float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
                 acc.jadd(2, 2 * m - 1, lj, li, fx(X * ebr, qs));
                 acc.jadd(2, 2 * m, lj, li, fx(X * ebi, qs));
             }
@@ -315,7 +379,7 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
             acc.jadd(0, 0, lj, li, fx(X, qs));
 #pragma unroll
             for (int m = 1; m < NM; m++) {
-                float ebr = e0r[m] + 0.5f * der[m], ebi = e0i[m] + 0.5f * dei[m];
+                float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
                 acc.jadd(0, 2 * m - 1, lj, li, fx(X * ebr, qs));
                 acc.jadd(0, 2 * m, lj, li, fx(X * ebi, qs));
             }
@@ -323,9 +387,6 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
     }
     // azimuthal current at nodes: m = 0 from the mid-point azimuthal displacement,
     // m >= 1 from i Q Sbar (e1 - e0) / m
-    const float xm = x0 + 0.5f * ddx, ym = y0 + 0.5f * ddy;
-    const float rm = sqrtf(xm * xm + ym * ym);
-    const float aphi = rm > 0.f ? (x0 * ddy - y0 * ddx) / (rm * a.dr) : 0.f;
 #pragma unroll
     for (int a2 = 0; a2 < 4; a2++) {
         if (a2 < zlo || a2 > zhi) continue;
@@ -336,44 +397,93 @@ __device__ __forceinline__ void push_particle(const Acc &acc, const PArgs &a, in
                              0.5f * (S0z[a2] * dSr[b] + dSz[a2] * S0r[b] + dSz[a2] * dSr[b]);
             const int lj = bj + b - 1, li = bi + a2 - 1;
             const float QS = Q * sb;
-            acc.jadd(1, 0, lj, li, fx(QS * aphi, qs));
+            acc.jadd(1, 0, lj, li, fx(QS * d.aphi, qs));
 #pragma unroll
             for (int m = 1; m < NM; m++) {
                 const float im = 1.f / (float)m;
-                acc.jadd(1, 2 * m - 1, lj, li, fx(-QS * dei[m] * im, qs));
-                acc.jadd(1, 2 * m, lj, li, fx(QS * der[m] * im, qs));
+                acc.jadd(1, 2 * m - 1, lj, li, fx(-QS * d.dei[m] * im, qs));
+                acc.jadd(1, 2 * m, lj, li, fx(QS * d.der[m] * im, qs));
             }
         }
     }
-    // ---- new state: offsets renormalised into the cell
-    float nz_ = oz + dzc, nr_ = orr + drc;
-    int diz = 0, djr = 0;
-    if (nz_ >= 1.f) { nz_ -= 1.f; diz = 1; } else if (nz_ < 0.f) { nz_ += 1.f; diz = -1; }
-    if (nz_ >= 1.f) nz_ = 0.99999994f;          // rounding guard
-    if (nr_ >= 1.f) { nr_ -= 1.f; djr = 1; } else if (nr_ < 0.f) { nr_ += 1.f; djr = -1; }
-    if (nr_ >= 1.f) nr_ = 0.99999994f;
-    if (s.jr + djr >= a.nr) { djr = a.nr - 1 - s.jr; nr_ = 0.99999994f; }   // r = R exactly
-    if (s.jr + djr < 0) { djr = -s.jr; nr_ = 0.f; }
-    s.oz = nz_; s.orr = nr_; s.cph = c1; s.sph = s1;
-    s.ux = unx; s.uy = uny; s.uz = unz;
-    s.diz = diz; s.djr = djr;
+}
+
+// Same-cell deposit with a warp-level reduction: the lanes of `grp` hold moves
+// inside the same cell, so their 8*NP contributions (J_z at 2 faces, J_r at 2
+// faces, J_phi at 4 nodes, each per part) go to the same addresses.  Each
+// contribution is split exactly into hi*2^20 + lo, both halves are summed over
+// the group with one 32-bit reduction each (exact: |sum| < 2^31), and the
+// group's leader adds the int64 total to shared memory.
+template <int NP>
+__device__ __forceinline__ void deposit_fast(const SmemAcc &acc, const PArgs &a, int li, int lj,
+                                             const DepIn<(NP + 1) / 2> &d, unsigned grp, bool leader)
+{
+    constexpr int NM = (NP + 1) / 2;
+    const float qs = a.qscale;
+    const float Qd = d.Q * qs;
+    const float dz_ = d.dzc, dr_ = d.drc;
+    const float Sz[2] = {(1.f - d.oz0) - 0.5f * dz_, d.oz0 + 0.5f * dz_};
+    const float Sr[2] = {(1.f - d.or0) - 0.5f * dr_, d.or0 + 0.5f * dr_};
+    const float c4 = 0.25f * dz_ * dr_;
+    float ebr[NM], ebi[NM];
+#pragma unroll
+    for (int m = 0; m < NM; m++) { ebr[m] = d.e0r[m] + 0.5f * d.der[m]; ebi[m] = d.e0i[m] + 0.5f * d.dei[m]; }
+    auto put = [&](int comp, int p, int dj, int di, float v) {
+        int hi, lo;
+        fx_split(v, hi, lo);
+        const int shi = (int)__reduce_add_sync(grp, (unsigned)hi);
+        const int slo = (int)__reduce_add_sync(grp, (unsigned)lo);
+        const long long tot = ((long long)shi << 20) + slo;
+        if (leader)
+            atomicAdd(&acc.sJ[((size_t)(comp * NP + p) * acc.JR + lj + dj) * acc.JW + li + di],
+                      (unsigned long long)tot);
+    };
+#pragma unroll
+    for (int b = 0; b < 2; b++) {                      // J_z at (i0+1/2, j0+b)
+        const float X = Qd * dz_ * Sr[b];
+        put(2, 0, b, 0, X);
+#pragma unroll
+        for (int m = 1; m < NM; m++) { put(2, 2 * m - 1, b, 0, X * ebr[m]); put(2, 2 * m, b, 0, X * ebi[m]); }
+    }
+#pragma unroll
+    for (int a2 = 0; a2 < 2; a2++) {                   // J_r at (i0+a, j0+1/2)
+        const float X = Qd * dr_ * Sz[a2];
+        put(0, 0, 0, a2, X);
+#pragma unroll
+        for (int m = 1; m < NM; m++) { put(0, 2 * m - 1, 0, a2, X * ebr[m]); put(0, 2 * m, 0, a2, X * ebi[m]); }
+    }
+#pragma unroll
+    for (int a2 = 0; a2 < 2; a2++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {                  // J_phi at (i0+a, j0+b)
+            const float sb = Sz[a2] * Sr[b] + (a2 == b ? c4 : -c4);
+            const float QS = Qd * sb;
+            put(1, 0, b, a2, QS * d.aphi);
+#pragma unroll
+            for (int m = 1; m < NM; m++) {
+                const float im = 1.f / (float)m;
+                put(1, 2 * m - 1, b, a2, -QS * d.dei[m] * im);
+                put(1, 2 * m, b, a2, QS * d.der[m] * im);
+            }
+        }
 }
 
 // ------------------------------------------------------------ the GPD kernel
 template <int NP>
-__global__ void __launch_bounds__(256) k_gpd(Particles P, const float *__restrict__ E,
+__global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__restrict__ E,
                                             const float *__restrict__ Bb,
                                             unsigned long long *__restrict__ J,
                                             const int32_t *__restrict__ offsets,
                                             const long long *__restrict__ dcount, PArgs a,
                                             int ntiles, int tail_chunk)
 {
+    constexpr int NM = (NP + 1) / 2;
     extern __shared__ unsigned long long sraw[];
     const int H = a.H;
     const int FW = a.TZ + 2 * H + 2, FR = a.TR + 2 * H + 2;
     const int JW = FW + 1, JR = FR + 1;
     long long begin, end;
-    bool tile_mode = blockIdx.x < (unsigned)ntiles;
+    const bool tile_mode = blockIdx.x < (unsigned)ntiles;
     int tz0 = 0, tr0 = 0;
     if (tile_mode) {
         const int t = blockIdx.x;
@@ -390,55 +500,88 @@ __global__ void __launch_bounds__(256) k_gpd(Particles P, const float *__restric
         if (begin >= end) return;
     }
     GlobAcc gacc{E, Bb, J, a};
-    SmemAcc sacc;
-    const long long col0 = (long long)tz0 - H - 1;
+    SmemAcc sacc{nullptr, nullptr, FW, FR, JW, JR, NP};
+    const int col0 = tz0 - H - 1;
     const int row0 = tr0 - H - 1;
-    if (tile_mode) {
+    const bool smem_usable = tile_mode && a.nzp >= 2 * JW;
+    if (smem_usable) {
         unsigned long long *sJ = sraw;
         float *sf = reinterpret_cast<float *>(sraw + (size_t)3 * NP * JW * JR);
         sacc = SmemAcc{sf, sJ, FW, FR, JW, JR, NP};
         const int nJ = 3 * NP * JW * JR;
         for (int k = threadIdx.x; k < nJ; k += blockDim.x) sJ[k] = 0ull;
-        const int nF = 6 * NP * FW * FR;
-        for (int k = threadIdx.x; k < nF; k += blockDim.x) {
-            int li = k % FW, t2 = k / FW, lj = t2 % FR, pl = t2 / FR;
-            int p = pl % NP, cc = (pl / NP) % 3, fb = pl / (3 * NP);
-            sf[k] = gsample(E, Bb, a, fb, cc, p, row0 + lj, col0 + li);
+        // one (plane, row) strip of FW columns per pass of a warp
+        const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, ln = threadIdx.x & 31;
+        for (int strip = warp; strip < 6 * NP * FR; strip += nwarp) {
+            const int lj = strip % FR, pl = strip / FR;
+            const int p = pl % NP, cc = (pl / NP) % 3, fb = pl / (3 * NP);
+            for (int li = ln; li < FW; li += 32) {
+                int col = col0 + li;
+                col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
+                sf[strip * FW + li] = gsample(E, Bb, a, fb, cc, p, row0 + lj, col);
+            }
         }
         __syncthreads();
     }
-    for (long long idx = begin + threadIdx.x; idx < end; idx += blockDim.x) {
-        int cell = P.cell[idx];
-        if (cell < 0) continue;
-        int iz = cell / a.nr, jr = cell - iz * a.nr;
-        if (!a.periodic && pwrap((long long)iz - a.zoff, a.nzp) >= a.nz) {
-            P.cell[idx] = -1;                  // behind the moving window
-            continue;
-        }
-        PState s;
-        s.oz = P.oz[idx]; s.orr = P.orr[idx]; s.cph = P.cph[idx]; s.sph = P.sph[idx];
-        s.ux = P.ux[idx]; s.uy = P.uy[idx]; s.uz = P.uz[idx]; s.w = P.w[idx];
-        s.W0 = a.track_work ? P.W0[idx] : 0.f;
-        s.W1 = a.track_work ? P.W1[idx] : 0.f;
-        s.jr = jr;
-        bool done = false;
-        if (tile_mode) {
-            int li = pwrap((long long)iz - col0, a.nzp), lj = jr - row0;
-            if (li >= 1 && li <= FW - 2 && lj >= 1 && lj <= FR - 2 && a.nzp >= 2 * JW) {
-                push_particle<NP>(sacc, a, li, lj, s);
-                done = true;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int zoff = (int)a.zoff;
+    for (long long base = begin; base < end; base += blockDim.x) {
+        const long long idx = base + threadIdx.x;
+        int cell = idx < end ? P.cell[idx] : -1;
+        bool act = cell >= 0;
+        int iz = 0, jr = 0;
+        if (act) {
+            iz = cell / a.nr;
+            jr = cell - iz * a.nr;
+            if (!a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
+                P.cell[idx] = -1;              // behind the moving window
+                act = false;
             }
         }
-        if (!done) push_particle<NP>(gacc, a, iz, jr, s);
-        int niz = pwrap((long long)iz + s.diz, a.nzp);
-        int njr = jr + s.djr;
-        bool dead = !a.periodic && pwrap((long long)niz - a.zoff, a.nzp) >= a.nz;
-        P.cell[idx] = dead ? -1 : niz * a.nr + njr;
-        P.oz[idx] = s.oz; P.orr[idx] = s.orr; P.cph[idx] = s.cph; P.sph[idx] = s.sph;
-        P.ux[idx] = s.ux; P.uy[idx] = s.uy; P.uz[idx] = s.uz;
-        if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+        PState s;
+        DepIn<NM> d;
+        bool fast = false;
+        int li = 0, lj = 0;
+        if (act) {
+            s.oz = P.oz[idx]; s.orr = P.orr[idx]; s.cph = P.cph[idx]; s.sph = P.sph[idx];
+            s.ux = P.ux[idx]; s.uy = P.uy[idx]; s.uz = P.uz[idx]; s.w = P.w[idx];
+            s.W0 = a.track_work ? P.W0[idx] : 0.f;
+            s.W1 = a.track_work ? P.W1[idx] : 0.f;
+            s.jr = jr;
+            bool in_smem = false;
+            if (smem_usable) {
+                li = wrapn(iz - col0, a.nzp);
+                lj = jr - row0;
+                in_smem = li >= 1 && li <= FW - 2 && lj >= 1 && lj <= FR - 2;
+            }
+            if (in_smem) {
+                push_move<NP>(sacc, a, li, lj, s, d);
+                fast = same_cell(d);
+                if (!fast) deposit_general<NP>(sacc, a, li, lj, d);
+            } else {
+                push_move<NP>(gacc, a, iz, jr, s, d);
+                deposit_general<NP>(gacc, a, iz, jr, d);
+            }
+        }
+        if (smem_usable) {                     // block-uniform branch
+            const unsigned fm = __ballot_sync(FULL, fast);
+            if (fast) {
+                const unsigned grp = __match_any_sync(fm, (unsigned)((lj << 12) | li));
+                deposit_fast<NP>(sacc, a, li, lj, d, grp, lane == __ffs(grp) - 1);
+            }
+        }
+        if (act) {
+            int niz = wrapn(iz + s.diz, a.nzp);
+            int njr = jr + s.djr;
+            bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
+            P.cell[idx] = dead ? -1 : niz * a.nr + njr;
+            P.oz[idx] = s.oz; P.orr[idx] = s.orr; P.cph[idx] = s.cph; P.sph[idx] = s.sph;
+            P.ux[idx] = s.ux; P.uy[idx] = s.uy; P.uz[idx] = s.uz;
+            if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+        }
     }
-    if (tile_mode) {
+    if (smem_usable) {
         __syncthreads();
         const int nJ = 3 * NP * JW * JR;
         for (int k = threadIdx.x; k < nJ; k += blockDim.x) {
@@ -447,7 +590,7 @@ __global__ void __launch_bounds__(256) k_gpd(Particles P, const float *__restric
             int li = k % JW, t2 = k / JW, lj = t2 % JR, pl = t2 / JR;
             int j = row0 + lj;
             if (j < 0 || j > a.nr) continue;
-            int col = pwrap(col0 + li, a.nzp);
+            int col = wrapn(col0 + li, a.nzp);
             atomicAdd(&J[(size_t)pl * a.plane + (size_t)j * a.nzp + col], v);
         }
     }
@@ -505,14 +648,23 @@ __device__ __forceinline__ int sort_key(int cell, const PArgs &a)
     return ((tzi * a.ntr + tri) * a.TR + (jr - tri * a.TR)) * a.TZ + (iz - tzi * a.TZ);
 }
 
+// histogram of live particles per key; lanes of a warp that share a key (the
+// buffer is nearly sorted) add their count with one atomic
 __global__ void k_count(const int32_t *__restrict__ cell, const long long *dcount, int32_t *counts,
                         PArgs a)
 {
     const long long np = dcount[0];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
-         i += (long long)gridDim.x * blockDim.x) {
-        int c = cell[i];
-        if (c >= 0) atomicAdd(&counts[sort_key(c, a)], 1);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < np; i0 += stride) {
+        const long long i = i0 + threadIdx.x;
+        const int c = i < np ? cell[i] : -1;
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+        if (c >= 0) {
+            const int k = sort_key(c, a);
+            const unsigned grp = __match_any_sync(act, k);
+            if (lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&counts[k], __popc(grp));
+        }
     }
 }
 
@@ -594,13 +746,21 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
                           const int32_t *offsets, PArgs a)
 {
     const long long np = dcount[0];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
-         i += (long long)gridDim.x * blockDim.x) {
-        int c = src.cell[i];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < np; i0 += stride) {
+        const long long i = i0 + threadIdx.x;
+        const int c = i < np ? src.cell[i] : -1;
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
         if (c < 0) continue;
-        int k = sort_key(c, a);
-        int pos = atomicSub(&counts[k], 1) - 1;
-        long long d = (long long)offsets[k] + pos;
+        const int k = sort_key(c, a);
+        const unsigned grp = __match_any_sync(act, k);
+        const int leader = __ffs(grp) - 1, n = __popc(grp);
+        int top = 0;
+        if ((int)lane == leader) top = atomicSub(&counts[k], n);      // slots [top-n, top)
+        top = __shfl_sync(grp, top, leader);
+        const int rank = __popc(grp & ((1u << lane) - 1u));
+        const long long d = (long long)offsets[k] + top - n + rank;
         dst.cell[d] = c; dst.oz[d] = src.oz[i]; dst.orr[d] = src.orr[i];
         dst.cph[d] = src.cph[i]; dst.sph[d] = src.sph[i];
         dst.ux[d] = src.ux[i]; dst.uy[d] = src.uy[i]; dst.uz[d] = src.uz[i]; dst.w[d] = src.w[i];
@@ -807,7 +967,7 @@ __global__ void k_export(Particles P, long long n, double *out, long long stride
         const bool dead = cell < 0;
         if (dead) cell = 0;
         int iz = cell / L.nr, jr = cell - iz * L.nr;
-        long long il = ((long long)iz - L.zoff) % L.nzp;
+        int il = iz - (int)L.zoff;
         if (il < 0) il += L.nzp;
         out[0 * stride + i] = L.zmin + ((double)il + (double)P.oz[i]) * L.dz;
         out[1 * stride + i] = ((double)jr + (double)P.orr[i]) * L.dr;
@@ -841,14 +1001,14 @@ __global__ void k_rho(Particles P, long long n, double *out, LoadArgs L, int nm)
         int cell = P.cell[i];
         if (cell < 0) continue;
         int iz = cell / L.nr, jr = cell - iz * L.nr;
-        long long il = ((long long)iz - L.zoff) % L.nzp;
+        int il = iz - (int)L.zoff;
         if (il < 0) il += L.nzp;
         double oz = P.oz[i], orr = P.orr[i], Q = -(double)P.w[i];
         double c1 = P.cph[i], s1 = -(double)P.sph[i];      // e^{-i phi}
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++) {
-                long long ic = il + a;
-                if (L.periodic) ic %= L.nz;
+                int ic = il + a;
+                if (L.periodic) ic = ic >= L.nz ? ic - L.nz : ic;
                 else if (ic >= L.nz) continue;
                 int j = jr + b;
                 double wgt = (a ? oz : 1.0 - oz) * (b ? orr : 1.0 - orr);
@@ -888,9 +1048,11 @@ __global__ void k_psums_partial(Particles P, const long long *dcount, double *pa
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (P.cell[i] < 0) continue;
-        double w = P.w[i], ux = P.ux[i], uy = P.uy[i], uz = P.uz[i];
-        cnt += 1.0; chg -= w;
-        ke += w * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+        const float ux = P.ux[i], uy = P.uy[i], uz = P.uz[i];
+        const float u2 = ux * ux + uy * uy + uz * uz;
+        const float gm1 = u2 / (1.f + sqrtf(1.f + u2));          // gamma - 1 without cancellation
+        cnt += 1.0; chg -= (double)P.w[i];
+        ke += (double)P.w[i] * (double)gm1;
     }
     s0[threadIdx.x] = cnt; s1[threadIdx.x] = chg; s2[threadIdx.x] = ke;
     __syncthreads();

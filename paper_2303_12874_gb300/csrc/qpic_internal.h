@@ -90,7 +90,7 @@ struct qpic_ctx {
     qpic::Particles p, ps;        // live buffers and the sort's second buffer
     qpic::Particles64 p64;
     double qref = 0.0;            // max |charge| of a particle
-    float qscale = 0.f;           // fixed-point scale 2^44 / qref
+    float qscale = 0.f;           // fixed-point scale 2^40 / qref
 
     // plasma (for the moving-window injection)
     bool have_plasma = false;

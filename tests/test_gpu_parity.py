@@ -114,16 +114,18 @@ def o_cB(o):
     return C.dual_coefficients(o.dt, o.dz)[1]
 
 
-@pytest.mark.parametrize("solver", ["dual", "yee"])
-def test_full_step_config1(solver):
+@pytest.mark.parametrize("solver,sort_period", [("dual", 2), ("yee", 2), ("dual", 1), ("dual", 3)])
+def test_full_step_config1(solver, sort_period):
+    """sort_period 3 leaves particles up to 2 cells outside their tile: those
+    take the global-memory path of the same kernel"""
     w = synth.workload("cfg1_small")
     nz, nr = w["nz"], w["nr"]
     from oracle import coeffs as C
     dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], nr, 2, solver)
-    sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, solver=solver)
+    sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, solver=solver, sort_period=sort_period)
     _config1_state(sim, o)
     # a few GPU steps to build up currents and plasma motion, then inject that state
-    sim.step(3)
+    sim.step(4 if sort_period == 3 else 3)
     sync_fields(sim, o, ("E", "B"))
     p = sim.particles_raw()
     live = p["w"] > 0
