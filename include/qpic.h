@@ -182,6 +182,23 @@ qpic_status qpic_get_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t m
 qpic_status qpic_set_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t mode,
                            const double *re, const double *im);
 
+/* Charge density per mode like qpic_get_field(ctx, QPIC_FIELD_RHO, ...), but
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point serves callers that cannot allocate -- code running while a
+ * stream is being captured into a CUDA graph (cudaMalloc/cudaFree break a
+ * capture), hosts that give the library a fixed memory budget, callers inside
+ * an allocator's own callbacks.  The deposit uses a file-scope static device
+ * array of 2^21 doubles (16 MiB) that every GPU loading the library holds until
+ * exit; grids needing more than n_modes*2*(nr+1)*nz <= 2^21 doubles are
+ * rejected with QPIC_EINVAL and a message.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls share
+ * the array (each clears what it uses first); calls that overlap on the GPU,
+ * from any context or thread, race.  re/im: caller-owned host arrays of
+ * (nr+1)*nz doubles in the field-plane layout; im may be NULL.  Synchronises
+ * the context's stream. */
+qpic_status qpic_charge_density_noalloc(qpic_ctx *ctx, int32_t mode, double *re, double *im);
+
 /* Number of live particles. */
 qpic_status qpic_num_particles(qpic_ctx *ctx, int64_t *n);
 

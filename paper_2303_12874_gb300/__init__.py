@@ -101,6 +101,8 @@ def _declare(L):
                                        ctypes.c_double, _D]
     L.qpic_profile.argtypes = [_P, _I, _I]
     L.qpic_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+    L.qpic_charge_density_noalloc.argtypes = [_P, _I, _D, _D]
+    L.qpic_charge_density_noalloc.restype = ctypes.c_int
     L.qpic_launch_count.restype = ctypes.c_int
     L.qpic_kernel_times.argtypes = [_P, _I, _D, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I)]
