@@ -103,10 +103,11 @@ def _dist():
     return ws, rank, local
 
 
-def _make_sim(q, w, stream, track_work=False):
+def _make_sim(q, w, stream, track_work=False, precision=None):
+    kw = {} if precision is None else {"precision": precision}
     return q.Sim(w["nz"], w["nr"], w["dz"], w["dr"], n_modes=w["n_modes"], solver=w["solver"],
                  periodic=w["periodic"], moving_window=w["moving_window"], stream=stream,
-                 track_work=track_work, seed=w["plasma"]["seed"])
+                 track_work=track_work, seed=w["plasma"]["seed"], **kw)
 
 
 def _init_state(sim, w):
@@ -223,6 +224,7 @@ def run_ours(args, w):
     sim.step(args.prof_steps)
     kt = sim.kernel_times()
     sim.profile(False, True)
+    dt_used = sim.dt
     gpd_ms, gpd_n = kt["gather_push_deposit"]
     gpd_avg = gpd_ms / max(gpd_n, 1)
     solver_ms = sum(kt[k][0] for k in ("faraday", "j_decode", "jz_filter", "ampere"))
@@ -277,10 +279,31 @@ def run_ours(args, w):
         sim2.close()
         del d
 
+    # ---- the plain FP64 GPU path on the same workload and GPU
+    fp64 = None
+    if not args.no_fp64:
+        sim.close()
+        s64 = _make_sim(q, w, stream, precision=q.QPIC_FP64)
+        _init_state(s64, w)
+        for _ in range(2):
+            s64.step(1)
+        n64 = s64.diag()["particles"]
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(args.fp64_steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"value": n64 * args.fp64_steps / (ms64 / 1e3), "unit": "particle-steps/s",
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                "dtype": "f64", "note": "one thread per particle, FP64 atomics, no tiles or sort"}
+        s64.close()
+
     # ---- CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, n, t = oracle_sample(w, sim.dt, args.ref_nz, 2)
+        rate, n, t = oracle_sample(w, dt_used, args.ref_nz, 2)
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                "sample": "2 steps of a %d x %d periodic z-slab of the workload (%d particles), "
                          "single-threaded FP64 C, %.1f s" % (args.ref_nz, w["nr"], n, t)}
@@ -294,7 +317,7 @@ def run_ours(args, w):
             "config": {"workload": args.workload, "nz": w["nz"], "nr": w["nr"],
                        "modes": w["n_modes"], "ppc": list(w["plasma"]["ppc"]),
                        "particles_per_gpu": int(n_avg), "solver": "dual L=16",
-                       "dt": sim.dt, "deposit": "int64 fixed point",
+                       "dt": dt_used, "deposit": "int64 fixed point",
                        "l2": "inputs larger than L2 (particles %.1f GB)" % (n_avg * 36 / 1e9),
                        "parallelism": "replicas x%d" % ws},
             "cell_updates_per_s": cell_updates,
@@ -305,6 +328,8 @@ def run_ours(args, w):
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_source": peak_src + " (hbm_gbs, burst)",
                          "algorithmic_bytes_per_launch": gpd_bytes, "traffic": traffic},
+            "fp64_gpu_path": fp64,
+            "fp32_over_fp64": (value / ws / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         }
         print(json.dumps(line))
@@ -325,6 +350,8 @@ def main():
     ap.add_argument("--ref-nz", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -76,6 +76,22 @@ void free_particles(qpic_ctx *c, qpic::Particles &p)
     p = qpic::Particles();
 }
 
+bool alloc_particles64(qpic_ctx *c, qpic::Particles64 &p, long long cap)
+{
+    bool ok = alloc_arr(c, &p.z, cap) && alloc_arr(c, &p.x, cap) && alloc_arr(c, &p.y, cap) &&
+              alloc_arr(c, &p.ux, cap) && alloc_arr(c, &p.uy, cap) && alloc_arr(c, &p.uz, cap) &&
+              alloc_arr(c, &p.w, cap);
+    if (ok && c->cfg.track_work) ok = alloc_arr(c, &p.W0, cap) && alloc_arr(c, &p.W1, cap);
+    return ok;
+}
+
+void free_particles64(qpic_ctx *c, qpic::Particles64 &p)
+{
+    void *arr[9] = {p.z, p.x, p.y, p.ux, p.uy, p.uz, p.w, p.W0, p.W1};
+    for (void *a : arr) dfree(c, a);
+    p = qpic::Particles64();
+}
+
 qpic_status ensure_capacity(qpic_ctx *c, long long need)
 {
     if (need <= c->cap) return QPIC_OK;
@@ -83,6 +99,18 @@ qpic_status ensure_capacity(qpic_ctx *c, long long need)
                                              : std::max(need + need / 4 + 4096, c->cap);
     if (cap < need) return fail(c, QPIC_ECAPACITY, "particle capacity (max_particles) exceeded");
     cudaStreamSynchronize(c->stream);
+    if (c->fp64) {
+        free_particles64(c, c->p64);
+        free_particles64(c, c->ps64);
+        dfree(c, c->scan_flag); dfree(c, c->scan_pos); dfree(c, c->scan_tmp64);
+        c->cap = 0;
+        if (!alloc_particles64(c, c->p64, cap) || !alloc_particles64(c, c->ps64, cap) ||
+            !alloc_arr(c, &c->scan_flag, (size_t)cap + 1) || !alloc_arr(c, &c->scan_pos, (size_t)cap + 1) ||
+            !alloc_arr(c, &c->scan_tmp64, (size_t)(cap + 1) / 4096 + 4))
+            return fail(c, QPIC_ENOMEM, "particle buffers: device allocation failed");
+        c->cap = cap;
+        return QPIC_OK;
+    }
     free_particles(c, c->p);
     free_particles(c, c->ps);
     c->cap = 0;
@@ -97,6 +125,16 @@ long long phys_col(const qpic_ctx *c, long long il)
 {
     long long p = (il + c->g.zoff) % c->g.nzp;
     return p < 0 ? p + c->g.nzp : p;
+}
+
+double *field_base64(qpic_ctx *c, int which)
+{
+    switch (which) {
+    case QPIC_FIELD_E: return c->E64;
+    case QPIC_FIELD_B: return c->B64;
+    case QPIC_FIELD_BBAR: return c->Bb64;
+    default: return c->J64;
+    }
 }
 
 float *field_base(qpic_ctx *c, int which)
@@ -124,7 +162,10 @@ void do_shift(qpic_ctx *c)
     launch_zero_column(c, back);
     c->g.zoff = (c->g.zoff + 1) % c->g.nzp;
     c->shifts++;
-    if (c->have_plasma) {
+    if (c->have_plasma && c->fp64) {
+        if (c->np + (long long)c->g.nr * c->ppc_z * c->ppc_r * c->ppc_phi > c->cap) fp64_compact(c);
+        fp64_load_plasma(c, c->g.nz - 1, 1, true);
+    } else if (c->have_plasma) {
         if (c->np + (long long)c->g.nr * c->ppc_z * c->ppc_r * c->ppc_phi > c->cap) {
             // host bound is loose after sorts dropped particles: refresh it
             long long n = 0;
@@ -140,8 +181,12 @@ qpic_status run_one_step(qpic_ctx *c, int stages)
 {
     if (stages & QPIC_STAGE_FARADAY) launch_faraday(c);
     if (stages & QPIC_STAGE_PARTICLES) {
-        launch_gpd(c);
-        launch_jdecode(c);
+        if (c->fp64) {
+            fp64_push_deposit(c);
+        } else {
+            launch_gpd(c);
+            launch_jdecode(c);
+        }
         c->j_filtered = false;
     }
     if (stages & QPIC_STAGE_AMPERE) {
@@ -156,6 +201,7 @@ qpic_status run_one_step(qpic_ctx *c, int stages)
         while (c->cfg.window_v * ((double)c->nstep * c->dt) >= (double)(c->shifts + 1) * c->dz)
             do_shift(c);
     }
+    if ((stages & QPIC_STAGE_SORT) && c->fp64) return QPIC_OK;    // plain path: no sort
     if (stages & QPIC_STAGE_SORT) {
         bool due = c->sort_period <= 1 || (c->nstep % c->sort_period) == 0 ||
                    c->n_tail > c->cap / 64;
@@ -282,8 +328,9 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
         return bad(QPIC_EINVAL, "grid: need nz >= 4, nr >= 2, 1 <= n_modes <= 4");
     if (!(cfg->dz > 0) || !(cfg->dr > 0)) return bad(QPIC_EINVAL, "dz, dr must be positive");
     if (cfg->solver != QPIC_YEE && cfg->solver != QPIC_DUAL) return bad(QPIC_EINVAL, "solver");
-    if (cfg->precision == QPIC_FP64) return bad(QPIC_EINVAL, "FP64 path: use precision FP32_FIXED");
-    if (cfg->precision != QPIC_FP32_FIXED) return bad(QPIC_EINVAL, "precision");
+    if (cfg->precision != QPIC_FP32_FIXED && cfg->precision != QPIC_FP64)
+        return bad(QPIC_EINVAL, "precision: QPIC_FP32_FIXED or QPIC_FP64");
+    c->fp64 = cfg->precision == QPIC_FP64;
     if (cfg->moving_window && cfg->periodic_z) return bad(QPIC_EINVAL, "moving window needs periodic_z = 0");
     c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     c->dz = cfg->dz;
@@ -318,11 +365,25 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     g.plane = (size_t)(g.nr + 1) * g.nzp;
     g.dz = (float)c->dz; g.dr = (float)c->dr; g.dt = (float)c->dt;
     const size_t nplanes = (size_t)3 * g.nparts;
-    if (!alloc_arr(c, &c->E, nplanes * g.plane) || !alloc_arr(c, &c->B, nplanes * g.plane) ||
-        !alloc_arr(c, &c->Bb, nplanes * g.plane) || !alloc_arr(c, &c->Jf, nplanes * g.plane) ||
-        !alloc_arr(c, &c->Jzf, (size_t)g.nparts * g.plane) ||
-        !alloc_arr(c, &c->Jacc, nplanes * g.plane) || !alloc_arr(c, &c->rowf, (size_t)4 * (g.nr + 1)) ||
-        !alloc_arr(c, &c->coef, (size_t)2 * MAX_L + MAX_TAPS) || !alloc_arr(c, &c->d_err, 4) ||
+    if (c->fp64) {
+        if (!alloc_arr(c, &c->E64, nplanes * g.plane) || !alloc_arr(c, &c->B64, nplanes * g.plane) ||
+            !alloc_arr(c, &c->Bb64, nplanes * g.plane) || !alloc_arr(c, &c->J64, nplanes * g.plane) ||
+            !alloc_arr(c, &c->Jz64, (size_t)g.nparts * g.plane))
+            return bad(QPIC_ENOMEM, "field buffers: device allocation failed");
+        cudaMemsetAsync(c->E64, 0, nplanes * g.plane * 8, c->stream);
+        cudaMemsetAsync(c->B64, 0, nplanes * g.plane * 8, c->stream);
+        cudaMemsetAsync(c->Bb64, 0, nplanes * g.plane * 8, c->stream);
+        cudaMemsetAsync(c->J64, 0, nplanes * g.plane * 8, c->stream);
+        cudaMemsetAsync(c->Jz64, 0, (size_t)g.nparts * g.plane * 8, c->stream);
+    } else if (!alloc_arr(c, &c->E, nplanes * g.plane) || !alloc_arr(c, &c->B, nplanes * g.plane) ||
+               !alloc_arr(c, &c->Bb, nplanes * g.plane) || !alloc_arr(c, &c->Jf, nplanes * g.plane) ||
+               !alloc_arr(c, &c->Jzf, (size_t)g.nparts * g.plane) ||
+               !alloc_arr(c, &c->Jacc, nplanes * g.plane)) {
+        return bad(QPIC_ENOMEM, "field buffers: device allocation failed");
+    }
+    if (!alloc_arr(c, &c->rowf, (size_t)4 * (g.nr + 1)) ||
+        !alloc_arr(c, &c->coef, (size_t)2 * MAX_L + MAX_TAPS) ||
+        !alloc_arr(c, &c->coef64, (size_t)2 * MAX_L + MAX_TAPS) || !alloc_arr(c, &c->d_err, 4) ||
         !alloc_arr(c, &c->d_count, 4))
         return bad(QPIC_ENOMEM, "field buffers: device allocation failed");
     c->ntz = (g.nzp + c->TZ - 1) / c->TZ;
@@ -334,12 +395,14 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
         !alloc_arr(c, &c->offsets, (size_t)c->nkeys + 1) || !alloc_arr(c, &c->scan_tmp, (size_t)nb + 2) ||
         !alloc_arr(c, &c->d_red, (size_t)c->red_cap))
         return bad(QPIC_ENOMEM, "sort buffers: device allocation failed");
-    cudaMemsetAsync(c->E, 0, nplanes * g.plane * sizeof(float), c->stream);
-    cudaMemsetAsync(c->B, 0, nplanes * g.plane * sizeof(float), c->stream);
-    cudaMemsetAsync(c->Bb, 0, nplanes * g.plane * sizeof(float), c->stream);
-    cudaMemsetAsync(c->Jf, 0, nplanes * g.plane * sizeof(float), c->stream);
-    cudaMemsetAsync(c->Jzf, 0, (size_t)g.nparts * g.plane * sizeof(float), c->stream);
-    cudaMemsetAsync(c->Jacc, 0, nplanes * g.plane * 8, c->stream);
+    if (!c->fp64) {
+        cudaMemsetAsync(c->E, 0, nplanes * g.plane * sizeof(float), c->stream);
+        cudaMemsetAsync(c->B, 0, nplanes * g.plane * sizeof(float), c->stream);
+        cudaMemsetAsync(c->Bb, 0, nplanes * g.plane * sizeof(float), c->stream);
+        cudaMemsetAsync(c->Jf, 0, nplanes * g.plane * sizeof(float), c->stream);
+        cudaMemsetAsync(c->Jzf, 0, (size_t)g.nparts * g.plane * sizeof(float), c->stream);
+        cudaMemsetAsync(c->Jacc, 0, nplanes * g.plane * 8, c->stream);
+    }
     cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
     cudaMemsetAsync(c->d_count, 0, 4 * sizeof(long long), c->stream);
     cudaMemsetAsync(c->offsets, 0, ((size_t)c->nkeys + 1) * sizeof(int32_t), c->stream);
@@ -446,6 +509,11 @@ qpic_status qpic_load_plasma(qpic_ctx *c, double n0, double z_start, double ramp
     double rmax = (c->g.nr - 1 + (ppc_r - 0.5) / ppc_r) * c->dr;
     set_qscale(c, n0 * 2.0 * kPi * rmax * (c->dr / ppc_r) * (c->dz / ppc_z) / ppc_phi);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (c->fp64) {
+        if (!fp64_load_plasma(c, 0, c->g.nz, false)) return fail(c, QPIC_ECAPACITY, "capacity");
+        fp64_compact(c);
+        return cuda_check(c, "load_plasma");
+    }
     if (!launch_load_plasma(c, 0, c->g.nz, false)) return fail(c, QPIC_ECAPACITY, "capacity");
     launch_sort(c);
     live_count(c);
@@ -470,6 +538,13 @@ qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const d
         for (int k = 0; k < 7; k++)
             cudaMemcpyAsync(tmp + (size_t)k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
+    }
+    if (c->fp64) {
+        fp64_load_particles(c, n, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n, tmp + 5 * n,
+                            tmp + 6 * n);
+        cudaStreamSynchronize(c->stream);
+        if (tmp) dfree(c, tmp);
+        return cuda_check(c, "load_particles");
     }
     launch_load_particles(c, n, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n, tmp + 5 * n,
                           tmp + 6 * n);
@@ -533,6 +608,27 @@ qpic_status qpic_get_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
         dfree(c, d);
         return cuda_check(c, "get_field rho");
     }
+    if (c->fp64) {
+        std::vector<double> dre(g.plane), dim(g.plane, 0.0);
+        const double *base = field_base64(c, which);
+        int pre = mode == 0 ? 0 : 2 * mode - 1;
+        const double *sr = base + (size_t)(comp * g.nparts + pre) * g.plane;
+        const double *si = mode ? base + (size_t)(comp * g.nparts + pre + 1) * g.plane : nullptr;
+        if (which == QPIC_FIELD_J && comp == QPIC_COMP_Z && c->j_filtered) {
+            sr = c->Jz64 + (size_t)pre * g.plane;
+            si = mode ? c->Jz64 + (size_t)(pre + 1) * g.plane : nullptr;
+        }
+        cudaMemcpyAsync(dre.data(), sr, g.plane * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (si) cudaMemcpyAsync(dim.data(), si, g.plane * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "get_field");
+        for (int j = 0; j <= g.nr; j++)
+            for (int il = 0; il < g.nz; il++) {
+                size_t q = (size_t)j * g.nzp + phys_col(c, il);
+                re[(size_t)j * g.nz + il] = dre[q];
+                if (im) im[(size_t)j * g.nz + il] = dim[q];
+            }
+        return QPIC_OK;
+    }
     std::vector<float> hre(g.plane), him(g.plane, 0.f);
     const float *base = field_base(c, which);
     int pre = mode == 0 ? 0 : 2 * mode - 1;
@@ -562,6 +658,24 @@ qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
         (which != QPIC_FIELD_E && which != QPIC_FIELD_B && which != QPIC_FIELD_BBAR))
         return fail(c, QPIC_EINVAL, "set_field arguments");
     const FieldGeom &g = c->g;
+    if (c->fp64) {
+        std::vector<double> dre(g.plane, 0.0), dim(g.plane, 0.0);
+        for (int j = 0; j <= g.nr; j++)
+            for (int il = 0; il < g.nz; il++) {
+                size_t q = (size_t)j * g.nzp + phys_col(c, il);
+                dre[q] = re[(size_t)j * g.nz + il];
+                dim[q] = im ? im[(size_t)j * g.nz + il] : 0.0;
+            }
+        double *base = field_base64(c, which);
+        int pre = mode == 0 ? 0 : 2 * mode - 1;
+        cudaMemcpyAsync(base + (size_t)(comp * g.nparts + pre) * g.plane, dre.data(), g.plane * 8,
+                        cudaMemcpyHostToDevice, c->stream);
+        if (mode)
+            cudaMemcpyAsync(base + (size_t)(comp * g.nparts + pre + 1) * g.plane, dim.data(),
+                            g.plane * 8, cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        return cuda_check(c, "set_field");
+    }
     std::vector<float> hre(g.plane, 0.f), him(g.plane, 0.f);
     for (int j = 0; j <= g.nr; j++)
         for (int il = 0; il < g.nz; il++) {
@@ -583,6 +697,11 @@ qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
 qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
 {
     if (!c || !n) return QPIC_EINVAL;
+    if (c->fp64) {
+        fp64_compact(c);
+        *n = c->np;
+        return cuda_check(c, "num_particles");
+    }
     launch_sort(c);
     *n = live_count(c);
     return cuda_check(c, "num_particles");
@@ -591,14 +710,21 @@ qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
 qpic_status qpic_get_particles(qpic_ctx *c, double *out, int64_t capacity, int64_t *n_out)
 {
     if (!c || !out || !n_out) return QPIC_EINVAL;
-    launch_sort(c);
-    long long n = live_count(c);
+    long long n;
+    if (c->fp64) {
+        fp64_compact(c);
+        n = c->np;
+    } else {
+        launch_sort(c);
+        n = live_count(c);
+    }
     *n_out = n;
     if (n > capacity) return fail(c, QPIC_ECAPACITY, "get_particles: capacity too small");
     double *d = nullptr;
     if (n > 0) {
         if (!alloc_arr(c, &d, (size_t)9 * n)) return fail(c, QPIC_ENOMEM, "export buffer");
-        launch_export_particles(c, d, n);
+        if (c->fp64) fp64_export_particles(c, d, n);
+        else launch_export_particles(c, d, n);
         for (int k = 0; k < 9; k++)
             cudaMemcpyAsync(out + (size_t)k * capacity, d + (size_t)k * n, n * sizeof(double),
                             cudaMemcpyDeviceToHost, c->stream);
@@ -611,13 +737,14 @@ qpic_status qpic_get_particles(qpic_ctx *c, double *out, int64_t capacity, int64
 qpic_status qpic_get_particles_raw(qpic_ctx *c, double *out, int64_t capacity, int64_t *n_out)
 {
     if (!c || !out || !n_out) return QPIC_EINVAL;
-    long long n = live_count(c);           // buffer slots in use (device count)
+    long long n = c->fp64 ? c->np : live_count(c);   // buffer slots in use
     *n_out = n;
     if (n > capacity) return fail(c, QPIC_ECAPACITY, "get_particles_raw: capacity too small");
     double *d = nullptr;
     if (n > 0) {
         if (!alloc_arr(c, &d, (size_t)9 * n)) return fail(c, QPIC_ENOMEM, "export buffer");
-        launch_export_particles(c, d, n);
+        if (c->fp64) fp64_export_particles(c, d, n);
+        else launch_export_particles(c, d, n);
         for (int k = 0; k < 9; k++)
             cudaMemcpyAsync(out + (size_t)k * capacity, d + (size_t)k * n, n * sizeof(double),
                             cudaMemcpyDeviceToHost, c->stream);
@@ -636,7 +763,8 @@ qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)
     v[1] = (double)c->nstep;
     v[2] = (double)c->shifts;
     double s3[3];
-    launch_particle_sums(c, s3);
+    if (c->fp64) fp64_particle_sums(c, s3);
+    else launch_particle_sums(c, s3);
     v[3] = s3[0]; v[4] = s3[1]; v[5] = s3[2];
     std::vector<double> fe(nm);
     launch_field_energy(c, fe.data());

@@ -28,6 +28,11 @@ void set_solver_constants(qpic_ctx *c)
     for (int l = 0; l < c->L; l++) { h[l] = (float)c->cE[l]; h[MAX_L + l] = (float)c->cB[l]; }
     for (size_t q = 0; q < c->taps.size(); q++) h[2 * MAX_L + q] = (float)c->taps[q];
     cudaMemcpyAsync(c->coef, h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+    static double h64[2 * MAX_L + MAX_TAPS];
+    for (int k = 0; k < 2 * MAX_L + MAX_TAPS; k++) h64[k] = 0.0;
+    for (int l = 0; l < c->L; l++) { h64[l] = c->cE[l]; h64[MAX_L + l] = c->cB[l]; }
+    for (size_t q = 0; q < c->taps.size(); q++) h64[2 * MAX_L + q] = c->taps[q];
+    cudaMemcpy(c->coef64, h64, sizeof(h64), cudaMemcpyHostToDevice);
 }
 
 struct GridArgs {
@@ -35,7 +40,9 @@ struct GridArgs {
     long long zoff;
     size_t plane;
     float dz, dr, dt;
-    const float *coef;     // [cE | cB | taps]
+    double dz64, dr64, dt64;
+    const float *coef;     // [cE | cB | taps] FP32
+    const double *coef64;  // the same in FP64 (plain FP64 path)
 };
 
 static GridArgs grid_args(const qpic_ctx *c)
@@ -44,7 +51,9 @@ static GridArgs grid_args(const qpic_ctx *c)
     a.nz = c->g.nz; a.nr = c->g.nr; a.nzp = c->g.nzp; a.nparts = c->g.nparts; a.L = c->L;
     a.zoff = c->g.zoff % c->g.nzp; a.plane = c->g.plane;
     a.dz = (float)c->dz; a.dr = (float)c->dr; a.dt = (float)c->dt;
+    a.dz64 = c->dz; a.dr64 = c->dr; a.dt64 = c->dt;
     a.coef = c->coef;
+    a.coef64 = c->coef64;
     return a;
 }
 
@@ -69,18 +78,21 @@ __device__ __forceinline__ int part_mode(int p) { return (p + 1) >> 1; }
 // ---------------------------------------------------------------- Faraday
 // dB/dt = -curl E:  B_r: -(i m/r) E_z + D^E_z E_phi;  B_phi: -D^E_z E_r + d_r E_z;
 // B_z: -(1/r) d_r(r E_phi) + (i m/r) E_r.  Writes B^{n+1/2} and Bbar^n.
-__global__ void __launch_bounds__(FTILE) k_faraday(const float *__restrict__ E, float *__restrict__ B,
-                                                  float *__restrict__ Bb, GridArgs a)
+template <typename T>
+__global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *__restrict__ B,
+                                                  T *__restrict__ Bb, GridArgs a)
 {
-    extern __shared__ float sh[];
+    extern __shared__ __align__(16) unsigned char shraw[];
+    T *sh = reinterpret_cast<T *>(shraw);
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * FTILE;
     const int W = FTILE + 2 * a.L;
     const int P = a.nparts;
-    float *sC = sh;                  // [L] C^E
-    float *sEphi = sh + MAX_L;       // [P][W]
-    float *sEr = sEphi + P * W;      // [P][W]
-    for (int k = threadIdx.x; k < a.L; k += FTILE) sC[k] = a.coef[k];
+    T *sC = sh;                      // [L] C^E
+    T *sEphi = sh + MAX_L;           // [P][W]
+    T *sEr = sEphi + P * W;          // [P][W]
+    for (int k = threadIdx.x; k < a.L; k += FTILE)
+        sC[k] = sizeof(T) == 8 ? (T)a.coef64[k] : (T)a.coef[k];
     for (int k = threadIdx.x; k < W; k += FTILE) {
         int col = wrapz(i0 - a.L + k, a.nzp);
         for (int p = 0; p < P; p++) {
@@ -92,72 +104,72 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const float *__restrict__ E, 
     const int i = i0 + threadIdx.x;
     if (i >= a.nzp) return;
     const bool gap = in_gap(i, a);
-    const float dr = a.dr, dz = a.dz, dt = a.dt;
-    const float rj = j * dr, rh = (j + 0.5f) * dr, rj1 = (j + 1) * dr;
+    const T dr = (T)a.dr64, dz = (T)a.dz64, dt = (T)a.dt64;
+    const T rj = j * dr, rh = (j + (T)0.5) * dr, rj1 = (j + 1) * dr;
     const int s = threadIdx.x + a.L;   // smem index of column i
     for (int p = 0; p < P; p++) {
         const int m = part_mode(p);
         const bool isim = (p > 0) && !(p & 1);
         const int pr = isim ? p - 1 : p, pim = isim ? p : p + 1;   // re / im partner
         // D^E_z of E_phi and E_r at i + 1/2
-        float dEphi = 0.f, dEr = 0.f;
+        T dEphi = 0, dEr = 0;
         for (int l = 1; l <= a.L; l++) {
-            float cl = sC[l - 1];
+            T cl = sC[l - 1];
             dEphi += cl * (sEphi[p * W + s + l] - sEphi[p * W + s + 1 - l]);
             dEr += cl * (sEr[p * W + s + l] - sEr[p * W + s + 1 - l]);
         }
         dEphi /= dz; dEr /= dz;
         const size_t base = (size_t)j * a.nzp + i;
         // B_r at (i+1/2, j)
-        float d;
+        T d;
         if (j == 0) {
             if (m == 1) {
                 // -(i/r) E_z -> -i E_z^1(dr)/dr on the axis
-                const float *Ez = E + (size_t)(2 * P) * a.plane + (size_t)1 * a.nzp + i;
-                float ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
+                const T *Ez = E + (size_t)(2 * P) * a.plane + (size_t)1 * a.nzp + i;
+                T ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
                 d = (isim ? -ezr : ezi) / dr + dEphi;
             } else {
-                d = 0.f;
+                d = 0;
             }
         } else {
-            float imr = 0.f;
+            T imr = 0;
             if (m > 0) {
-                const float *Ez = E + (size_t)(2 * P) * a.plane + base;
-                float ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
-                imr = (isim ? ezr : -ezi) * (float)m / rj;      // part of (i m / r) E_z
+                const T *Ez = E + (size_t)(2 * P) * a.plane + base;
+                T ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
+                imr = (isim ? ezr : -ezi) * (T)m / rj;      // part of (i m / r) E_z
             }
             d = -imr + dEphi;
         }
         {
             size_t q = (size_t)(0 * P + p) * a.plane + base;
-            float bo = B[q], bn = gap ? 0.f : bo + dt * d;
-            B[q] = bn; Bb[q] = gap ? 0.f : 0.5f * (bo + bn);
+            T bo = B[q], bn = gap ? (T)0 : bo + dt * d;
+            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bo + bn);
         }
         if (j < a.nr) {
             // B_phi at (i+1/2, j+1/2)
-            const float *Ez = E + (size_t)(2 * P + p) * a.plane + base;
+            const T *Ez = E + (size_t)(2 * P + p) * a.plane + base;
             d = -dEr + (Ez[a.nzp] - Ez[0]) / dr;
             size_t q = (size_t)(1 * P + p) * a.plane + base;
-            float bo = B[q], bn = gap ? 0.f : bo + dt * d;
-            B[q] = bn; Bb[q] = gap ? 0.f : 0.5f * (bo + bn);
+            T bo = B[q], bn = gap ? (T)0 : bo + dt * d;
+            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bo + bn);
             // B_z at (i, j+1/2)
-            const float *Ep = E + (size_t)(1 * P + p) * a.plane + base;
-            float imr = 0.f;
+            const T *Ep = E + (size_t)(1 * P + p) * a.plane + base;
+            T imr = 0;
             if (m > 0) {
-                const float *Er = E + (size_t)(0 * P) * a.plane + base;
-                float err_ = Er[(size_t)pr * a.plane], eri = Er[(size_t)pim * a.plane];
-                imr = (isim ? err_ : -eri) * (float)m / rh;
+                const T *Er = E + (size_t)(0 * P) * a.plane + base;
+                T err_ = Er[(size_t)pr * a.plane], eri = Er[(size_t)pim * a.plane];
+                imr = (isim ? err_ : -eri) * (T)m / rh;
             }
             d = -(rj1 * Ep[a.nzp] - rj * Ep[0]) / (rh * dr) + imr;
             q = (size_t)(2 * P + p) * a.plane + base;
-            bo = B[q]; bn = gap ? 0.f : bo + dt * d;
-            B[q] = bn; Bb[q] = gap ? 0.f : 0.5f * (bo + bn);
+            bo = B[q]; bn = gap ? (T)0 : bo + dt * d;
+            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bo + bn);
         } else {
             // half-r row beyond the wall: not advanced; its average is the value itself
             size_t q = (size_t)(1 * P + p) * a.plane + base;
-            Bb[q] = gap ? 0.f : B[q];
+            Bb[q] = gap ? (T)0 : B[q];
             q = (size_t)(2 * P + p) * a.plane + base;
-            Bb[q] = gap ? 0.f : B[q];
+            Bb[q] = gap ? (T)0 : B[q];
         }
     }
 }
@@ -166,9 +178,14 @@ void launch_faraday(qpic_ctx *c)
 {
     GridArgs a = grid_args(c);
     dim3 grid((a.nzp + FTILE - 1) / FTILE, a.nr + 1);
-    size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
     prof_begin(c);
-    k_faraday<<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Bb, a);
+    if (c->fp64) {
+        size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(double);
+        k_faraday<double><<<grid, FTILE, sm, c->stream>>>(c->E64, c->B64, c->Bb64, a);
+    } else {
+        size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
+        k_faraday<float><<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Bb, a);
+    }
     prof_end(c, KC_FARADAY);
 }
 
@@ -209,24 +226,27 @@ void launch_jdecode(qpic_ctx *c)
 // ---------------------------------------------------------------- J_z filter
 // J_z <- K * J_z along z (symbol [k]_Yee/[k]_B): keeps Gauss's law in the dual
 // form when the deposit satisfies the two-point continuity equation.
-__global__ void __launch_bounds__(JTILE) k_jfilter(const float *__restrict__ Jf, float *__restrict__ Jzf,
+template <typename T>
+__global__ void __launch_bounds__(JTILE) k_jfilter(const T *__restrict__ Jf, T *__restrict__ Jzf,
                                                   GridArgs a, int nk)
 {
-    extern __shared__ float sh2[];
+    extern __shared__ __align__(16) unsigned char shraw2[];
+    T *sh2 = reinterpret_cast<T *>(shraw2);
     const int j = blockIdx.y, p = blockIdx.z;
     const int i0 = blockIdx.x * JTILE;
     const int H = nk - 1, W = JTILE + 2 * H;
-    float *sT = sh2, *sh = sh2 + MAX_TAPS;
-    for (int k = threadIdx.x; k < nk; k += JTILE) sT[k] = a.coef[2 * MAX_L + k];
-    const float *src = Jf + (size_t)(2 * a.nparts + p) * a.plane + (size_t)j * a.nzp;
+    T *sT = sh2, *sh = sh2 + MAX_TAPS;
+    for (int k = threadIdx.x; k < nk; k += JTILE)
+        sT[k] = sizeof(T) == 8 ? (T)a.coef64[2 * MAX_L + k] : (T)a.coef[2 * MAX_L + k];
+    const T *src = Jf + (size_t)(2 * a.nparts + p) * a.plane + (size_t)j * a.nzp;
     for (int k = threadIdx.x; k < W; k += JTILE) sh[k] = src[wrapz(i0 - H + k, a.nzp)];
     __syncthreads();
     const int i = i0 + threadIdx.x;
     if (i >= a.nzp) return;
     const int s = threadIdx.x + H;
-    float acc = sT[0] * sh[s];
+    T acc = sT[0] * sh[s];
     for (int q = 1; q < nk; q++) acc += sT[q] * (sh[s + q] + sh[s - q]);
-    Jzf[(size_t)p * a.plane + (size_t)j * a.nzp + i] = in_gap(i, a) ? 0.f : acc;
+    Jzf[(size_t)p * a.plane + (size_t)j * a.nzp + i] = in_gap(i, a) ? (T)0 : acc;
 }
 
 void launch_jfilter(qpic_ctx *c)
@@ -234,9 +254,15 @@ void launch_jfilter(qpic_ctx *c)
     GridArgs a = grid_args(c);
     int nk = (int)c->taps.size();
     dim3 grid((a.nzp + JTILE - 1) / JTILE, a.nr + 1, a.nparts);
-    size_t sm = (size_t)(MAX_TAPS + JTILE + 2 * (nk - 1)) * sizeof(float);
     prof_begin(c);
-    k_jfilter<<<grid, JTILE, sm, c->stream>>>(c->Jf, c->Jzf, a, nk);
+    if (c->fp64) {
+        size_t sm = (size_t)(MAX_TAPS + JTILE + 2 * (nk - 1)) * sizeof(double);
+        cudaFuncSetAttribute(k_jfilter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_jfilter<double><<<grid, JTILE, sm, c->stream>>>(c->J64, c->Jz64, a, nk);
+    } else {
+        size_t sm = (size_t)(MAX_TAPS + JTILE + 2 * (nk - 1)) * sizeof(float);
+        k_jfilter<float><<<grid, JTILE, sm, c->stream>>>(c->Jf, c->Jzf, a, nk);
+    }
     prof_end(c, KC_JFILTER);
 }
 
@@ -245,18 +271,21 @@ void launch_jfilter(qpic_ctx *c)
 // E_phi: D^B_z B_r - d_r B_z - J_phi;  E_z: (1/r) d_r(r B_phi) - (i m/r) B_r - J_z.
 // Axis: m = 0: E_phi = 0, E_z uses 4 B_phi(dr/2)/dr; m = 1: E_z = 0,
 // d_r B_z(0) = 2 B_z(dr/2)/dr; m >= 2: 0.  Wall: E_phi = E_z = 0.
-__global__ void __launch_bounds__(FTILE) k_ampere(float *__restrict__ E, const float *__restrict__ B,
-                                                 const float *__restrict__ Jf,
-                                                 const float *__restrict__ Jz, GridArgs a)
+template <typename T>
+__global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__restrict__ B,
+                                                 const T *__restrict__ Jf,
+                                                 const T *__restrict__ Jz, GridArgs a)
 {
-    extern __shared__ float sh[];
+    extern __shared__ __align__(16) unsigned char shraw[];
+    T *sh = reinterpret_cast<T *>(shraw);
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * FTILE;
     const int W = FTILE + 2 * a.L;
     const int P = a.nparts;
-    float *sC = sh;                      // [L] C^B
-    float *sBphi = sh + MAX_L, *sBr = sBphi + P * W;
-    for (int k = threadIdx.x; k < a.L; k += FTILE) sC[k] = a.coef[MAX_L + k];
+    T *sC = sh;                          // [L] C^B
+    T *sBphi = sh + MAX_L, *sBr = sBphi + P * W;
+    for (int k = threadIdx.x; k < a.L; k += FTILE)
+        sC[k] = sizeof(T) == 8 ? (T)a.coef64[MAX_L + k] : (T)a.coef[MAX_L + k];
     for (int k = threadIdx.x; k < W; k += FTILE) {
         int col = wrapz(i0 - a.L + k, a.nzp);
         for (int p = 0; p < P; p++) {
@@ -268,8 +297,8 @@ __global__ void __launch_bounds__(FTILE) k_ampere(float *__restrict__ E, const f
     const int i = i0 + threadIdx.x;
     if (i >= a.nzp) return;
     const bool gap = in_gap(i, a);
-    const float dr = a.dr, dz = a.dz, dt = a.dt;
-    const float rj = j * dr, rh = (j + 0.5f) * dr, rl = (j - 0.5f) * dr;
+    const T dr = (T)a.dr64, dz = (T)a.dz64, dt = (T)a.dt64;
+    const T rj = j * dr, rh = (j + (T)0.5) * dr, rl = (j - (T)0.5) * dr;
     const int s = threadIdx.x + a.L;
     const size_t base = (size_t)j * a.nzp + i;
     for (int p = 0; p < P; p++) {
@@ -277,64 +306,64 @@ __global__ void __launch_bounds__(FTILE) k_ampere(float *__restrict__ E, const f
         const bool isim = (p > 0) && !(p & 1);
         const int pr = isim ? p - 1 : p, pim = isim ? p : p + 1;
         // D^B_z of B_phi and B_r at integer i: sum_l C_l (f_{i+l-1/2} - f_{i-l+1/2})
-        float dBphi = 0.f, dBr = 0.f;
+        T dBphi = 0, dBr = 0;
         for (int l = 1; l <= a.L; l++) {
-            float cl = sC[l - 1];
+            T cl = sC[l - 1];
             dBphi += cl * (sBphi[p * W + s + l - 1] - sBphi[p * W + s - l]);
             dBr += cl * (sBr[p * W + s + l - 1] - sBr[p * W + s - l]);
         }
         dBphi /= dz; dBr /= dz;
         // E_r at (i, j+1/2)
         if (j < a.nr) {
-            float imr = 0.f;
+            T imr = 0;
             if (m > 0) {
-                const float *Bz = B + (size_t)(2 * P) * a.plane + base;
-                float bzr = Bz[(size_t)pr * a.plane], bzi = Bz[(size_t)pim * a.plane];
-                imr = (isim ? bzr : -bzi) * (float)m / rh;
+                const T *Bz = B + (size_t)(2 * P) * a.plane + base;
+                T bzr = Bz[(size_t)pr * a.plane], bzi = Bz[(size_t)pim * a.plane];
+                imr = (isim ? bzr : -bzi) * (T)m / rh;
             }
             size_t q = (size_t)(0 * P + p) * a.plane + base;
-            float d = imr - dBphi - Jf[q];
-            E[q] = gap ? 0.f : E[q] + dt * d;
+            T d = imr - dBphi - Jf[q];
+            E[q] = gap ? (T)0 : E[q] + dt * d;
         }
         // E_phi at (i, j)
         {
             size_t q = (size_t)(1 * P + p) * a.plane + base;
-            float v;
+            T v;
             if (j == a.nr || (j == 0 && m != 1)) {
-                v = 0.f;
+                v = 0;
             } else if (j == 0) {
-                const float *Bz = B + (size_t)(2 * P + p) * a.plane + base;
-                float d = dBr - 2.f * Bz[0] / dr - Jf[q];
+                const T *Bz = B + (size_t)(2 * P + p) * a.plane + base;
+                T d = dBr - (T)2 * Bz[0] / dr - Jf[q];
                 v = E[q] + dt * d;
             } else {
-                const float *Bz = B + (size_t)(2 * P + p) * a.plane + base;
-                float d = dBr - (Bz[0] - Bz[-(long long)a.nzp]) / dr - Jf[q];
+                const T *Bz = B + (size_t)(2 * P + p) * a.plane + base;
+                T d = dBr - (Bz[0] - Bz[-(long long)a.nzp]) / dr - Jf[q];
                 v = E[q] + dt * d;
             }
-            E[q] = gap ? 0.f : v;
+            E[q] = gap ? (T)0 : v;
         }
         // E_z at (i+1/2, j)
         {
             size_t q = (size_t)(2 * P + p) * a.plane + base;
             size_t qz = (size_t)p * a.plane + base;
-            float v;
+            T v;
             if (j == a.nr || (j == 0 && m != 0)) {
-                v = 0.f;
+                v = 0;
             } else if (j == 0) {
-                const float *Bp = B + (size_t)(1 * P + p) * a.plane + base;
-                v = E[q] + dt * (4.f * Bp[0] / dr - Jz[qz]);
+                const T *Bp = B + (size_t)(1 * P + p) * a.plane + base;
+                v = E[q] + dt * ((T)4 * Bp[0] / dr - Jz[qz]);
             } else {
-                const float *Bp = B + (size_t)(1 * P + p) * a.plane + base;
-                float imr = 0.f;
+                const T *Bp = B + (size_t)(1 * P + p) * a.plane + base;
+                T imr = 0;
                 if (m > 0) {
-                    const float *Br = B + (size_t)(0 * P) * a.plane + base;
-                    float brr = Br[(size_t)pr * a.plane], bri = Br[(size_t)pim * a.plane];
-                    imr = (isim ? brr : -bri) * (float)m / rj;
+                    const T *Br = B + (size_t)(0 * P) * a.plane + base;
+                    T brr = Br[(size_t)pr * a.plane], bri = Br[(size_t)pim * a.plane];
+                    imr = (isim ? brr : -bri) * (T)m / rj;
                 }
-                float d = (rh * Bp[0] - rl * Bp[-(long long)a.nzp]) / (rj * dr) - imr - Jz[qz];
+                T d = (rh * Bp[0] - rl * Bp[-(long long)a.nzp]) / (rj * dr) - imr - Jz[qz];
                 v = E[q] + dt * d;
             }
-            E[q] = gap ? 0.f : v;
+            E[q] = gap ? (T)0 : v;
         }
     }
 }
@@ -343,23 +372,30 @@ void launch_ampere(qpic_ctx *c)
 {
     GridArgs a = grid_args(c);
     dim3 grid((a.nzp + FTILE - 1) / FTILE, a.nr + 1);
-    size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
-    const float *jz = c->taps.empty() ? c->Jf + (size_t)2 * a.nparts * a.plane : c->Jzf;
     prof_begin(c);
-    k_ampere<<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Jf, jz, a);
+    if (c->fp64) {
+        size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(double);
+        const double *jz = c->taps.empty() ? c->J64 + (size_t)2 * a.nparts * a.plane : c->Jz64;
+        k_ampere<double><<<grid, FTILE, sm, c->stream>>>(c->E64, c->B64, c->J64, jz, a);
+    } else {
+        size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
+        const float *jz = c->taps.empty() ? c->Jf + (size_t)2 * a.nparts * a.plane : c->Jzf;
+        k_ampere<float><<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Jf, jz, a);
+    }
     prof_end(c, KC_AMPERE);
 }
 
 // ---------------------------------------------------------------- window column
-__global__ void k_zero_column(float *E, float *B, float *Bb, float *Jf, float *Jzf, int col,
-                              GridArgs a, int nplanes, int nzf)
+template <typename T>
+__global__ void k_zero_column(T *E, T *B, T *Bb, T *Jf, T *Jzf, int col, GridArgs a, int nplanes,
+                              int nzf)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int pl = blockIdx.y;
     if (j > a.nr) return;
     size_t q = (size_t)pl * a.plane + (size_t)j * a.nzp + col;
-    E[q] = 0.f; B[q] = 0.f; Bb[q] = 0.f; Jf[q] = 0.f;
-    if (pl < nzf) Jzf[q] = 0.f;
+    E[q] = 0; B[q] = 0; Bb[q] = 0; Jf[q] = 0;
+    if (pl < nzf) Jzf[q] = 0;
 }
 
 void launch_zero_column(qpic_ctx *c, long long phys_col)
@@ -368,8 +404,12 @@ void launch_zero_column(qpic_ctx *c, long long phys_col)
     int np = 3 * a.nparts;
     dim3 grid((a.nr + 1 + 127) / 128, np);
     prof_begin(c);
-    k_zero_column<<<grid, 128, 0, c->stream>>>(c->E, c->B, c->Bb, c->Jf, c->Jzf,
-                                               (int)(phys_col % a.nzp), a, np, a.nparts);
+    if (c->fp64)
+        k_zero_column<double><<<grid, 128, 0, c->stream>>>(c->E64, c->B64, c->Bb64, c->J64, c->Jz64,
+                                                           (int)(phys_col % a.nzp), a, np, a.nparts);
+    else
+        k_zero_column<float><<<grid, 128, 0, c->stream>>>(c->E, c->B, c->Bb, c->Jf, c->Jzf,
+                                                          (int)(phys_col % a.nzp), a, np, a.nparts);
     prof_end(c, KC_WINDOW);
 }
 
@@ -418,7 +458,8 @@ __device__ void laser_core(const LaserArgs &L, double z, double r, double t, dou
     *hr = -(exc_r * qr + exc_i * qi) / qq;
 }
 
-__global__ void k_laser(float *E, float *B, GridArgs a, LaserArgs L)
+template <typename T>
+__global__ void k_laser(T *E, T *B, GridArgs a, LaserArgs L)
 {
     const int il = blockIdx.x * blockDim.x + threadIdx.x;     // logical column
     const int j = blockIdx.y;
@@ -431,11 +472,11 @@ __global__ void k_laser(float *E, float *B, GridArgs a, LaserArgs L)
     const double ri = j * L.dr, rh = (j + 0.5) * L.dr;
     double ex, h;
     // value (vr + i vi) * e^{-i psi} added to mode-1 planes of component comp
-    auto add = [&](float *F, int comp, double vr, double vi, bool zero) {
+    auto add = [&](T *F, int comp, double vr, double vi, bool zero) {
         if (zero) return;
         double wr = vr * cp - vi * sp, wi = vr * sp + vi * cp;
-        F[(size_t)(comp * P + 1) * a.plane + base] += (float)wr;
-        F[(size_t)(comp * P + 2) * a.plane + base] += (float)wi;
+        F[(size_t)(comp * P + 1) * a.plane + base] += (T)wr;
+        F[(size_t)(comp * P + 2) * a.plane + base] += (T)wi;
     };
     const bool wall = (j == a.nr);
     // E at t = 0
@@ -466,14 +507,16 @@ void launch_laser(qpic_ctx *c, double a0, double w0, double fwhm, double zc, dou
     L.periodic = c->g.periodic;
     dim3 grid((a.nz + 127) / 128, a.nr + 1);
     prof_begin(c);
-    k_laser<<<grid, 128, 0, c->stream>>>(c->E, c->B, a, L);
+    if (c->fp64) k_laser<double><<<grid, 128, 0, c->stream>>>(c->E64, c->B64, a, L);
+    else k_laser<float><<<grid, 128, 0, c->stream>>>(c->E, c->B, a, L);
     prof_end(c, KC_OTHER);
 }
 
 // ---------------------------------------------------------------- field energy (FP64)
 // 1/2 sum V(r_loc) (|E|^2 + |B|^2) per mode, each component at its own radius,
 // modes m >= 1 counted twice.  Deterministic two-pass reduction.
-__global__ void k_energy_partial(const float *E, const float *B, GridArgs a, double *part)
+template <typename T>
+__global__ void k_energy_partial(const T *E, const T *B, GridArgs a, double *part)
 {
     __shared__ double red[256];
     const int j = blockIdx.y, m = blockIdx.z;
@@ -490,7 +533,7 @@ __global__ void k_energy_partial(const float *E, const float *B, GridArgs a, dou
         size_t base = (size_t)j * a.nzp + col;
         for (int k = 0; k < (m ? 2 : 1); k++) {
             int p = m ? 2 * m - 1 + k : 0;
-            auto v2 = [&](const float *F, int comp) {
+            auto v2 = [&](const T *F, int comp) {
                 double x = F[(size_t)(comp * a.nparts + p) * a.plane + base];
                 return x * x;
             };
@@ -525,7 +568,8 @@ void launch_field_energy(qpic_ctx *c, double *out_modes)
     size_t need = (size_t)nbx * (a.nr + 1) * nm + nm;
     if ((size_t)c->red_cap < need) return;
     prof_begin(c);
-    k_energy_partial<<<grid, 256, 0, c->stream>>>(c->E, c->B, a, c->d_red);
+    if (c->fp64) k_energy_partial<double><<<grid, 256, 0, c->stream>>>(c->E64, c->B64, a, c->d_red);
+    else k_energy_partial<float><<<grid, 256, 0, c->stream>>>(c->E, c->B, a, c->d_red);
     k_sum_ordered<<<1, 32, 0, c->stream>>>(c->d_red, nbx * (a.nr + 1), nm, c->d_red + need - nm);
     prof_end(c, KC_DIAG, 2);
     cudaMemcpyAsync(out_modes, c->d_red + need - nm, nm * sizeof(double), cudaMemcpyDeviceToHost,

@@ -768,6 +768,16 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
     }
 }
 
+// exclusive prefix sum of n ints into out (tmp: >= n/4096 + 2 ints)
+void exclusive_scan(qpic_ctx *c, const int32_t *in, int32_t *out, int32_t *tmp, long long n)
+{
+    const long long per = (long long)SCAN_B * SCAN_I;
+    int nb = (int)((n + per - 1) / per);
+    k_scan_local<<<nb, SCAN_B, 0, c->stream>>>(in, out, tmp, n);
+    k_scan_sums<<<1, SCAN_B, 0, c->stream>>>(tmp, nb, tmp + nb);
+    k_scan_add<<<nb, SCAN_B, 0, c->stream>>>(out, tmp, n);
+}
+
 __global__ void k_set_counts(long long *dcount, const int32_t *total)
 {
     dcount[0] = *total;
@@ -1030,6 +1040,7 @@ __global__ void k_rho(Particles P, long long n, double *out, LoadArgs L, int nm)
 
 void launch_rho(qpic_ctx *c, double *dplanes)
 {
+    if (c->fp64) { fp64_rho(c, dplanes); return; }
     LoadArgs L = load_args(c);
     long long n = c->np;
     size_t sz = (size_t)c->g.nm * 2 * (c->g.nr + 1) * c->g.nz;

@@ -78,6 +78,7 @@ struct qpic_ctx {
     unsigned long long *Jacc = nullptr;
     float *rowf = nullptr;        // [4][nr+1]: J_z, J_r, J_phi(m>=1), J_phi(m=0)
     float *coef = nullptr;        // [cE (MAX_L) | cB (MAX_L) | taps (MAX_TAPS)] FP32
+    double *coef64 = nullptr;     // the same in FP64
     bool j_filtered = false;      // J_z of the last deposit has been filtered
 
     // FP64 fields (plain path)
@@ -88,7 +89,8 @@ struct qpic_ctx {
     long long n_tail = 0;         // particles appended since the last sort (unsorted tail)
     long long *d_count = nullptr; // device: [0] particles in the buffer, [1] of them sorted
     qpic::Particles p, ps;        // live buffers and the sort's second buffer
-    qpic::Particles64 p64;
+    qpic::Particles64 p64, ps64;  // plain FP64 path: live buffers and compaction target
+    int32_t *scan_flag = nullptr, *scan_pos = nullptr, *scan_tmp64 = nullptr;
     double qref = 0.0;            // max |charge| of a particle
     float qscale = 0.f;           // fixed-point scale 2^40 / qref
 
@@ -154,6 +156,7 @@ void launch_load_particles(qpic_ctx *c, long long n, const double *dz_, const do
 void launch_export_particles(qpic_ctx *c, double *dout, long long stride);
 void launch_rho(qpic_ctx *c, double *dplanes);               // nm*2 planes (nr+1)*nz logical
 void launch_particle_sums(qpic_ctx *c, double *out3);        // count, charge, kinetic
+void exclusive_scan(qpic_ctx *c, const int32_t *in, int32_t *out, int32_t *tmp, long long n);
 
 // ---- plain FP64 path (k_fp64.cu) ----
 void fp64_faraday(qpic_ctx *c);
