@@ -65,7 +65,8 @@ enum { QPIC_STAGE_FARADAY = 1, QPIC_STAGE_PARTICLES = 2, QPIC_STAGE_AMPERE = 4,
        QPIC_STAGE_WINDOW = 8, QPIC_STAGE_SORT = 16 };
 
 typedef struct {
-    int32_t nz, nr;        /* logical grid: nz cells along z, nr cells in r (wall at nr dr) */
+    int32_t nz, nr;        /* logical grid: nz cells along z (< ~32000), nr cells in r (wall
+                              at nr dr) */
     int32_t n_modes;       /* M + 1 azimuthal modes (1..4) */
     double dz, dr;
     double dt;             /* <= 0: dt = cfl_frac x the solver's stability limit */
@@ -79,7 +80,7 @@ typedef struct {
     int32_t periodic_z;    /* 1: periodic box; 0: open box (zero fields outside) */
     int32_t moving_window; /* 1: window moves at window_v (needs periodic_z = 0) */
     double window_v;
-    int32_t tile_z, tile_r;   /* particle tile in cells (0: default 16 x 8) */
+    int32_t tile_z, tile_r;   /* particle tile in cells: 16x8 (default), 32x8, 8x8, 16x16, 32x4 */
     int32_t sort_period;      /* steps between particle sorts (0: default 2; a particle moves
                                  < 1 cell per step, so 2 keeps every one inside its tile halo) */
     int32_t track_work;       /* 1: accumulate modal work W0, W1 per particle (Eq. 16) */

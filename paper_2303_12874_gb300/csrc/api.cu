@@ -353,6 +353,8 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     // geometry: circular z buffer, gap wider than the widest stencil for open boxes
     c->TZ = cfg->tile_z > 0 ? cfg->tile_z : 16;
     c->TR = cfg->tile_r > 0 ? cfg->tile_r : 8;
+    if (!gpd_tile_supported(c->TZ, c->TR))
+        return bad(QPIC_EINVAL, "tile_z x tile_r: one of 16x8, 32x8, 8x8, 16x16, 32x4");
     c->halo = 1;
     c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 2;
     FieldGeom &g = c->g;
@@ -361,6 +363,8 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     int reach = std::max({2 * c->L + 2, (int)c->taps.size() + 2, 2 * (c->TZ + 2 * c->halo + 3)});
     g.gap = g.periodic ? 0 : ((reach + c->TZ - 1) / c->TZ) * c->TZ;
     g.nzp = g.nz + g.gap;
+    if (g.nzp >= 32768 || g.nr >= 65536)
+        return bad(QPIC_EINVAL, "grid too large for the packed cell index (nz + gap < 32768, nr < 65536)");
     g.zoff = 0;
     g.plane = (size_t)(g.nr + 1) * g.nzp;
     g.dz = (float)c->dz; g.dr = (float)c->dr; g.dt = (float)c->dt;
@@ -391,6 +395,12 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->nkeys = (long long)c->ntz * c->ntr * c->TZ * c->TR;
     const int nb = (int)((c->nkeys + 1 + 4095) / 4096);
     c->red_cap = std::max(4 * (g.nr + 1) * g.nm + 64, 8 + 3 * 305);
+    if (!c->fp64) {
+        const size_t tw = gpd_tile_words(g.nparts, c->TZ, c->TR) * (size_t)c->ntz * c->ntr;
+        if (!alloc_arr(c, &c->Jtile, tw) || !alloc_arr(c, &c->tstamp, (size_t)c->ntz * c->ntr))
+            return bad(QPIC_ENOMEM, "tile accumulators: device allocation failed");
+        cudaMemsetAsync(c->tstamp, 0xff, (size_t)c->ntz * c->ntr * sizeof(int), c->stream);
+    }
     if (!alloc_arr(c, &c->counts, (size_t)c->nkeys + 1) ||
         !alloc_arr(c, &c->offsets, (size_t)c->nkeys + 1) || !alloc_arr(c, &c->scan_tmp, (size_t)nb + 2) ||
         !alloc_arr(c, &c->d_red, (size_t)c->red_cap))

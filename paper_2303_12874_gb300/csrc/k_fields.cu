@@ -189,40 +189,6 @@ void launch_faraday(qpic_ctx *c)
     prof_end(c, KC_FARADAY);
 }
 
-// ---------------------------------------------------------------- J decode
-// int64 fixed point -> FP32 current with the per-row finite-volume factors,
-// and the accumulator is cleared for the next deposit.
-__global__ void k_jdecode(unsigned long long *__restrict__ Jacc, float *__restrict__ Jf,
-                          const float *__restrict__ rowf, GridArgs a, float inv_qscale, int *err)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const int pl = blockIdx.z;            // plane = comp * nparts + part
-    if (i >= a.nzp) return;
-    const int comp = pl / a.nparts, part = pl % a.nparts;
-    const size_t q = (size_t)pl * a.plane + (size_t)j * a.nzp + i;
-    long long v = (long long)Jacc[q];
-    Jacc[q] = 0ull;
-    if (v > (1ll << 62) || v < -(1ll << 62)) atomicOr(err, 1);     // fixed-point headroom gone
-    float f;
-    if (comp == 2) f = rowf[j];                                   // J_z
-    else if (comp == 0) f = rowf[(a.nr + 1) + j];                  // J_r
-    else f = part == 0 ? rowf[3 * (a.nr + 1) + j] : rowf[2 * (a.nr + 1) + j];  // J_phi
-    // int64 -> float from two 32-bit halves (integer conversions stay off the FP64 pipe)
-    const float fv = __int2float_rn((int)(v >> 32)) * 4294967296.f + __uint2float_rn((unsigned)v);
-    Jf[q] = in_gap(i, a) ? 0.f : fv * inv_qscale * f;
-}
-
-void launch_jdecode(qpic_ctx *c)
-{
-    GridArgs a = grid_args(c);
-    dim3 grid((a.nzp + 255) / 256, a.nr + 1, 3 * a.nparts);
-    prof_begin(c);
-    k_jdecode<<<grid, 256, 0, c->stream>>>(c->Jacc, c->Jf, c->rowf, a, 1.0f / c->qscale,
-                                           c->d_err);
-    prof_end(c, KC_JDECODE);
-}
-
 // ---------------------------------------------------------------- J_z filter
 // J_z <- K * J_z along z (symbol [k]_Yee/[k]_B): keeps Gauss's law in the dual
 // form when the deposit satisfies the two-point continuity equation.

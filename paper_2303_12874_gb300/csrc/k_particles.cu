@@ -35,7 +35,7 @@ struct PArgs {
     size_t plane;
     float dz, dr, dt, inv_dz, inv_dr, R;
     int periodic;
-    int TZ, TR, ntz, ntr, H;
+    int TZ, TR, ntz, ntr, H, lTZ, lTR;
     float qscale;
     int track_work;
 };
@@ -50,6 +50,7 @@ static PArgs pargs(const qpic_ctx *c)
     a.R = (float)(c->g.nr * c->dr);
     a.periodic = c->g.periodic;
     a.TZ = c->TZ; a.TR = c->TR; a.ntz = c->ntz; a.ntr = c->ntr; a.H = c->halo;
+    a.lTZ = __builtin_ctz(c->TZ); a.lTR = __builtin_ctz(c->TR);
     a.qscale = c->qscale;
     a.track_work = c->cfg.track_work;
     return a;
@@ -92,27 +93,59 @@ __device__ __forceinline__ float gsample(const float *E, const float *Bb, const 
 }
 
 // ------------------------------------------------------------ accessors
+// Staged tile of E and Bbar: per (field, component, row, column) node the NP
+// mode parts are packed in V = ceil(NP/4) float4 words, so a gather corner is
+// one (or two) 16-byte shared loads.  Current accumulators: int64 per
+// (component, part, row, column).
+template <int NP, int TZ, int TR>
+struct TileGeom {
+    static constexpr int H = 1;                    // halo of cells around the tile
+    static constexpr int FW = TZ + 2 * H + 2, FR = TR + 2 * H + 2;   // staged fields
+    static constexpr int JW = FW + 1, JR = FR + 1;                   // accumulators
+    static constexpr int V = (NP + 3) / 4;
+    static constexpr int JWORDS = 3 * NP * JW * JR;                   // int64 words
+    static constexpr int JPAD = (JWORDS + 1) & ~1;                    // keeps the float4 tile 16-B aligned
+    static constexpr int FVEC = 2 * 3 * FR * FW * V;                  // float4 words
+    static constexpr int NM = (NP + 1) / 2;
+    static constexpr int QW = 8 + 4 * (NM - 1);                       // words per queued move
+    static constexpr int QCAP = 512;                                  // queued cell-crossing moves
+    static constexpr size_t SMEM =
+        (size_t)JPAD * 8 + (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + 16;
+    static_assert((JPAD * 8) % 16 == 0, "float4 tile alignment");
+};
+
+template <int NP, int TZ, int TR>
 struct SmemAcc {
-    const float *sf;             // [2][3][P][FR][FW]
-    unsigned long long *sJ;      // [3][P][JR][JW]
-    int FW, FR, JW, JR, P;
-    __device__ __forceinline__ float f(int fb, int c, int p, int lj, int li) const
+    using G = TileGeom<NP, TZ, TR>;
+    const float4 *sf;            // [2][3][FR][FW][V]
+    unsigned long long *sJ;      // [3][NP][JR][JW]
+    __device__ __forceinline__ void node(int fb, int c, int lj, int li, float out[NP]) const
     {
-        return sf[((size_t)((fb * 3 + c) * P + p) * FR + lj) * FW + li];
+        const float4 *q = sf + ((size_t)((fb * 3 + c) * G::FR + lj) * G::FW + li) * G::V;
+#pragma unroll
+        for (int v = 0; v < G::V; v++) {
+            const float4 t = q[v];
+            if (4 * v + 0 < NP) out[4 * v + 0] = t.x;
+            if (4 * v + 1 < NP) out[4 * v + 1] = t.y;
+            if (4 * v + 2 < NP) out[4 * v + 2] = t.z;
+            if (4 * v + 3 < NP) out[4 * v + 3] = t.w;
+        }
     }
     __device__ __forceinline__ void jadd(int c, int p, int lj, int li, long long v) const
     {
-        if (v) atomicAdd(&sJ[((size_t)(c * P + p) * JR + lj) * JW + li], (unsigned long long)v);
+        if (v) atomicAdd(&sJ[((size_t)(c * NP + p) * G::JR + lj) * G::JW + li], (unsigned long long)v);
     }
 };
 
+template <int NP>
 struct GlobAcc {
     const float *E, *Bb;
     unsigned long long *J;
     PArgs a;
-    __device__ __forceinline__ float f(int fb, int c, int p, int j, int i) const
+    __device__ __forceinline__ void node(int fb, int c, int j, int i, float out[NP]) const
     {
-        return gsample(E, Bb, a, fb, c, p, j, i);
+#pragma unroll
+        for (int p = 0; p < NP; p++) out[p] = gsample(E, Bb, a, fb, c, p, j, i);
     }
     __device__ __forceinline__ void jadd(int c, int p, int j, int i, long long v) const
     {
@@ -206,11 +239,14 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
             const int hz = hz_of(fb, c), hr = hr_of(fb, c);
             const int i0 = bi + (hz ? ozh : 0), j0 = bj + (hr ? orh : 0);
             const float tz = hz ? wzH : oz, tr = hr ? wrH : orr;
+            float v00[NP], v01[NP], v10[NP], v11[NP];
+            acc.node(fb, c, j0, i0, v00);
+            acc.node(fb, c, j0, i0 + 1, v01);
+            acc.node(fb, c, j0 + 1, i0, v10);
+            acc.node(fb, c, j0 + 1, i0 + 1, v11);
 #pragma unroll
             for (int p = 0; p < NP; p++) {
-                float v00 = acc.f(fb, c, p, j0, i0), v01 = acc.f(fb, c, p, j0, i0 + 1);
-                float v10 = acc.f(fb, c, p, j0 + 1, i0), v11 = acc.f(fb, c, p, j0 + 1, i0 + 1);
-                float lo = v00 + tz * (v01 - v00), hi = v10 + tz * (v11 - v10);
+                float lo = v00[p] + tz * (v01[p] - v00[p]), hi = v10[p] + tz * (v11[p] - v10[p]);
                 F[fb][c][p] = lo + tr * (hi - lo);
             }
         }
@@ -413,113 +449,158 @@ __device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, 
 // faces, J_phi at 4 nodes, each per part) go to the same addresses.  Each
 // contribution is split exactly into hi*2^20 + lo, both halves are summed over
 // the group with one 32-bit reduction each (exact: |sum| < 2^31), and the
-// group's leader adds the int64 total to shared memory.
-template <int NP>
-__device__ __forceinline__ void deposit_fast(const SmemAcc &acc, const PArgs &a, int li, int lj,
-                                             const DepIn<(NP + 1) / 2> &d, unsigned grp, bool leader)
+// group's leader adds the int64 total to shared memory.  Tile geometry is
+// compile-time, so every accumulator offset below is an immediate.
+template <int NP, int TZ, int TR>
+__device__ __forceinline__ void deposit_fast(const SmemAcc<NP, TZ, TR> &acc, const PArgs &a,
+                                             int li, int lj, const DepIn<(NP + 1) / 2> &d,
+                                             unsigned grp, bool leader)
 {
+    using G = TileGeom<NP, TZ, TR>;
     constexpr int NM = (NP + 1) / 2;
-    const float qs = a.qscale;
-    const float Qd = d.Q * qs;
+    constexpr int PL = G::JR * G::JW;                   // words per accumulator plane
+    unsigned long long *base = acc.sJ + lj * G::JW + li;
+    const float Qd = d.Q * a.qscale;
     const float dz_ = d.dzc, dr_ = d.drc;
-    const float Sz[2] = {(1.f - d.oz0) - 0.5f * dz_, d.oz0 + 0.5f * dz_};
-    const float Sr[2] = {(1.f - d.or0) - 0.5f * dr_, d.or0 + 0.5f * dr_};
+    const float Sz0 = (1.f - d.oz0) - 0.5f * dz_, Sz1 = d.oz0 + 0.5f * dz_;
+    const float Sr0 = (1.f - d.or0) - 0.5f * dr_, Sr1 = d.or0 + 0.5f * dr_;
     const float c4 = 0.25f * dz_ * dr_;
     float ebr[NM], ebi[NM];
 #pragma unroll
     for (int m = 0; m < NM; m++) { ebr[m] = d.e0r[m] + 0.5f * d.der[m]; ebi[m] = d.e0i[m] + 0.5f * d.dei[m]; }
-    auto put = [&](int comp, int p, int dj, int di, float v) {
+    auto put = [&](int off, float v) {
         int hi, lo;
         fx_split(v, hi, lo);
         const int shi = (int)__reduce_add_sync(grp, (unsigned)hi);
         const int slo = (int)__reduce_add_sync(grp, (unsigned)lo);
-        const long long tot = ((long long)shi << 20) + slo;
-        if (leader)
-            atomicAdd(&acc.sJ[((size_t)(comp * NP + p) * acc.JR + lj + dj) * acc.JW + li + di],
-                      (unsigned long long)tot);
+        if (leader) atomicAdd(base + off, (unsigned long long)(((long long)shi << 20) + slo));
     };
+    const float Xz0 = Qd * dz_ * Sr0, Xz1 = Qd * dz_ * Sr1;      // J_z at (i0+1/2, j0+b)
+    const float Xr0 = Qd * dr_ * Sz0, Xr1 = Qd * dr_ * Sz1;      // J_r at (i0+a, j0+1/2)
+    put((2 * NP) * PL, Xz0);
+    put((2 * NP) * PL + G::JW, Xz1);
+    put(0, Xr0);
+    put(1, Xr1);
 #pragma unroll
-    for (int b = 0; b < 2; b++) {                      // J_z at (i0+1/2, j0+b)
-        const float X = Qd * dz_ * Sr[b];
-        put(2, 0, b, 0, X);
-#pragma unroll
-        for (int m = 1; m < NM; m++) { put(2, 2 * m - 1, b, 0, X * ebr[m]); put(2, 2 * m, b, 0, X * ebi[m]); }
+    for (int m = 1; m < NM; m++) {
+        put((2 * NP + 2 * m - 1) * PL, Xz0 * ebr[m]);
+        put((2 * NP + 2 * m) * PL, Xz0 * ebi[m]);
+        put((2 * NP + 2 * m - 1) * PL + G::JW, Xz1 * ebr[m]);
+        put((2 * NP + 2 * m) * PL + G::JW, Xz1 * ebi[m]);
+        put((2 * m - 1) * PL, Xr0 * ebr[m]);
+        put((2 * m) * PL, Xr0 * ebi[m]);
+        put((2 * m - 1) * PL + 1, Xr1 * ebr[m]);
+        put((2 * m) * PL + 1, Xr1 * ebi[m]);
     }
+    // J_phi at (i0+a, j0+b): m = 0 from the azimuthal displacement, m >= 1 from
+    // i Q Sbar (e1 - e0)/m, Sbar_ab = Sz_a Sr_b + (dSz_a dSr_b)/4
+    const float S[4] = {Sz0 * Sr0 + c4, Sz1 * Sr0 - c4, Sz0 * Sr1 - c4, Sz1 * Sr1 + c4};
+    const int noff[4] = {0, 1, G::JW, G::JW + 1};
 #pragma unroll
-    for (int a2 = 0; a2 < 2; a2++) {                   // J_r at (i0+a, j0+1/2)
-        const float X = Qd * dr_ * Sz[a2];
-        put(0, 0, 0, a2, X);
+    for (int k = 0; k < 4; k++) {
+        const float QS = Qd * S[k];
+        put(NP * PL + noff[k], QS * d.aphi);
 #pragma unroll
-        for (int m = 1; m < NM; m++) { put(0, 2 * m - 1, 0, a2, X * ebr[m]); put(0, 2 * m, 0, a2, X * ebi[m]); }
-    }
-#pragma unroll
-    for (int a2 = 0; a2 < 2; a2++)
-#pragma unroll
-        for (int b = 0; b < 2; b++) {                  // J_phi at (i0+a, j0+b)
-            const float sb = Sz[a2] * Sr[b] + (a2 == b ? c4 : -c4);
-            const float QS = Qd * sb;
-            put(1, 0, b, a2, QS * d.aphi);
-#pragma unroll
-            for (int m = 1; m < NM; m++) {
-                const float im = 1.f / (float)m;
-                put(1, 2 * m - 1, b, a2, -QS * d.dei[m] * im);
-                put(1, 2 * m, b, a2, QS * d.der[m] * im);
-            }
+        for (int m = 1; m < NM; m++) {
+            const float im = 1.f / (float)m;
+            put((NP + 2 * m - 1) * PL + noff[k], -QS * d.dei[m] * im);
+            put((NP + 2 * m) * PL + noff[k], QS * d.der[m] * im);
         }
+    }
 }
 
 // ------------------------------------------------------------ the GPD kernel
-template <int NP>
-__global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__restrict__ E,
-                                            const float *__restrict__ Bb,
-                                            unsigned long long *__restrict__ J,
-                                            const int32_t *__restrict__ offsets,
-                                            const long long *__restrict__ dcount, PArgs a,
-                                            int ntiles, int tail_chunk)
+// cell index of a particle: (iz_phys << 16) | jr
+__host__ __device__ __forceinline__ int cell_iz(int cell) { return cell >> 16; }
+__host__ __device__ __forceinline__ int cell_jr(int cell) { return cell & 0xFFFF; }
+__host__ __device__ __forceinline__ int make_cell(int iz, int jr) { return (iz << 16) | jr; }
+
+// queued cell-crossing move: local cell, offsets, displacement, charge,
+// azimuthal displacement, then e0/de per mode m >= 1
+template <int NM>
+__device__ __forceinline__ void queue_put(float *q, int li, int lj, const DepIn<NM> &d)
 {
+    q[0] = __int_as_float(li); q[1] = __int_as_float(lj);
+    q[2] = d.oz0; q[3] = d.or0; q[4] = d.dzc; q[5] = d.drc; q[6] = d.Q; q[7] = d.aphi;
+#pragma unroll
+    for (int m = 1; m < NM; m++) {
+        q[8 + 4 * (m - 1)] = d.e0r[m]; q[9 + 4 * (m - 1)] = d.e0i[m];
+        q[10 + 4 * (m - 1)] = d.der[m]; q[11 + 4 * (m - 1)] = d.dei[m];
+    }
+}
+
+template <int NM>
+__device__ __forceinline__ void queue_get(const float *q, int &li, int &lj, DepIn<NM> &d)
+{
+    li = __float_as_int(q[0]); lj = __float_as_int(q[1]);
+    d.oz0 = q[2]; d.or0 = q[3]; d.dzc = q[4]; d.drc = q[5]; d.Q = q[6]; d.aphi = q[7];
+    d.e0r[0] = 1.f; d.e0i[0] = 0.f; d.der[0] = 0.f; d.dei[0] = 0.f;
+#pragma unroll
+    for (int m = 1; m < NM; m++) {
+        d.e0r[m] = q[8 + 4 * (m - 1)]; d.e0i[m] = q[9 + 4 * (m - 1)];
+        d.der[m] = q[10 + 4 * (m - 1)]; d.dei[m] = q[11 + 4 * (m - 1)];
+    }
+}
+
+template <int NP, int TZ, int TR>
+__global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__restrict__ E,
+                                               const float *__restrict__ Bb,
+                                               unsigned long long *__restrict__ J,
+                                               unsigned long long *__restrict__ Jtile,
+                                               int *__restrict__ tstamp, int epoch,
+                                               const int32_t *__restrict__ offsets,
+                                               const long long *__restrict__ dcount, PArgs a,
+                                               int ntiles, int tail_chunk)
+{
+    using G = TileGeom<NP, TZ, TR>;
     constexpr int NM = (NP + 1) / 2;
-    extern __shared__ unsigned long long sraw[];
-    const int H = a.H;
-    const int FW = a.TZ + 2 * H + 2, FR = a.TR + 2 * H + 2;
-    const int JW = FW + 1, JR = FR + 1;
+    extern __shared__ __align__(16) unsigned long long sraw[];
     long long begin, end;
     const bool tile_mode = blockIdx.x < (unsigned)ntiles;
     int tz0 = 0, tr0 = 0;
     if (tile_mode) {
         const int t = blockIdx.x;
-        const int TS = a.TZ * a.TR;
-        begin = offsets[(size_t)t * TS];
-        end = offsets[(size_t)(t + 1) * TS];
+        begin = offsets[(size_t)t * (TZ * TR)];
+        end = offsets[(size_t)(t + 1) * (TZ * TR)];
         if (begin == end) return;
-        tz0 = (t / a.ntr) * a.TZ;
-        tr0 = (t % a.ntr) * a.TR;
+        tz0 = (t / a.ntr) * TZ;
+        tr0 = (t % a.ntr) * TR;
     } else {
         const long long nsorted = dcount[1], np = dcount[0];
         begin = nsorted + (long long)(blockIdx.x - ntiles) * tail_chunk;
         end = min(begin + tail_chunk, np);
         if (begin >= end) return;
     }
-    GlobAcc gacc{E, Bb, J, a};
-    SmemAcc sacc{nullptr, nullptr, FW, FR, JW, JR, NP};
-    const int col0 = tz0 - H - 1;
-    const int row0 = tr0 - H - 1;
-    const bool smem_usable = tile_mode && a.nzp >= 2 * JW;
+    GlobAcc<NP> gacc{E, Bb, J, a};
+    SmemAcc<NP, TZ, TR> sacc{nullptr, nullptr};
+    const int col0 = tz0 - G::H - 1;
+    const int row0 = tr0 - G::H - 1;
+    const bool smem_usable = tile_mode && a.nzp >= 2 * G::JW;
+    float *queue = nullptr;
+    int *qcount = nullptr;
     if (smem_usable) {
         unsigned long long *sJ = sraw;
-        float *sf = reinterpret_cast<float *>(sraw + (size_t)3 * NP * JW * JR);
-        sacc = SmemAcc{sf, sJ, FW, FR, JW, JR, NP};
-        const int nJ = 3 * NP * JW * JR;
-        for (int k = threadIdx.x; k < nJ; k += blockDim.x) sJ[k] = 0ull;
-        // one (plane, row) strip of FW columns per pass of a warp
-        const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, ln = threadIdx.x & 31;
-        for (int strip = warp; strip < 6 * NP * FR; strip += nwarp) {
-            const int lj = strip % FR, pl = strip / FR;
-            const int p = pl % NP, cc = (pl / NP) % 3, fb = pl / (3 * NP);
-            for (int li = ln; li < FW; li += 32) {
-                int col = col0 + li;
-                col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
-                sf[strip * FW + li] = gsample(E, Bb, a, fb, cc, p, row0 + lj, col);
+        float4 *sf = reinterpret_cast<float4 *>(sraw + G::JPAD);
+        queue = reinterpret_cast<float *>(sf + G::FVEC);
+        qcount = reinterpret_cast<int *>(queue + G::QCAP * G::QW);
+        sacc.sJ = sJ;
+        sacc.sf = sf;
+        for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) sJ[k] = 0ull;
+        if (threadIdx.x == 0) *qcount = 0;
+        // one float4 word (up to 4 mode parts of one node) per thread and pass
+        for (int k = threadIdx.x; k < G::FVEC; k += blockDim.x) {
+            const int v = k % G::V, t1 = k / G::V;
+            const int li = t1 % G::FW, t2 = t1 / G::FW, lj = t2 % G::FR, fc = t2 / G::FR;
+            const int c = fc % 3, fb = fc / 3;
+            int col = col0 + li;
+            col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
+            float w4[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int p = 4 * v + e;
+                w4[e] = p < NP ? gsample(E, Bb, a, fb, c, p, row0 + lj, col) : 0.f;
             }
+            sf[k] = make_float4(w4[0], w4[1], w4[2], w4[3]);
         }
         __syncthreads();
     }
@@ -528,19 +609,15 @@ __global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__rest
     const int zoff = (int)a.zoff;
     for (long long base = begin; base < end; base += blockDim.x) {
         const long long idx = base + threadIdx.x;
-        int cell = idx < end ? P.cell[idx] : -1;
+        const int cell = idx < end ? P.cell[idx] : -1;
         bool act = cell >= 0;
-        int iz = 0, jr = 0;
-        if (act) {
-            iz = cell / a.nr;
-            jr = cell - iz * a.nr;
-            if (!a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
-                P.cell[idx] = -1;              // behind the moving window
-                act = false;
-            }
+        const int iz = cell_iz(cell), jr = cell_jr(cell);
+        if (act && !a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
+            P.cell[idx] = -1;                  // behind the moving window
+            act = false;
         }
         PState s;
-        DepIn<NM> d;
+        DepIn<NM> d = {};                      // lanes without a particle reduce zeros
         bool fast = false;
         int li = 0, lj = 0;
         if (act) {
@@ -553,99 +630,216 @@ __global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__rest
             if (smem_usable) {
                 li = wrapn(iz - col0, a.nzp);
                 lj = jr - row0;
-                in_smem = li >= 1 && li <= FW - 2 && lj >= 1 && lj <= FR - 2;
+                in_smem = li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2;
             }
             if (in_smem) {
                 push_move<NP>(sacc, a, li, lj, s, d);
                 fast = same_cell(d);
-                if (!fast) deposit_general<NP>(sacc, a, li, lj, d);
+                // a move across a cell boundary waits in the queue (no divergence here)
+                if (!fast) queue_put<NM>(queue + G::QW * atomicAdd(qcount, 1), li, lj, d);
             } else {
                 push_move<NP>(gacc, a, iz, jr, s, d);
                 deposit_general<NP>(gacc, a, iz, jr, d);
             }
         }
         if (smem_usable) {                     // block-uniform branch
+            // same-cell moves: lanes of one cell reduce together, one atomic per group
             const unsigned fm = __ballot_sync(FULL, fast);
             if (fast) {
                 const unsigned grp = __match_any_sync(fm, (unsigned)((lj << 12) | li));
-                deposit_fast<NP>(sacc, a, li, lj, d, grp, lane == __ffs(grp) - 1);
+                deposit_fast<NP, TZ, TR>(sacc, a, li, lj, d, grp, lane == __ffs(grp) - 1);
             }
         }
         if (act) {
-            int niz = wrapn(iz + s.diz, a.nzp);
-            int njr = jr + s.djr;
-            bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
-            P.cell[idx] = dead ? -1 : niz * a.nr + njr;
+            const int niz = wrapn(iz + s.diz, a.nzp);
+            const int njr = jr + s.djr;
+            const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
+            P.cell[idx] = dead ? -1 : make_cell(niz, njr);
             P.oz[idx] = s.oz; P.orr[idx] = s.orr; P.cph[idx] = s.cph; P.sph[idx] = s.sph;
             P.ux[idx] = s.ux; P.uy[idx] = s.uy; P.uz[idx] = s.uz;
             if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
         }
+        if (smem_usable) {
+            // drain the queue when another round could overflow it, and at the end
+            __syncthreads();
+            const int nq = *qcount;
+            if (nq > G::QCAP - (int)blockDim.x || base + blockDim.x >= end) {
+                for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+                    int qi, qj;
+                    DepIn<NM> dq;
+                    queue_get<NM>(queue + G::QW * k, qi, qj, dq);
+                    deposit_general<NP>(sacc, a, qi, qj, dq);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) *qcount = 0;
+                __syncthreads();
+            }
+        }
     }
     if (smem_usable) {
-        __syncthreads();
-        const int nJ = 3 * NP * JW * JR;
-        for (int k = threadIdx.x; k < nJ; k += blockDim.x) {
-            unsigned long long v = sacc.sJ[k];
-            if (!v) continue;
-            int li = k % JW, t2 = k / JW, lj = t2 % JR, pl = t2 / JR;
-            int j = row0 + lj;
-            if (j < 0 || j > a.nr) continue;
-            int col = wrapn(col0 + li, a.nzp);
-            atomicAdd(&J[(size_t)pl * a.plane + (size_t)j * a.nzp + col], v);
-        }
+        // the tile's accumulators go to its own scratch block with plain stores;
+        // the gather kernel sums the (at most 4) tiles that cover each node
+        unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
+        for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) dst[k] = sacc.sJ[k];
+        if (threadIdx.x == 0) tstamp[blockIdx.x] = epoch;
     }
 }
 
-static size_t gpd_smem(const qpic_ctx *c)
+template <int NP, int TZ, int TR>
+static void gpd_launch(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk)
 {
-    const int H = c->halo, P = c->g.nparts;
-    const int FW = c->TZ + 2 * H + 2, FR = c->TR + 2 * H + 2;
-    return (size_t)3 * P * (FW + 1) * (FR + 1) * 8 + (size_t)6 * P * FW * FR * 4;
+    const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
+    cudaFuncSetAttribute(k_gpd<NP, TZ, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gpd<NP, TZ, TR><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jtile,
+                                                    c->tstamp, c->epoch, c->offsets, c->d_count, a,
+                                                    ntiles, chunk);
+}
+
+template <int NP>
+static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk)
+{
+    if (c->TZ == 16 && c->TR == 8) gpd_launch<NP, 16, 8>(c, a, grid, ntiles, chunk);
+    else if (c->TZ == 32 && c->TR == 8) gpd_launch<NP, 32, 8>(c, a, grid, ntiles, chunk);
+    else if (c->TZ == 8 && c->TR == 8) gpd_launch<NP, 8, 8>(c, a, grid, ntiles, chunk);
+    else if (c->TZ == 16 && c->TR == 16) gpd_launch<NP, 16, 16>(c, a, grid, ntiles, chunk);
+    else if (c->TZ == 32 && c->TR == 4) gpd_launch<NP, 32, 4>(c, a, grid, ntiles, chunk);
+    else return false;
+    return true;
+}
+
+bool gpd_tile_supported(int tz, int tr)
+{
+    return (tz == 16 && tr == 8) || (tz == 32 && tr == 8) || (tz == 8 && tr == 8) ||
+           (tz == 16 && tr == 16) || (tz == 32 && tr == 4);
 }
 
 static const int TAIL_CHUNK = 4096;
 
+size_t gpd_tile_words(int nparts, int tz, int tr)
+{
+    const int FW = tz + 4, FR = tr + 4;
+    return (size_t)3 * nparts * (FW + 1) * (FR + 1);
+}
+
 void launch_gpd(qpic_ctx *c)
 {
+    c->epoch++;
     PArgs a = pargs(c);
     const int ntiles = c->ntz * c->ntr;
     long long tail = c->n_tail;              // particles appended since the last sort
     int ntail = (int)((tail + TAIL_CHUNK - 1) / TAIL_CHUNK);
     int grid = ntiles + ntail;
-    size_t sm = gpd_smem(c);
-    long long *dcount = c->d_count;   // [0] np, [1] nsorted
     prof_begin(c);
     switch (c->g.nparts) {
-    case 1:
-        cudaFuncSetAttribute(k_gpd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_gpd<1><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
-                                               ntiles, TAIL_CHUNK);
-        break;
-    case 3:
-        cudaFuncSetAttribute(k_gpd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_gpd<3><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
-                                               ntiles, TAIL_CHUNK);
-        break;
-    case 5:
-        cudaFuncSetAttribute(k_gpd<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_gpd<5><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
-                                               ntiles, TAIL_CHUNK);
-        break;
-    default:
-        cudaFuncSetAttribute(k_gpd<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_gpd<7><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->offsets, dcount, a,
-                                               ntiles, TAIL_CHUNK);
-        break;
+    case 1: gpd_dispatch_tile<1>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    case 3: gpd_dispatch_tile<3>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    case 5: gpd_dispatch_tile<5>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    default: gpd_dispatch_tile<7>(c, a, grid, ntiles, TAIL_CHUNK); break;
     }
     prof_end(c, KC_GPD);
 }
 
+// ------------------------------------------------------------ current reduction + decode
+// One thread per node of a tile's core (its TZ x TR cells; the last tile row
+// also owns the wall row j = nr).  A node's current is the global-path
+// accumulator plus the word of every neighbouring tile block (3 x 3 candidates,
+// written this step, whose staged region covers the node), summed in a fixed
+// order in int64 and turned into FP32 current with the per-row finite-volume
+// factor.  The global-path accumulator is cleared.
+template <int TZ, int TR>
+__global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
+                                                     const int *__restrict__ tstamp, int epoch,
+                                                     unsigned long long *__restrict__ Jacc,
+                                                     float *__restrict__ Jf,
+                                                     const float *__restrict__ rowf, PArgs a,
+                                                     long long tile_words, float inv_qscale,
+                                                     int tiles_ok, int *err)
+{
+    constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3;
+    const int c = threadIdx.x % TZ, r0 = threadIdx.x / TZ;
+    const int t = blockIdx.x;
+    const int tzi = t / a.ntr, tri = t - tzi * a.ntr;
+    const int tz0 = tzi * TZ, tr0 = tri * TR;
+    if (c >= a.nzp - tz0) return;                          // past the last (partial) column
+    const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
+    const int i = tz0 + c;
+    long long kbase[9];
+    int li[9], ljb[9];
+    bool ok[9];
+#pragma unroll
+    for (int d = 0; d < 9; d++) {
+        const int dz = d / 3 - 1, dr = d % 3 - 1;
+        int kz = tzi + dz;
+        kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
+        const int kr = tri + dr;
+        ok[d] = false;
+        li[d] = 0; ljb[d] = 0; kbase[d] = 0;
+        if (tiles_ok && kr >= 0 && kr < a.ntr) {
+            const int kt = kz * a.ntr + kr;
+            li[d] = wrapn(i - (kz * TZ - H - 1), a.nzp);
+            ljb[d] = tr0 - (kr * TR - H - 1);
+            kbase[d] = (long long)kt * tile_words + li[d];
+            ok[d] = li[d] < JW && tstamp[kt] == epoch;
+        }
+    }
+    int l = i - (int)a.zoff;
+    l = l < 0 ? l + a.nzp : l;
+    const bool gap = l >= a.nz;
+    const int NPL = 3 * a.nparts;
+    for (int r = r0; r < CR; r += TR) {
+        const int j = tr0 + r;
+        for (int pl = 0; pl < NPL; pl++) {
+            const size_t q = (size_t)pl * a.plane + (size_t)j * a.nzp + i;
+            long long v = (long long)Jacc[q];
+            Jacc[q] = 0ull;
+#pragma unroll
+            for (int d = 0; d < 9; d++) {
+                const int lj = ljb[d] + r;
+                if (ok[d] && lj >= 0 && lj < JR)
+                    v += (long long)Jtile[kbase[d] + (long long)pl * (JR * JW) + lj * JW];
+            }
+            if (v > (1ll << 62) || v < -(1ll << 62)) atomicOr(err, 1);     // fixed-point headroom gone
+            const int comp = pl / a.nparts, part = pl - comp * a.nparts;
+            float f;
+            if (comp == 2) f = rowf[j];                                               // J_z
+            else if (comp == 0) f = rowf[(a.nr + 1) + j];                             // J_r
+            else f = part == 0 ? rowf[3 * (a.nr + 1) + j] : rowf[2 * (a.nr + 1) + j]; // J_phi
+            // int64 -> float from two 32-bit halves (integer conversions stay off the FP64 pipe)
+            const float fv = __int2float_rn((int)(v >> 32)) * 4294967296.f + __uint2float_rn((unsigned)v);
+            Jf[q] = gap ? 0.f : fv * inv_qscale * f;
+        }
+    }
+}
+
+template <int TZ, int TR>
+static void jreduce_launch(qpic_ctx *c, const PArgs &a, int tiles_ok)
+{
+    k_jreduce<TZ, TR><<<c->ntz * c->ntr, TZ * TR, 0, c->stream>>>(
+        c->Jtile, c->tstamp, c->epoch, c->Jacc, c->Jf, c->rowf, a,
+        (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err);
+}
+
+void launch_jdecode(qpic_ctx *c)
+{
+    PArgs a = pargs(c);
+    const int JW = c->TZ + 2 * c->halo + 3;
+    const int tiles_ok = c->g.nzp >= 2 * JW ? 1 : 0;
+    prof_begin(c);
+    if (c->TZ == 16 && c->TR == 8) jreduce_launch<16, 8>(c, a, tiles_ok);
+    else if (c->TZ == 32 && c->TR == 8) jreduce_launch<32, 8>(c, a, tiles_ok);
+    else if (c->TZ == 8 && c->TR == 8) jreduce_launch<8, 8>(c, a, tiles_ok);
+    else if (c->TZ == 16 && c->TR == 16) jreduce_launch<16, 16>(c, a, tiles_ok);
+    else jreduce_launch<32, 4>(c, a, tiles_ok);
+    prof_end(c, KC_JDECODE);
+}
+
 // ------------------------------------------------------------ sort
+// tile-major key: tile (tz, tr), then row and column inside the tile (TZ, TR powers of 2)
 __device__ __forceinline__ int sort_key(int cell, const PArgs &a)
 {
-    int iz = cell / a.nr, jr = cell - iz * a.nr;
-    int tzi = iz / a.TZ, tri = jr / a.TR;
-    return ((tzi * a.ntr + tri) * a.TR + (jr - tri * a.TR)) * a.TZ + (iz - tzi * a.TZ);
+    const int iz = cell_iz(cell), jr = cell_jr(cell);
+    const int tzi = iz >> a.lTZ, tri = jr >> a.lTR;
+    return ((((tzi * a.ntr + tri) << a.lTR) + (jr & (a.TR - 1))) << a.lTZ) + (iz & (a.TZ - 1));
 }
 
 // histogram of live particles per key; lanes of a warp that share a key (the
@@ -856,7 +1050,7 @@ __global__ void k_load_plasma(Particles P, PlasmaArgs L, long long ntot, int tra
         double w = n * 2.0 * PI * r * (L.dr / L.pr) * (L.dz / L.pz) / L.pp;
         long long d = base + t;
         int iz = (int)(((il + L.zoff) % L.nzp + L.nzp) % L.nzp);
-        P.cell[d] = w > 0.0 ? iz * L.nr + jr : -1;
+        P.cell[d] = w > 0.0 ? make_cell(iz, jr) : -1;
         P.oz[d] = (float)((a + 0.5) / L.pz);
         P.orr[d] = (float)((b + 0.5) / L.pr);
         P.cph[d] = (float)cos(phi); P.sph[d] = (float)sin(phi);
@@ -930,7 +1124,7 @@ __global__ void k_load_particles(Particles P, long long n, const double *z, cons
         if (ozf >= 1.f) ozf = 0.99999994f;
         if (orf >= 1.f) orf = 0.99999994f;
         int iz = (int)(((il + L.zoff) % L.nzp + L.nzp) % L.nzp);
-        P.cell[i] = (dead || !(w[i] > 0.0)) ? -1 : iz * L.nr + jr;
+        P.cell[i] = (dead || !(w[i] > 0.0)) ? -1 : make_cell(iz, jr);
         P.oz[i] = ozf; P.orr[i] = orf;
         P.cph[i] = (float)cos(phi[i]); P.sph[i] = (float)sin(phi[i]);
         P.ux[i] = (float)ux[i]; P.uy[i] = (float)uy[i]; P.uz[i] = (float)uz[i];
@@ -976,7 +1170,7 @@ __global__ void k_export(Particles P, long long n, double *out, long long stride
         int cell = P.cell[i];
         const bool dead = cell < 0;
         if (dead) cell = 0;
-        int iz = cell / L.nr, jr = cell - iz * L.nr;
+        int iz = cell_iz(cell), jr = cell_jr(cell);
         int il = iz - (int)L.zoff;
         if (il < 0) il += L.nzp;
         out[0 * stride + i] = L.zmin + ((double)il + (double)P.oz[i]) * L.dz;
@@ -1010,7 +1204,7 @@ __global__ void k_rho(Particles P, long long n, double *out, LoadArgs L, int nm)
          i += (long long)gridDim.x * blockDim.x) {
         int cell = P.cell[i];
         if (cell < 0) continue;
-        int iz = cell / L.nr, jr = cell - iz * L.nr;
+        int iz = cell_iz(cell), jr = cell_jr(cell);
         int il = iz - (int)L.zoff;
         if (il < 0) il += L.nzp;
         double oz = P.oz[i], orr = P.orr[i], Q = -(double)P.w[i];

@@ -9,7 +9,7 @@
 //   zero columns wider than every stencil, so stencils that reach past either
 //   end read zeros; a periodic box has gap = 0 and wraps.  A moving window only
 //   advances zoff, zeroes the column that left and fills the new front one.
-//   Particles: structure of arrays, 36 B each: cell = iz_phys*nr + jr (int32,
+//   Particles: structure of arrays, 36 B each: cell = (iz_phys << 16) | jr (int32,
 //   -1 = dead), oz, or in [0,1) (offsets in the cell), cos phi, sin phi,
 //   ux, uy, uz, w (float); optional W0, W1 (modal work, Eq. 16).
 //   Current: int64 fixed point per plane, value = round(X * qscale) where X is
@@ -75,7 +75,10 @@ struct qpic_ctx {
 
     // FP32 fields
     float *E = nullptr, *B = nullptr, *Bb = nullptr, *Jf = nullptr, *Jzf = nullptr;
-    unsigned long long *Jacc = nullptr;
+    unsigned long long *Jacc = nullptr;   // global-path deposits (int64 atomics)
+    unsigned long long *Jtile = nullptr;  // per-tile accumulator blocks
+    int *tstamp = nullptr;                // epoch at which each tile block was written
+    int epoch = 0;
     float *rowf = nullptr;        // [4][nr+1]: J_z, J_r, J_phi(m>=1), J_phi(m=0)
     float *coef = nullptr;        // [cE (MAX_L) | cB (MAX_L) | taps (MAX_TAPS)] FP32
     double *coef64 = nullptr;     // the same in FP64
@@ -148,6 +151,8 @@ void launch_field_energy(qpic_ctx *c, double *out_modes);   // host out[n_modes]
 
 // ---- kernel launchers (k_particles.cu) ----
 void launch_gpd(qpic_ctx *c);
+bool gpd_tile_supported(int tile_z, int tile_r);
+size_t gpd_tile_words(int nparts, int tile_z, int tile_r);   // accumulator words per tile
 void launch_sort(qpic_ctx *c);
 int launch_load_plasma(qpic_ctx *c, long long first_logical_col, int ncols, bool append);
 void launch_load_particles(qpic_ctx *c, long long n, const double *dz_, const double *dr_,
