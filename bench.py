@@ -96,6 +96,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _measured_traffic(workload, kernel_rev):
+    """DRAM bytes per k_gpd launch from the committed ncu summary, when it was
+    taken on this workload with this kernel revision; else None."""
+    path = os.path.join(ROOT, "profiles", "gpd_%s_dram_traffic.md" % workload)
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("|"):
+            k, _, v = line.partition(":")
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_rev") != kernel_rev or kv.get("workload") != workload:
+        return None
+    try:
+        return int(kv["bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -237,15 +256,7 @@ def run_ours(args, w):
     if not hbm:
         hbm, peak_src = 6800.0, "fallback"
     achieved = gpd_bytes / (gpd_avg / 1e3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "gpd_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tr = json.load(open(tpath))
-            if tr.get("workload") == args.workload and tr.get("kernel_rev") == q.KERNEL_REV:
-                traffic = tr["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic = _measured_traffic(args.workload, q.KERNEL_REV)
 
     # ---- end to end through the C ABI with host buffers (rank-local)
     e2e = None
@@ -341,7 +352,7 @@ def run_ours(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2_lwfa")

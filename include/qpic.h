@@ -219,6 +219,20 @@ qpic_status qpic_get_particles_raw(qpic_ctx *ctx, double *out, int64_t capacity,
  * [6..6+M] field energy per mode, then the overflow flag. */
 qpic_status qpic_get_diag(qpic_ctx *ctx, double *out, int32_t count);
 
+/* Gauss's law residual per mode in the dual form of Eq. 10: out[2m] = L2 norm
+ * over nodes of div_B E_m - (rho_e + rho_ion)_m, out[2m+1] = L2 norm of the net
+ * charge density (rho_e + rho_ion)_m, where rho_ion = -rho_e at the last particle
+ * load (a fixed neutralising background) and div_B uses the finite-volume
+ * radial divergence with D^B_z in z.  Conductor nodes and the m >= 1 axis node
+ * are left out.  QPIC_ESTATE with a moving window (the background would move). */
+qpic_status qpic_gauss_residual(qpic_ctx *ctx, double *out, int32_t count);
+
+/* Energy spectrum of the electrons: weights[k] = sum of w over particles with
+ * kinetic energy (gamma - 1) 0.511 MeV in [edges_mev[k], edges_mev[k+1]),
+ * k < nbins (edges strictly increasing, nbins <= 4096).  Weights are summed in
+ * int64 fixed point, so the result does not depend on particle order. */
+qpic_status qpic_spectrum(qpic_ctx *ctx, const double *edges_mev, int32_t nbins, double *weights);
+
 /* Number of CUDA kernels this context has launched so far. */
 qpic_status qpic_launch_count(const qpic_ctx *ctx, int64_t *n);
 

@@ -102,6 +102,10 @@ def _declare(L):
     L.qpic_profile.argtypes = [_P, _I, _I]
     L.qpic_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
     L.qpic_charge_density_noalloc.argtypes = [_P, _I, _D, _D]
+    L.qpic_gauss_residual.argtypes = [_P, _D, _I]
+    L.qpic_gauss_residual.restype = ctypes.c_int
+    L.qpic_spectrum.argtypes = [_P, _D, _I, _D]
+    L.qpic_spectrum.restype = ctypes.c_int
     L.qpic_charge_density_noalloc.restype = ctypes.c_int
     L.qpic_launch_count.restype = ctypes.c_int
     L.qpic_kernel_times.argtypes = [_P, _I, _D, ctypes.POINTER(ctypes.c_int64),
@@ -331,6 +335,18 @@ class Sim:
         return {"time": v[0], "steps": int(v[1]), "shifts": int(v[2]), "particles": int(v[3]),
                 "charge": v[4], "kinetic": v[5], "field_energy": list(v[6:6 + self.nm]),
                 "overflow": bool(v[6 + self.nm])}
+
+    def gauss_residual(self):
+        """per mode (|div_B E - rho_net|, |rho_net|) L2 norms"""
+        v = np.zeros(2 * self.nm)
+        self._check(self.L.qpic_gauss_residual(self.h, _dp(v), len(v)), "gauss_residual")
+        return [(v[2 * m], v[2 * m + 1]) for m in range(self.nm)]
+
+    def spectrum(self, edges_mev):
+        e = np.ascontiguousarray(edges_mev, dtype=np.float64)
+        out = np.zeros(len(e) - 1)
+        self._check(self.L.qpic_spectrum(self.h, _dp(e), len(out), _dp(out)), "spectrum")
+        return out
 
     def profile(self, enable=True, reset=True):
         self._check(self.L.qpic_profile(self.h, int(enable), int(reset)), "profile")

@@ -230,6 +230,15 @@ long long live_count(qpic_ctx *c)
     return n;
 }
 
+// fixed ion background: minus the electron density at load time
+void record_ions(qpic_ctx *c)
+{
+    const size_t n = (size_t)c->g.nm * 2 * (c->g.nr + 1) * c->g.nz;
+    if (!c->rho_ion && !alloc_arr(c, &c->rho_ion, n)) return;
+    launch_rho(c, c->rho_ion);
+    scale_buffer(c, c->rho_ion, n, -1.0);
+}
+
 }  // namespace
 
 namespace qpic {
@@ -522,11 +531,13 @@ qpic_status qpic_load_plasma(qpic_ctx *c, double n0, double z_start, double ramp
     if (c->fp64) {
         if (!fp64_load_plasma(c, 0, c->g.nz, false)) return fail(c, QPIC_ECAPACITY, "capacity");
         fp64_compact(c);
+        record_ions(c);
         return cuda_check(c, "load_plasma");
     }
     if (!launch_load_plasma(c, 0, c->g.nz, false)) return fail(c, QPIC_ECAPACITY, "capacity");
     launch_sort(c);
     live_count(c);
+    record_ions(c);
     return cuda_check(c, "load_plasma");
 }
 
@@ -554,6 +565,7 @@ qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const d
                             tmp + 6 * n);
         cudaStreamSynchronize(c->stream);
         if (tmp) dfree(c, tmp);
+        record_ions(c);
         return cuda_check(c, "load_particles");
     }
     launch_load_particles(c, n, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n, tmp + 5 * n,
@@ -562,6 +574,7 @@ qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const d
     cudaStreamSynchronize(c->stream);
     if (tmp) dfree(c, tmp);
     live_count(c);
+    record_ions(c);
     return cuda_check(c, "load_particles");
 }
 
@@ -784,6 +797,60 @@ qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)
     v[6 + nm] = (e & 1) ? 1.0 : 0.0;
     for (int k = 0; k < count && k < (int)v.size(); k++) out[k] = v[k];
     return cuda_check(c, "get_diag");
+}
+
+qpic_status qpic_gauss_residual(qpic_ctx *c, double *out, int32_t count)
+{
+    if (!c || !out) return QPIC_EINVAL;
+    if (c->cfg.moving_window) return fail(c, QPIC_ESTATE, "gauss_residual: ion background moves with the window");
+    if (!c->rho_ion) return fail(c, QPIC_ESTATE, "gauss_residual: no particles loaded");
+    const int nm = c->g.nm;
+    const size_t n = (size_t)nm * 2 * (c->g.nr + 1) * c->g.nz;
+    double *rho = nullptr, *scr = nullptr;
+    const size_t nscr = (size_t)2 * 4 * (c->g.nr + 1) * nm + 2 * nm;
+    if (!alloc_arr(c, &rho, n) || !alloc_arr(c, &scr, nscr)) {
+        dfree(c, rho);
+        return fail(c, QPIC_ENOMEM, "gauss_residual buffers");
+    }
+    launch_rho(c, rho);
+    std::vector<double> h(2 * nm);
+    launch_gauss(c, rho, c->rho_ion, scr, h.data());
+    dfree(c, rho);
+    dfree(c, scr);
+    for (int k = 0; k < 2 * nm && k < count; k++) out[k] = std::sqrt(h[k]);
+    return cuda_check(c, "gauss_residual");
+}
+
+qpic_status qpic_spectrum(qpic_ctx *c, const double *edges_mev, int32_t nbins, double *weights)
+{
+    if (!c || !edges_mev || !weights || nbins < 1 || nbins > 4096) return fail(c, QPIC_EINVAL, "spectrum arguments");
+    for (int k = 0; k < nbins; k++)
+        if (!(edges_mev[k + 1] > edges_mev[k])) return fail(c, QPIC_EINVAL, "spectrum: edges must increase");
+    const double wmax = c->fp64 ? 0.0 : c->qref;
+    double *de = nullptr;
+    unsigned long long *dh = nullptr;
+    if (!alloc_arr(c, &de, (size_t)nbins + 1) || !alloc_arr(c, &dh, (size_t)nbins)) {
+        dfree(c, de);
+        return fail(c, QPIC_ENOMEM, "spectrum buffers");
+    }
+    cudaMemcpyAsync(de, edges_mev, (nbins + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    // weights in int64 fixed point at 2^32 per largest weight
+    double wref = wmax;
+    if (c->fp64 || !(wref > 0)) {
+        double s3[3];
+        if (c->fp64) fp64_particle_sums(c, s3); else launch_particle_sums(c, s3);
+        wref = s3[0] > 0 ? std::fabs(s3[1]) / s3[0] * 64.0 : 1.0;    // mean weight x 64
+    }
+    const double wscale = 4294967296.0 / wref;
+    if (c->fp64) fp64_spectrum(c, de, nbins, wscale, dh);
+    else launch_spectrum(c, de, nbins, wscale, dh);
+    std::vector<unsigned long long> h(nbins);
+    cudaMemcpyAsync(h.data(), dh, nbins * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    dfree(c, de);
+    dfree(c, dh);
+    for (int k = 0; k < nbins; k++) weights[k] = (double)h[k] / wscale;
+    return cuda_check(c, "spectrum");
 }
 
 qpic_status qpic_profile(qpic_ctx *c, int32_t enable, int32_t reset)

@@ -544,3 +544,106 @@ void launch_field_energy(qpic_ctx *c, double *out_modes)
 }
 
 }  // namespace qpic
+
+namespace qpic {
+
+// ---------------------------------------------------------------- Gauss residual
+// R_m(i,j) = div_B E_m - (rho_e + rho_ion)_m with the finite-volume divergence
+// (r_{j+1/2} E_r(j+1/2) - r_{j-1/2} E_r(j-1/2))/(r_j dr) + (i m/r_j) E_phi + D^B_z E_z
+// (4 E_r(dr/2)/dr on the axis for m = 0).  Nodes on the conductor and the
+// m >= 1 axis node are excluded.  Per mode: sum |R|^2 and sum |rho_net|^2.
+// rho planes: [nm][2][nr+1][nz] in logical order.
+template <typename T>
+__global__ void k_gauss_partial(const T *E, const double *rho_e, const double *rho_ion, GridArgs a,
+                                int nm, double *part)
+{
+    __shared__ double s0[256], s1[256];
+    const int j = blockIdx.y, m = blockIdx.z;
+    const int nz = a.nz;
+    double sr = 0.0, sq = 0.0;
+    const double dr = a.dr64, dz = a.dz64;
+    for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < nz; il += gridDim.x * blockDim.x) {
+        if (j >= a.nr || (j == 0 && m > 0)) break;
+        const int col = wrapz(il + (int)a.zoff, a.nzp);
+        double dre = 0.0, dim = 0.0;
+        for (int q = 0; q < (m ? 2 : 1); q++) {
+            const int p = m ? 2 * m - 1 + q : 0;
+            const T *Er = E + (size_t)(0 * a.nparts + p) * a.plane;
+            const T *Ez = E + (size_t)(2 * a.nparts + p) * a.plane;
+            double v;
+            if (j == 0) {
+                v = 4.0 * (double)Er[col] / dr;
+            } else {
+                const double rp = (j + 0.5) * dr, rm = (j - 0.5) * dr, rj = j * dr;
+                v = (rp * (double)Er[(size_t)j * a.nzp + col] - rm * (double)Er[(size_t)(j - 1) * a.nzp + col]) /
+                    (rj * dr);
+            }
+            double dzv = 0.0;
+            for (int l = 1; l <= a.L; l++) {
+                const double cl = a.coef64[MAX_L + l - 1];
+                dzv += cl * ((double)Ez[(size_t)j * a.nzp + wrapz(col + l - 1, a.nzp)] -
+                             (double)Ez[(size_t)j * a.nzp + wrapz(col - l, a.nzp)]);
+            }
+            v += dzv / dz;
+            if (q == 0) dre = v; else dim = v;
+        }
+        if (m > 0 && j > 0) {
+            // (i m / r_j) E_phi
+            const T *Epr = E + (size_t)(1 * a.nparts + 2 * m - 1) * a.plane;
+            const T *Epi = E + (size_t)(1 * a.nparts + 2 * m) * a.plane;
+            const double rj = j * dr;
+            dre += -m * (double)Epi[(size_t)j * a.nzp + col] / rj;
+            dim += m * (double)Epr[(size_t)j * a.nzp + col] / rj;
+        }
+        const size_t qr = ((size_t)(2 * m) * (a.nr + 1) + j) * nz + il;
+        const size_t qi = ((size_t)(2 * m + 1) * (a.nr + 1) + j) * nz + il;
+        const double nre = rho_e[qr] + rho_ion[qr], nim = rho_e[qi] + rho_ion[qi];
+        const double rre = dre - nre, rim = dim - nim;
+        sr += rre * rre + rim * rim;
+        sq += nre * nre + nim * nim;
+    }
+    s0[threadIdx.x] = sr; s1[threadIdx.x] = sq;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) { s0[threadIdx.x] += s0[threadIdx.x + w]; s1[threadIdx.x] += s1[threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const size_t k = ((size_t)m * gridDim.y + j) * gridDim.x + blockIdx.x;
+        part[2 * k] = s0[0];
+        part[2 * k + 1] = s1[0];
+    }
+}
+
+__global__ void k_gauss_final(const double *part, int per_mode, int nm, double *out)
+{
+    const int m = threadIdx.x;
+    if (m >= nm) return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int k = 0; k < per_mode; k++) {
+        a0 += part[2 * ((size_t)m * per_mode + k)];
+        a1 += part[2 * ((size_t)m * per_mode + k) + 1];
+    }
+    out[2 * m] = a0;
+    out[2 * m + 1] = a1;
+}
+
+// out[2m] = sum |R_m|^2, out[2m+1] = sum |rho_net,m|^2 (host); scratch >= 2*4*(nr+1)*nm + 2*nm doubles
+void launch_gauss(qpic_ctx *c, const double *rho_e, const double *rho_ion, double *scratch,
+                  double *out_host)
+{
+    GridArgs a = grid_args(c);
+    const int nm = c->g.nm, nbx = 4;
+    dim3 grid(nbx, a.nr + 1, nm);
+    prof_begin(c);
+    if (c->fp64) k_gauss_partial<double><<<grid, 256, 0, c->stream>>>(c->E64, rho_e, rho_ion, a, nm, scratch);
+    else k_gauss_partial<float><<<grid, 256, 0, c->stream>>>(c->E, rho_e, rho_ion, a, nm, scratch);
+    const int per = nbx * (a.nr + 1);
+    k_gauss_final<<<1, 32, 0, c->stream>>>(scratch, per, nm, scratch + (size_t)2 * per * nm);
+    prof_end(c, KC_DIAG, 2);
+    cudaMemcpyAsync(out_host, scratch + (size_t)2 * per * nm, 2 * nm * sizeof(double),
+                    cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace qpic

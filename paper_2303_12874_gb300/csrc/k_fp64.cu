@@ -451,6 +451,37 @@ void fp64_rho(qpic_ctx *c, double *dplanes)
     if (n > 0) k_rho64<<<nblk, 256, 0, c->stream>>>(c->p64, n, dplanes, a);
 }
 
+__global__ void k_spectrum64(Particles64 P, long long n, const double *edges, int nb, double wscale,
+                             unsigned long long *out)
+{
+    extern __shared__ unsigned long long hist[];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = 0ull;
+    __syncthreads();
+    const double mec2 = 0.51099895;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double w = P.w[i];
+        if (w == 0.0) continue;
+        const double u2 = P.ux[i] * P.ux[i] + P.uy[i] * P.uy[i] + P.uz[i] * P.uz[i];
+        const double e = u2 / (1.0 + sqrt(1.0 + u2)) * mec2;
+        if (e < edges[0] || e >= edges[nb]) continue;
+        int lo = 0, hi = nb;
+        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (e >= edges[mid]) lo = mid; else hi = mid; }
+        atomicAdd(&hist[lo], (unsigned long long)__double2ll_rn(w * wscale));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+        if (hist[k]) atomicAdd(&out[k], hist[k]);
+}
+
+void fp64_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale, unsigned long long *out)
+{
+    cudaMemsetAsync(out, 0, nb * sizeof(unsigned long long), c->stream);
+    if (c->np > 0)
+        k_spectrum64<<<152 * 2, 256, nb * sizeof(unsigned long long), c->stream>>>(c->p64, c->np, edges,
+                                                                                   nb, wscale, out);
+}
+
 __global__ void k_psums64(Particles64 P, long long n, double *part)
 {
     __shared__ double s0[256], s1[256], s2[256];

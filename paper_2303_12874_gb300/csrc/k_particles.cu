@@ -1244,6 +1244,54 @@ void launch_rho(qpic_ctx *c, double *dplanes)
     if (n > 0) k_rho<<<nblk, 256, 0, c->stream>>>(c->p, n, dplanes, L, c->g.nm);
 }
 
+__global__ void k_scale(double *buf, size_t n, double s)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        buf[i] *= s;
+}
+
+void scale_buffer(qpic_ctx *c, double *buf, size_t n, double s)
+{
+    k_scale<<<152 * 4, 256, 0, c->stream>>>(buf, n, s);
+}
+
+// ------------------------------------------------------------ energy spectrum
+// histogram of the kinetic energy (gamma - 1) m c^2 in MeV, weighted by w; each
+// weight is counted in int64 fixed point (w * 2^32 / w_max) so that the result
+// does not depend on the order of the additions.
+__global__ void k_spectrum(Particles P, const long long *dcount, const double *edges, int nb,
+                           double wscale, unsigned long long *out)
+{
+    extern __shared__ unsigned long long hist[];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = 0ull;
+    __syncthreads();
+    const long long n = dcount[0];
+    const double mec2 = 0.51099895;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (P.cell[i] < 0) continue;
+        const float ux = P.ux[i], uy = P.uy[i], uz = P.uz[i];
+        const float u2 = ux * ux + uy * uy + uz * uz;
+        const double e = (double)(u2 / (1.f + sqrtf(1.f + u2))) * mec2;
+        if (e < edges[0] || e >= edges[nb]) continue;
+        int lo = 0, hi = nb;                                  // edges[lo] <= e < edges[hi]
+        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (e >= edges[mid]) lo = mid; else hi = mid; }
+        atomicAdd(&hist[lo], (unsigned long long)__double2ll_rn((double)P.w[i] * wscale));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+        if (hist[k]) atomicAdd(&out[k], hist[k]);
+}
+
+void launch_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale, unsigned long long *out)
+{
+    cudaMemsetAsync(out, 0, nb * sizeof(unsigned long long), c->stream);
+    prof_begin(c);
+    k_spectrum<<<152 * 2, 256, nb * sizeof(unsigned long long), c->stream>>>(c->p, c->d_count, edges,
+                                                                             nb, wscale, out);
+    prof_end(c, KC_DIAG);
+}
+
 // ------------------------------------------------------------ particle sums
 __global__ void k_psums_partial(Particles P, const long long *dcount, double *part)
 {

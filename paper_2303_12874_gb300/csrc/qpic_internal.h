@@ -110,6 +110,7 @@ struct qpic_ctx {
 
     // device scratch
     int *d_err = nullptr;         // error word: bit 0 overflow, bit 1 capacity
+    double *rho_ion = nullptr;    // fixed ion background -rho_e at plasma load, [nm][2][nr+1][nz]
     double *d_red = nullptr;      // reduction scratch
     int red_cap = 0;
 
@@ -148,6 +149,10 @@ void launch_zero_column(qpic_ctx *c, long long phys_col);
 void launch_laser(qpic_ctx *c, double a0, double w0, double fwhm, double zc, double zf,
                   double psi);
 void launch_field_energy(qpic_ctx *c, double *out_modes);   // host out[n_modes]
+void launch_gauss(qpic_ctx *c, const double *rho_e, const double *rho_ion, double *scratch,
+                  double *out_host);
+void launch_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale,
+                     unsigned long long *out);
 
 // ---- kernel launchers (k_particles.cu) ----
 void launch_gpd(qpic_ctx *c);
@@ -177,6 +182,8 @@ void fp64_export_particles(qpic_ctx *c, double *dout, long long stride);
 void fp64_compact(qpic_ctx *c);
 void fp64_rho(qpic_ctx *c, double *dplanes);
 void fp64_particle_sums(qpic_ctx *c, double *out3);
+void fp64_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale, unsigned long long *out);
+void scale_buffer(qpic_ctx *c, double *buf, size_t n, double s);
 void fp64_field_energy(qpic_ctx *c, double *out_modes);
 
 // profiling helpers (api.cu)
