@@ -135,6 +135,52 @@ def _init_state(sim, w):
     sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
 
 
+def batch_scan(q, torch, stream, nruns, steps, seed=5):
+    """Parameter scan of independent periodic runs (grids 256-1024 x 32-128,
+    n 0.003-0.02, a0 1-4, ppc 8/16/32; run k draws from a generator seeded
+    (seed, k)).  The same runs are stepped one after another, then together as
+    one graph-launched batch.  Returns aggregate particle-steps/s of both."""
+    sims, npart = [], []
+    for k in range(nruns):
+        rng = np.random.default_rng([seed, k])
+        nz = int(rng.integers(256, 1025)) // 16 * 16
+        nr = int(rng.integers(32, 129))
+        n0 = float(rng.uniform(0.003, 0.02))
+        a0 = float(rng.uniform(1.0, 4.0))
+        ppc = [(2, 2, 2), (2, 2, 4), (2, 2, 8)][int(rng.integers(0, 3))]
+        sim = q.Sim(nz, nr, 0.2, 0.5, stream=stream, seed=seed * 1000 + k)
+        sim.load_plasma(n0, 0.0, 0.0, ppc)
+        zc = 0.5 * nz * 0.2
+        sim.add_laser(a0, 8.0, 15.0, zc, zc)
+        sims.append(sim)
+        npart.append(sim.diag()["particles"])
+    total = float(sum(npart))
+    for sm in sims:
+        sm.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sm in sims:
+        sm.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    batch = q.Batch(sims, stream=stream)
+    batch.step(batch.cycle)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(steps - steps % batch.cycle)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bat_ms = e0.elapsed_time(e1)
+    batch.close()
+    for sm in sims:
+        sm.close()
+    return {"runs": nruns, "particles": int(total), "steps": steps,
+            "sequential": total * steps / (seq_ms / 1e3), "batched_graph": total * steps / (bat_ms / 1e3),
+            "speedup": seq_ms / bat_ms, "unit": "particle-steps/s"}
+
+
 def oracle_sample(w, dt, nz_sample, steps):
     """The FP64 oracle, as it stands, on a z-slab of the workload: the same
     nr, dz, dr, dt, plasma and ppc over nz_sample columns (periodic).  Returns
@@ -311,6 +357,11 @@ def run_ours(args, w):
                 "dtype": "f64", "note": "one thread per particle, FP64 atomics, no tiles or sort"}
         s64.close()
 
+    # ---- optional: batched parameter scan (independent runs, one graph launch per cycle)
+    batch = None
+    if args.batch_runs > 0:
+        batch = batch_scan(q, torch, stream, args.batch_runs, args.batch_steps)
+
     # ---- CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -340,6 +391,7 @@ def run_ours(args, w):
                          "peak_source": peak_src + " (hbm_gbs, burst)",
                          "algorithmic_bytes_per_launch": gpd_bytes, "traffic": traffic},
             "fp64_gpu_path": fp64,
+            "batch_scan": batch,
             "fp32_over_fp64": (value / ws / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         }
@@ -363,6 +415,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--batch-runs", type=int, default=0)
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

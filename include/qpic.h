@@ -243,6 +243,28 @@ qpic_status qpic_profile(qpic_ctx *ctx, int32_t enable, int32_t reset);
 qpic_status qpic_kernel_times(qpic_ctx *ctx, int32_t n, double *ms, int64_t *launches,
                               const char **names, int32_t *n_classes);
 
+/* Batches: many independent runs (for example a parameter scan) advanced by
+ * one CUDA graph launch per cycle.  qpic_batch_create captures one cycle of
+ * 2 x `sort_period` full steps of every run (a sort swaps the particle
+ * buffers, so a cycle holds two sorts and every replay starts from the
+ * buffers the graph was recorded with) -- each run on its own stream, forked
+ * from and joined to cuda_stream -- into a single graph; the runs are parallel
+ * branches, so uneven runs overlap on the GPU and launch costs are paid once
+ * per cycle.  cuda_stream NULL: the batch uses a stream of its own (the legacy
+ * default stream cannot be captured).  Runs must use the FP32 path, a periodic box (no moving window),
+ * one common sort period, and profiling off; each is first brought to a cycle
+ * boundary.  The contexts stay owned by the caller and must outlive the batch;
+ * do not step them individually while the batch exists.
+ * qpic_batch_step: nsteps must be a multiple of qpic_batch_cycle(); it first
+ * waits for the runs' own streams, then synchronises cuda_stream and checks
+ * every run's error word. */
+typedef struct qpic_batch qpic_batch;
+qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_stream, qpic_batch **out);
+qpic_status qpic_batch_step(qpic_batch *batch, int32_t nsteps);
+int32_t qpic_batch_cycle(const qpic_batch *batch);
+const char *qpic_batch_last_error(const qpic_batch *batch);
+void qpic_batch_destroy(qpic_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,16 @@ def _declare(L):
     L.qpic_profile.argtypes = [_P, _I, _I]
     L.qpic_launch_count.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
     L.qpic_charge_density_noalloc.argtypes = [_P, _I, _D, _D]
+    L.qpic_batch_create.argtypes = [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(_P)]
+    L.qpic_batch_create.restype = ctypes.c_int
+    L.qpic_batch_step.argtypes = [_P, _I]
+    L.qpic_batch_step.restype = ctypes.c_int
+    L.qpic_batch_cycle.argtypes = [_P]
+    L.qpic_batch_cycle.restype = _I
+    L.qpic_batch_last_error.argtypes = [_P]
+    L.qpic_batch_last_error.restype = ctypes.c_char_p
+    L.qpic_batch_destroy.argtypes = [_P]
+    L.qpic_batch_destroy.restype = None
     L.qpic_gauss_residual.argtypes = [_P, _D, _I]
     L.qpic_gauss_residual.restype = ctypes.c_int
     L.qpic_spectrum.argtypes = [_P, _D, _I, _D]
@@ -155,6 +165,41 @@ def stability_limit(solver, dz, dr, nr, n_modes, n_coef=16, fit_band=0.8):
     if st != 0:
         raise QpicError("qpic_stability_limit: %s" % STATUS.get(st, st))
     return v.value
+
+
+class Batch:
+    """Independent runs advanced together by one CUDA graph launch per cycle."""
+
+    def __init__(self, sims, stream=None):
+        self.L = load()
+        self.sims = list(sims)
+        arr = (_P * len(self.sims))(*[sm.h for sm in self.sims])
+        st_ptr = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        h = _P()
+        st = self.L.qpic_batch_create(arr, len(self.sims), st_ptr, ctypes.byref(h))
+        self.h = h
+        if st != 0:
+            msg = self.L.qpic_batch_last_error(h).decode() if h else ""
+            self.close()
+            raise QpicError("qpic_batch_create: %s %s" % (STATUS.get(st, st), msg))
+        self.cycle = int(self.L.qpic_batch_cycle(h))
+
+    def step(self, n):
+        st = self.L.qpic_batch_step(self.h, int(n))
+        if st != 0:
+            raise QpicError("qpic_batch_step: %s %s" % (STATUS.get(st, st),
+                                                       self.L.qpic_batch_last_error(self.h).decode()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qpic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _TorchAllocator:

@@ -406,9 +406,11 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->red_cap = std::max(4 * (g.nr + 1) * g.nm + 64, 8 + 3 * 305);
     if (!c->fp64) {
         const size_t tw = gpd_tile_words(g.nparts, c->TZ, c->TR) * (size_t)c->ntz * c->ntr;
-        if (!alloc_arr(c, &c->Jtile, tw) || !alloc_arr(c, &c->tstamp, (size_t)c->ntz * c->ntr))
+        if (!alloc_arr(c, &c->Jtile, tw) || !alloc_arr(c, &c->tstamp, (size_t)c->ntz * c->ntr) ||
+            !alloc_arr(c, &c->d_epoch, 4))
             return bad(QPIC_ENOMEM, "tile accumulators: device allocation failed");
         cudaMemsetAsync(c->tstamp, 0xff, (size_t)c->ntz * c->ntr * sizeof(int), c->stream);
+        cudaMemsetAsync(c->d_epoch, 0, 4 * sizeof(int), c->stream);
     }
     if (!alloc_arr(c, &c->counts, (size_t)c->nkeys + 1) ||
         !alloc_arr(c, &c->offsets, (size_t)c->nkeys + 1) || !alloc_arr(c, &c->scan_tmp, (size_t)nb + 2) ||
@@ -884,6 +886,158 @@ qpic_status qpic_kernel_times(qpic_ctx *c, int32_t n, double *ms, int64_t *launc
         if (ms) ms[k] = c->kms[k];
         if (launches) launches[k] = c->klaunch[k];
         if (names) names[k] = kNames[k];
+    }
+    return QPIC_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// A batch advances many independent runs with one graph launch per cycle of
+// `period` steps (the sort period): at creation each run's cycle is captured
+// from its own stream, forked from and joined to the batch stream, so the runs
+// are parallel branches of a single CUDA graph.
+
+}  // extern "C"
+
+struct qpic_batch {
+    std::vector<qpic_ctx *> runs;
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int period = 2;
+    bool own_main = false;
+    std::vector<long long> kernels_per_cycle;
+    std::string err;
+};
+
+static qpic_status batch_fail(qpic_batch *b, qpic_status s, const std::string &m)
+{
+    b->err = m;
+    cudaGetLastError();               // leave no pending error for unrelated calls
+    return s;
+}
+
+extern "C" {
+
+void qpic_batch_destroy(qpic_batch *b)
+{
+    if (!b) return;
+    if (b->main) cudaStreamSynchronize(b->main);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->own_main && b->main) cudaStreamDestroy(b->main);
+    delete b;
+}
+
+int32_t qpic_batch_cycle(const qpic_batch *b)
+{
+    return b ? b->period : 0;
+}
+
+const char *qpic_batch_last_error(const qpic_batch *b) { return b ? b->err.c_str() : "no batch"; }
+
+qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_stream, qpic_batch **out)
+{
+    if (!out) return QPIC_EINVAL;
+    *out = nullptr;
+    if (!runs || n < 1) return QPIC_EINVAL;
+    qpic_batch *b = new (std::nothrow) qpic_batch();
+    if (!b) return QPIC_ENOMEM;
+    *out = b;
+    b->main = static_cast<cudaStream_t>(cuda_stream);
+    if (!b->main) {                    // the legacy default stream cannot be captured
+        if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess)
+            return batch_fail(b, QPIC_ECUDA, "batch stream creation failed");
+        b->own_main = true;
+    }
+    const int all = QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE |
+                    QPIC_STAGE_WINDOW | QPIC_STAGE_SORT;
+    // a sort swaps the particle buffers on the host; a captured cycle must hold
+    // an even number of sorts so that each replay starts from the buffers the
+    // graph was recorded with
+    b->period = 2 * (runs[0]->sort_period > 1 ? runs[0]->sort_period : 1);
+    for (int k = 0; k < n; k++) {
+        qpic_ctx *c = runs[k];
+        if (!c) { b->err = "null run"; return QPIC_EINVAL; }
+        if (c->fp64 || c->cfg.moving_window || c->profile) {
+            b->err = "batch runs: FP32 path, periodic box, profiling off";
+            return QPIC_EINVAL;
+        }
+        if (c->sort_period != runs[0]->sort_period) { b->err = "batch runs need one sort period"; return QPIC_EINVAL; }
+        b->runs.push_back(c);
+    }
+    // bring every run to a cycle boundary, then drain all work
+    for (qpic_ctx *c : b->runs) {
+        while (c->nstep % b->period) run_one_step(c, all);
+        if (c->n_tail > 0) launch_sort(c);
+        cudaStreamSynchronize(c->stream);
+    }
+    b->side.resize(n);
+    b->ev_join.resize(n);
+    for (int k = 0; k < n; k++) {
+        if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+            return batch_fail(b, QPIC_ECUDA, "stream/event creation failed");
+    }
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return batch_fail(b, QPIC_ECUDA, "event creation failed");
+    cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    cudaEventRecord(b->ev_fork, b->main);
+    b->kernels_per_cycle.resize(n);
+    for (int k = 0; k < n; k++) {
+        qpic_ctx *c = b->runs[k];
+        cudaStream_t old = c->stream;
+        c->stream = b->side[k];
+        cudaStreamWaitEvent(c->stream, b->ev_fork, 0);
+        const long long nk0 = c->n_kernels, ns0 = c->nstep;
+        const Particles p0 = c->p;
+        for (int s2 = 0; s2 < b->period; s2++) run_one_step(c, all);
+        b->kernels_per_cycle[k] = c->n_kernels - nk0;
+        c->n_kernels = nk0;                 // captured, not executed
+        c->nstep = ns0;
+        cudaEventRecord(b->ev_join[k], c->stream);
+        cudaStreamWaitEvent(b->main, b->ev_join[k], 0);
+        c->stream = old;
+        if (c->p.cell != p0.cell) {         // odd number of sorts in the cycle
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(b->main, &g);
+            if (g) cudaGraphDestroy(g);
+            Particles t = c->p; c->p = c->ps; c->ps = t;
+            return batch_fail(b, QPIC_EINVAL, "captured cycle holds an odd number of sorts");
+        }
+    }
+    e = cudaStreamEndCapture(b->main, &b->graph);
+    if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    return QPIC_OK;
+}
+
+qpic_status qpic_batch_step(qpic_batch *b, int32_t nsteps)
+{
+    if (!b || !b->exec || nsteps < 0) return QPIC_EINVAL;
+    if (nsteps % b->period) { b->err = "nsteps must be a multiple of the cycle (2 x sort period)"; return QPIC_EINVAL; }
+    for (qpic_ctx *c : b->runs) cudaStreamSynchronize(c->stream);   // earlier work of the runs
+    for (qpic_ctx *c : b->runs) cudaMemsetAsync(c->d_err, 0, sizeof(int), b->main);
+    for (int r = 0; r < nsteps / b->period; r++) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->main);
+        if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaStreamSynchronize(b->main);
+    if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    for (size_t k = 0; k < b->runs.size(); k++) {
+        qpic_ctx *c = b->runs[k];
+        c->nstep += nsteps;
+        c->n_kernels += b->kernels_per_cycle[k] * (nsteps / b->period);
+        int err = 0;
+        cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (err & 1) { b->err = "fixed-point overflow in run " + std::to_string(k); return QPIC_EOVERFLOW; }
     }
     return QPIC_OK;
 }

@@ -547,7 +547,8 @@ __global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__rest
                                                const float *__restrict__ Bb,
                                                unsigned long long *__restrict__ J,
                                                unsigned long long *__restrict__ Jtile,
-                                               int *__restrict__ tstamp, int epoch,
+                                               int *__restrict__ tstamp,
+                                               const int *__restrict__ d_epoch,
                                                const int32_t *__restrict__ offsets,
                                                const long long *__restrict__ dcount, PArgs a,
                                                int ntiles, int tail_chunk)
@@ -681,7 +682,7 @@ __global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__rest
         // the gather kernel sums the (at most 4) tiles that cover each node
         unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
         for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) dst[k] = sacc.sJ[k];
-        if (threadIdx.x == 0) tstamp[blockIdx.x] = epoch;
+        if (threadIdx.x == 0) tstamp[blockIdx.x] = *d_epoch;
     }
 }
 
@@ -691,7 +692,7 @@ static void gpd_launch(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int ch
     const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
     cudaFuncSetAttribute(k_gpd<NP, TZ, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_gpd<NP, TZ, TR><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jtile,
-                                                    c->tstamp, c->epoch, c->offsets, c->d_count, a,
+                                                    c->tstamp, c->d_epoch, c->offsets, c->d_count, a,
                                                     ntiles, chunk);
 }
 
@@ -721,9 +722,14 @@ size_t gpd_tile_words(int nparts, int tz, int tr)
     return (size_t)3 * nparts * (FW + 1) * (FR + 1);
 }
 
+__global__ void k_next_epoch(int *e) { *e += 1; }
+
 void launch_gpd(qpic_ctx *c)
 {
-    c->epoch++;
+    // the epoch that stamps this step's tile blocks lives on the device, so a
+    // captured graph advances it on every replay
+    k_next_epoch<<<1, 1, 0, c->stream>>>(c->d_epoch);
+    c->n_kernels += 1;
     PArgs a = pargs(c);
     const int ntiles = c->ntz * c->ntr;
     long long tail = c->n_tail;              // particles appended since the last sort
@@ -748,7 +754,8 @@ void launch_gpd(qpic_ctx *c)
 // factor.  The global-path accumulator is cleared.
 template <int TZ, int TR>
 __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
-                                                     const int *__restrict__ tstamp, int epoch,
+                                                     const int *__restrict__ tstamp,
+                                                     const int *__restrict__ d_epoch,
                                                      unsigned long long *__restrict__ Jacc,
                                                      float *__restrict__ Jf,
                                                      const float *__restrict__ rowf, PArgs a,
@@ -763,6 +770,7 @@ __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *_
     if (c >= a.nzp - tz0) return;                          // past the last (partial) column
     const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
     const int i = tz0 + c;
+    const int epoch = *d_epoch;
     long long kbase[9];
     int li[9], ljb[9];
     bool ok[9];
@@ -815,7 +823,7 @@ template <int TZ, int TR>
 static void jreduce_launch(qpic_ctx *c, const PArgs &a, int tiles_ok)
 {
     k_jreduce<TZ, TR><<<c->ntz * c->ntr, TZ * TR, 0, c->stream>>>(
-        c->Jtile, c->tstamp, c->epoch, c->Jacc, c->Jf, c->rowf, a,
+        c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->Jf, c->rowf, a,
         (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err);
 }
 
