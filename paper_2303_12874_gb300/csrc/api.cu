@@ -62,16 +62,14 @@ qpic_status cuda_check(qpic_ctx *c, const char *where)
 
 bool alloc_particles(qpic_ctx *c, qpic::Particles &p, long long cap)
 {
-    bool ok = alloc_arr(c, &p.cell, cap) && alloc_arr(c, &p.oz, cap) && alloc_arr(c, &p.orr, cap) &&
-              alloc_arr(c, &p.cph, cap) && alloc_arr(c, &p.sph, cap) && alloc_arr(c, &p.ux, cap) &&
-              alloc_arr(c, &p.uy, cap) && alloc_arr(c, &p.uz, cap) && alloc_arr(c, &p.w, cap);
+    bool ok = alloc_arr(c, &p.cell, cap) && alloc_arr(c, &p.rec, 2 * (size_t)cap);
     if (ok && c->cfg.track_work) ok = alloc_arr(c, &p.W0, cap) && alloc_arr(c, &p.W1, cap);
     return ok;
 }
 
 void free_particles(qpic_ctx *c, qpic::Particles &p)
 {
-    void *arr[11] = {p.cell, p.oz, p.orr, p.cph, p.sph, p.ux, p.uy, p.uz, p.w, p.W0, p.W1};
+    void *arr[4] = {p.cell, p.rec, p.W0, p.W1};
     for (void *a : arr) dfree(c, a);
     p = qpic::Particles();
 }

@@ -70,8 +70,18 @@ __host__ __device__ __forceinline__ int hr_of(int fb, int c) { return fb == 0 ? 
 // (any integer, wrapped) and row j (any integer).  Half-r components continue
 // below the axis with the mode parity (radial/azimuthal (-1)^(m+1), B_z (-1)^m)
 // and beyond the wall with their even image; integer-r components are 0 outside.
+__device__ __forceinline__ float gsample_at(const float *E, const float *Bb, const PArgs &a, int fb,
+                                            int c, int p, int j, int ic);
+
 __device__ __forceinline__ float gsample(const float *E, const float *Bb, const PArgs &a, int fb,
                                          int c, int p, int j, int col)
+{
+    return gsample_at(E, Bb, a, fb, c, p, j, pwrap(col, a.nzp));
+}
+
+// as gsample, for a column ic already in [0, nzp)
+__device__ __forceinline__ float gsample_at(const float *E, const float *Bb, const PArgs &a, int fb,
+                                            int c, int p, int j, int ic)
 {
     const float *F = fb == 0 ? E : Bb;
     float sgn = 1.f;
@@ -88,7 +98,6 @@ __device__ __forceinline__ float gsample(const float *E, const float *Bb, const 
     } else {
         if (j < 0 || j > a.nr) return 0.f;
     }
-    int ic = pwrap(col, a.nzp);
     return sgn * F[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic];
 }
 
@@ -109,8 +118,9 @@ struct TileGeom {
     static constexpr int NM = (NP + 1) / 2;
     static constexpr int QW = 8 + 4 * (NM - 1);                       // words per queued move
     static constexpr int QCAP = 512;                                  // queued cell-crossing moves
+    static constexpr int PB = 9 * 256;      // prefetched words per buffer: 256 cells, 2 x 256 float4
     static constexpr size_t SMEM =
-        (size_t)JPAD * 8 + (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + 16;
+        (size_t)JPAD * 8 + (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
     static_assert((JPAD * 8) % 16 == 0, "float4 tile alignment");
 };
 
@@ -204,6 +214,15 @@ __device__ __forceinline__ void shape_delta(float x0, float d, float S0[4], floa
     }
 }
 
+// approximate square root (PTX sqrt.approx, relative error ~2^-23); the move
+// needs no IEEE rounding (charge conservation uses the displacement as computed)
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct PState {
     float oz, orr, cph, sph, ux, uy, uz, w, W0, W1;
     int jr;          // r cell (absolute)
@@ -231,6 +250,17 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
     const int ozh = oz >= 0.5f ? 0 : -1, orh = orr >= 0.5f ? 0 : -1;
     const float wzH = oz >= 0.5f ? oz - 0.5f : oz + 0.5f;
     const float wrH = orr >= 0.5f ? orr - 0.5f : orr + 0.5f;
+    // bilinear weights of the four staggering classes (half z?, half r?)
+    const float tzs[2] = {oz, wzH}, trs[2] = {orr, wrH};
+    float W[2][2][4];
+#pragma unroll
+    for (int hz = 0; hz < 2; hz++)
+#pragma unroll
+        for (int hr = 0; hr < 2; hr++) {
+            const float tz = tzs[hz], tr = trs[hr], uz = 1.f - tz, ur = 1.f - tr;
+            W[hz][hr][0] = uz * ur; W[hz][hr][1] = tz * ur;
+            W[hz][hr][2] = uz * tr; W[hz][hr][3] = tz * tr;
+        }
     float F[2][3][NP];
 #pragma unroll
     for (int fb = 0; fb < 2; fb++)
@@ -238,17 +268,15 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
         for (int c = 0; c < 3; c++) {
             const int hz = hz_of(fb, c), hr = hr_of(fb, c);
             const int i0 = bi + (hz ? ozh : 0), j0 = bj + (hr ? orh : 0);
-            const float tz = hz ? wzH : oz, tr = hr ? wrH : orr;
+            const float *w = W[hz][hr];
             float v00[NP], v01[NP], v10[NP], v11[NP];
             acc.node(fb, c, j0, i0, v00);
             acc.node(fb, c, j0, i0 + 1, v01);
             acc.node(fb, c, j0 + 1, i0, v10);
             acc.node(fb, c, j0 + 1, i0 + 1, v11);
 #pragma unroll
-            for (int p = 0; p < NP; p++) {
-                float lo = v00[p] + tz * (v01[p] - v00[p]), hi = v10[p] + tz * (v11[p] - v10[p]);
-                F[fb][c][p] = lo + tr * (hi - lo);
-            }
+            for (int p = 0; p < NP; p++)
+                F[fb][c][p] = w[0] * v00[p] + w[1] * v01[p] + w[2] * v10[p] + w[3] * v11[p];
         }
     // ---- modal sum, rotation to Cartesian
     float cm[NM], sm[NM];
@@ -304,13 +332,13 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
     const float r0 = ((float)s.jr + orr) * a.dr;
     const float x0 = r0 * cph, y0 = r0 * sph;
     float x1 = x0 + ddx, y1 = y0 + ddy;
-    float r1 = sqrtf(x1 * x1 + y1 * y1);
+    float r1 = sqrt_fast(x1 * x1 + y1 * y1);
     float drr, c1, s1, dc, ds;
     if (r1 <= a.R) {
         float den = r0 + r1;
-        drr = den > 0.f ? (ddx * (2.f * x0 + ddx) + ddy * (2.f * y0 + ddy)) / den : 0.f;
+        drr = den > 0.f ? __fdividef(ddx * (2.f * x0 + ddx) + ddy * (2.f * y0 + ddy), den) : 0.f;
         if (r1 > 0.f) {
-            float ir = 1.f / r1;
+            float ir = __fdividef(1.f, r1);
             c1 = x1 * ir; s1 = y1 * ir;
             dc = (ddx - cph * drr) * ir; ds = (ddy - sph * drr) * ir;
         } else {
@@ -343,8 +371,8 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
         }
     }
     const float xm = x0 + 0.5f * ddx, ym = y0 + 0.5f * ddy;
-    const float rm = sqrtf(xm * xm + ym * ym);
-    d.aphi = rm > 0.f ? (x0 * ddy - y0 * ddx) / (rm * a.dr) : 0.f;
+    const float rm = sqrt_fast(xm * xm + ym * ym);
+    d.aphi = rm > 0.f ? __fdividef(x0 * ddy - y0 * ddx, rm * a.dr) : 0.f;
     // ---- new state: offsets renormalised into the cell
     float nz_ = oz + dzc, nr_ = orr + drc;
     int diz = 0, djr = 0;
@@ -444,72 +472,157 @@ __device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, 
     }
 }
 
-// Same-cell deposit with a warp-level reduction: the lanes of `grp` hold moves
-// inside the same cell, so their 8*NP contributions (J_z at 2 faces, J_r at 2
-// faces, J_phi at 4 nodes, each per part) go to the same addresses.  Each
-// contribution is split exactly into hi*2^20 + lo, both halves are summed over
-// the group with one 32-bit reduction each (exact: |sum| < 2^31), and the
-// group's leader adds the int64 total to shared memory.  Tile geometry is
-// compile-time, so every accumulator offset below is an immediate.
+// Same-cell deposits summed in registers.  A thread takes consecutive particles
+// of its tile (see tile_slot), so successive moves mostly stay in one cell and
+// go to the same 8*NP accumulator words (J_z at 2 faces, J_r at 2 faces, J_phi
+// at 4 nodes, each per part).  Each contribution is rounded to the int64 fixed
+// point exactly as fx() does, kept as hi*2^20 + lo, and the two halves are
+// summed in 32-bit registers; the biased bit patterns of the rounding sums
+// (1.5*2^23 + hi) are added directly and the bias is removed once per flush.
+// Integer sums make the result independent of particle order.  A flush adds
+// the int64 totals to the tile's shared accumulators when the cell changes and
+// at the end of each chunk.  Tile geometry is compile-time, so every
+// accumulator offset is an immediate.
 template <int NP, int TZ, int TR>
-__device__ __forceinline__ void deposit_fast(const SmemAcc<NP, TZ, TR> &acc, const PArgs &a,
-                                             int li, int lj, const DepIn<(NP + 1) / 2> &d,
-                                             unsigned grp, bool leader)
-{
+struct FastSum {
     using G = TileGeom<NP, TZ, TR>;
-    constexpr int NM = (NP + 1) / 2;
-    constexpr int PL = G::JR * G::JW;                   // words per accumulator plane
-    unsigned long long *base = acc.sJ + lj * G::JW + li;
-    const float Qd = d.Q * a.qscale;
-    const float dz_ = d.dzc, dr_ = d.drc;
-    const float Sz0 = (1.f - d.oz0) - 0.5f * dz_, Sz1 = d.oz0 + 0.5f * dz_;
-    const float Sr0 = (1.f - d.or0) - 0.5f * dr_, Sr1 = d.or0 + 0.5f * dr_;
-    const float c4 = 0.25f * dz_ * dr_;
-    float ebr[NM], ebi[NM];
+    static constexpr int NV = 8 * NP;
+    static constexpr int PL = G::JR * G::JW;           // words per accumulator plane
+    unsigned hs[NV], ls[NV];
+    unsigned n;                                         // moves summed since the last flush
+    int key;                                            // (lj << 12) | li of those moves
+
+    __device__ __forceinline__ void clear()
+    {
 #pragma unroll
-    for (int m = 0; m < NM; m++) { ebr[m] = d.e0r[m] + 0.5f * d.der[m]; ebi[m] = d.e0i[m] + 0.5f * d.dei[m]; }
-    auto put = [&](int off, float v) {
-        int hi, lo;
-        fx_split(v, hi, lo);
-        const int shi = (int)__reduce_add_sync(grp, (unsigned)hi);
-        const int slo = (int)__reduce_add_sync(grp, (unsigned)lo);
-        if (leader) atomicAdd(base + off, (unsigned long long)(((long long)shi << 20) + slo));
-    };
-    const float Xz0 = Qd * dz_ * Sr0, Xz1 = Qd * dz_ * Sr1;      // J_z at (i0+1/2, j0+b)
-    const float Xr0 = Qd * dr_ * Sz0, Xr1 = Qd * dr_ * Sz1;      // J_r at (i0+a, j0+1/2)
-    put((2 * NP) * PL, Xz0);
-    put((2 * NP) * PL + G::JW, Xz1);
-    put(0, Xr0);
-    put(1, Xr1);
-#pragma unroll
-    for (int m = 1; m < NM; m++) {
-        put((2 * NP + 2 * m - 1) * PL, Xz0 * ebr[m]);
-        put((2 * NP + 2 * m) * PL, Xz0 * ebi[m]);
-        put((2 * NP + 2 * m - 1) * PL + G::JW, Xz1 * ebr[m]);
-        put((2 * NP + 2 * m) * PL + G::JW, Xz1 * ebi[m]);
-        put((2 * m - 1) * PL, Xr0 * ebr[m]);
-        put((2 * m) * PL, Xr0 * ebi[m]);
-        put((2 * m - 1) * PL + 1, Xr1 * ebr[m]);
-        put((2 * m) * PL + 1, Xr1 * ebi[m]);
+        for (int i = 0; i < NV; i++) { hs[i] = 0u; ls[i] = 0u; }
+        n = 0u;
+        key = -1;
     }
-    // J_phi at (i0+a, j0+b): m = 0 from the azimuthal displacement, m >= 1 from
-    // i Q Sbar (e1 - e0)/m, Sbar_ab = Sz_a Sr_b + (dSz_a dSr_b)/4
-    const float S[4] = {Sz0 * Sr0 + c4, Sz1 * Sr0 - c4, Sz0 * Sr1 - c4, Sz1 * Sr1 + c4};
-    const int noff[4] = {0, 1, G::JW, G::JW + 1};
+    // accumulator word of value i relative to the cell's (lj, li)
+    static __device__ __forceinline__ constexpr int off(int i)
+    {
+        const int p = i >> 3, e = i & 7;
+        return e == 0 ? (2 * NP + p) * PL
+             : e == 1 ? (2 * NP + p) * PL + G::JW
+             : e == 2 ? p * PL
+             : e == 3 ? p * PL + 1
+                      : (NP + p) * PL + ((e - 4) & 1) + ((e - 4) >> 1) * G::JW;
+    }
+    // t = contribution * qscale * 2^-20, |t| < 2^22
+    __device__ __forceinline__ void put(int i, float t)
+    {
+        const float M = 12582912.0f;                    // 1.5 * 2^23
+        const float tm = __fadd_rn(t, M);               // bits: 0x4B400000 + round(t)
+        hs[i] += __float_as_uint(tm);
+        const float r = __fsub_rn(t, __fsub_rn(tm, M)); // t - round(t), exact
+        ls[i] += __float_as_uint(__fmaf_rn(r, 1048576.0f, M));
+    }
+    __device__ __forceinline__ void add(const DepIn<(NP + 1) / 2> &d, float q20)
+    {
+        constexpr int NM = (NP + 1) / 2;
+        const float dz_ = d.dzc, dr_ = d.drc;
+        const float Sz0 = (1.f - d.oz0) - 0.5f * dz_, Sz1 = d.oz0 + 0.5f * dz_;
+        const float Sr0 = (1.f - d.or0) - 0.5f * dr_, Sr1 = d.or0 + 0.5f * dr_;
+        const float c4 = 0.25f * dz_ * dr_;
+        const float qz = q20 * dz_, qr = q20 * dr_;
+        const float Xz0 = qz * Sr0, Xz1 = qz * Sr1;    // J_z at (i0+1/2, j0+b)
+        const float Xr0 = qr * Sz0, Xr1 = qr * Sz1;    // J_r at (i0+a, j0+1/2)
+        // J_phi at (i0+a, j0+b): Sbar_ab = Sz_a Sr_b + (dSz_a dSr_b)/4
+        const float QS[4] = {q20 * (Sz0 * Sr0 + c4), q20 * (Sz1 * Sr0 - c4),
+                             q20 * (Sz0 * Sr1 - c4), q20 * (Sz1 * Sr1 + c4)};
+        put(0, Xz0); put(1, Xz1); put(2, Xr0); put(3, Xr1);
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float QS = Qd * S[k];
-        put(NP * PL + noff[k], QS * d.aphi);
+        for (int k = 0; k < 4; k++) put(4 + k, QS[k] * d.aphi);      // m = 0: azimuthal displacement
 #pragma unroll
         for (int m = 1; m < NM; m++) {
+            const float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
             const float im = 1.f / (float)m;
-            put((NP + 2 * m - 1) * PL + noff[k], -QS * d.dei[m] * im);
-            put((NP + 2 * m) * PL + noff[k], QS * d.der[m] * im);
+            const int pr = 8 * (2 * m - 1), pi = 8 * (2 * m);
+            put(pr + 0, Xz0 * ebr); put(pr + 1, Xz1 * ebr); put(pr + 2, Xr0 * ebr); put(pr + 3, Xr1 * ebr);
+            put(pi + 0, Xz0 * ebi); put(pi + 1, Xz1 * ebi); put(pi + 2, Xr0 * ebi); put(pi + 3, Xr1 * ebi);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {                            // m >= 1: i Q Sbar (e1 - e0)/m
+                put(pr + 4 + k, -QS[k] * d.dei[m] * im);
+                put(pi + 4 + k, QS[k] * d.der[m] * im);
+            }
         }
+        n += 1u;
     }
-}
+    __device__ __forceinline__ void flush(unsigned long long *sJ)
+    {
+        if (n == 0u) return;
+        unsigned long long *b = sJ + (key >> 12) * G::JW + (key & 0xFFF);
+        const unsigned bias = 0x4B400000u * n;
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            const long long w = ((long long)(int)(hs[i] - bias) << 20) + (long long)(int)(ls[i] - bias);
+            atomicAdd(b + off(i), (unsigned long long)w);
+            hs[i] = 0u; ls[i] = 0u;
+        }
+        n = 0u;
+    }
+};
 
 // ------------------------------------------------------------ the GPD kernel
+// Particle order inside a tile.  The n particles of a tile (sorted by cell) are
+// taken in chunks: full chunks of GPD_C = GPD_T * GPD_K, then the rest (rc <
+// GPD_C).  In a chunk every thread takes kc consecutive particles (GPD_K in a
+// full chunk, kc = ceil(rc / GPD_T) in the last; nt = rc / kc threads take kc,
+// thread nt the rem = rc - nt kc left), so one thread's moves mostly share a
+// cell (FastSum).  Thread t's k-th particle of a chunk is q0 + t kc + k.
+constexpr int GPD_T = 256, GPD_K = 8, GPD_C = GPD_T * GPD_K;
+
+struct Chunk { int q0, rc, kc, nt, rem; };
+
+__host__ __device__ __forceinline__ int imin(int x, int y) { return x < y ? x : y; }
+
+__host__ __device__ __forceinline__ int tile_nchunks(int n) { return (n + GPD_C - 1) / GPD_C; }
+
+__host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c)
+{
+    const int nfull = n / GPD_C;
+    Chunk k;
+    if (c < nfull) {
+        k.q0 = c * GPD_C; k.rc = GPD_C; k.kc = GPD_K; k.nt = GPD_T; k.rem = 0;
+    } else {
+        k.q0 = nfull * GPD_C;
+        k.rc = n - k.q0;
+        k.kc = (k.rc + GPD_T - 1) / GPD_T;
+        k.nt = k.rc / k.kc;
+        k.rem = k.rc - k.nt * k.kc;
+    }
+    return k;
+}
+
+// Ampere-style asynchronous 4-byte global -> shared copies (one per thread and
+// word); a thread waits only for its own groups
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// one particle record (two float4 words, 32-byte aligned) in a single 256-bit access
+__device__ __forceinline__ void ld_rec(const float4 *p, float4 &a, float4 &b)
+{
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+__device__ __forceinline__ void st_rec(float4 *p, const float4 &a, const float4 &b)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
+                 "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // cell index of a particle: (iz_phys << 16) | jr
 __host__ __device__ __forceinline__ int cell_iz(int cell) { return cell >> 16; }
 __host__ __device__ __forceinline__ int cell_jr(int cell) { return cell & 0xFFFF; }
@@ -543,15 +656,15 @@ __device__ __forceinline__ void queue_get(const float *q, int &li, int &lj, DepI
 }
 
 template <int NP, int TZ, int TR>
-__global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__restrict__ E,
-                                               const float *__restrict__ Bb,
-                                               unsigned long long *__restrict__ J,
-                                               unsigned long long *__restrict__ Jtile,
-                                               int *__restrict__ tstamp,
-                                               const int *__restrict__ d_epoch,
-                                               const int32_t *__restrict__ offsets,
-                                               const long long *__restrict__ dcount, PArgs a,
-                                               int ntiles, int tail_chunk)
+__global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__restrict__ E,
+                                                 const float *__restrict__ Bb,
+                                                 unsigned long long *__restrict__ J,
+                                                 unsigned long long *__restrict__ Jtile,
+                                                 int *__restrict__ tstamp,
+                                                 const int *__restrict__ d_epoch,
+                                                 const int32_t *__restrict__ offsets,
+                                                 const long long *__restrict__ dcount, PArgs a,
+                                                 int ntiles, int tail_chunk)
 {
     using G = TileGeom<NP, TZ, TR>;
     constexpr int NM = (NP + 1) / 2;
@@ -573,117 +686,161 @@ __global__ void __launch_bounds__(256, 3) k_gpd(Particles P, const float *__rest
         if (begin >= end) return;
     }
     GlobAcc<NP> gacc{E, Bb, J, a};
-    SmemAcc<NP, TZ, TR> sacc{nullptr, nullptr};
-    const int col0 = tz0 - G::H - 1;
-    const int row0 = tr0 - G::H - 1;
-    const bool smem_usable = tile_mode && a.nzp >= 2 * G::JW;
-    float *queue = nullptr;
-    int *qcount = nullptr;
-    if (smem_usable) {
-        unsigned long long *sJ = sraw;
-        float4 *sf = reinterpret_cast<float4 *>(sraw + G::JPAD);
-        queue = reinterpret_cast<float *>(sf + G::FVEC);
-        qcount = reinterpret_cast<int *>(queue + G::QCAP * G::QW);
-        sacc.sJ = sJ;
-        sacc.sf = sf;
-        for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) sJ[k] = 0ull;
-        if (threadIdx.x == 0) *qcount = 0;
-        // one float4 word (up to 4 mode parts of one node) per thread and pass
-        for (int k = threadIdx.x; k < G::FVEC; k += blockDim.x) {
-            const int v = k % G::V, t1 = k / G::V;
-            const int li = t1 % G::FW, t2 = t1 / G::FW, lj = t2 % G::FR, fc = t2 / G::FR;
-            const int c = fc % 3, fb = fc / 3;
-            int col = col0 + li;
-            col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
-            float w4[4];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int p = 4 * v + e;
-                w4[e] = p < NP ? gsample(E, Bb, a, fb, c, p, row0 + lj, col) : 0.f;
-            }
-            sf[k] = make_float4(w4[0], w4[1], w4[2], w4[3]);
-        }
-        __syncthreads();
-    }
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
     const int zoff = (int)a.zoff;
-    for (long long base = begin; base < end; base += blockDim.x) {
-        const long long idx = base + threadIdx.x;
-        const int cell = idx < end ? P.cell[idx] : -1;
-        bool act = cell >= 0;
-        const int iz = cell_iz(cell), jr = cell_jr(cell);
-        if (act && !a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
-            P.cell[idx] = -1;                  // behind the moving window
-            act = false;
-        }
-        PState s;
-        DepIn<NM> d = {};                      // lanes without a particle reduce zeros
-        bool fast = false;
-        int li = 0, lj = 0;
-        if (act) {
-            s.oz = P.oz[idx]; s.orr = P.orr[idx]; s.cph = P.cph[idx]; s.sph = P.sph[idx];
-            s.ux = P.ux[idx]; s.uy = P.uy[idx]; s.uz = P.uz[idx]; s.w = P.w[idx];
+    if (!tile_mode || a.nzp < 2 * G::JW) {
+        // particles appended since the last sort, or a box too short for the
+        // staged tile: every access goes to global memory
+        for (long long idx = begin + threadIdx.x; idx < end; idx += blockDim.x) {
+            const int cell = P.cell[idx];
+            if (cell < 0) continue;
+            const int iz = cell_iz(cell), jr = cell_jr(cell);
+            if (!a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) { P.cell[idx] = -1; continue; }
+            PState s;
+            DepIn<NM> d;
+            float4 ra, rb;
+            ld_rec(P.rec + 2 * idx, ra, rb);
+            s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
+            s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
             s.W0 = a.track_work ? P.W0[idx] : 0.f;
             s.W1 = a.track_work ? P.W1[idx] : 0.f;
             s.jr = jr;
-            bool in_smem = false;
-            if (smem_usable) {
-                li = wrapn(iz - col0, a.nzp);
-                lj = jr - row0;
-                in_smem = li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2;
-            }
-            if (in_smem) {
-                push_move<NP>(sacc, a, li, lj, s, d);
-                fast = same_cell(d);
-                // a move across a cell boundary waits in the queue (no divergence here)
-                if (!fast) queue_put<NM>(queue + G::QW * atomicAdd(qcount, 1), li, lj, d);
-            } else {
-                push_move<NP>(gacc, a, iz, jr, s, d);
-                deposit_general<NP>(gacc, a, iz, jr, d);
-            }
-        }
-        if (smem_usable) {                     // block-uniform branch
-            // same-cell moves: lanes of one cell reduce together, one atomic per group
-            const unsigned fm = __ballot_sync(FULL, fast);
-            if (fast) {
-                const unsigned grp = __match_any_sync(fm, (unsigned)((lj << 12) | li));
-                deposit_fast<NP, TZ, TR>(sacc, a, li, lj, d, grp, lane == __ffs(grp) - 1);
-            }
-        }
-        if (act) {
+            push_move<NP>(gacc, a, iz, jr, s, d);
+            deposit_general<NP>(gacc, a, iz, jr, d);
             const int niz = wrapn(iz + s.diz, a.nzp);
-            const int njr = jr + s.djr;
             const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
-            P.cell[idx] = dead ? -1 : make_cell(niz, njr);
-            P.oz[idx] = s.oz; P.orr[idx] = s.orr; P.cph[idx] = s.cph; P.sph[idx] = s.sph;
-            P.ux[idx] = s.ux; P.uy[idx] = s.uy; P.uz[idx] = s.uz;
+            P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
+            st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph), make_float4(s.ux, s.uy, s.uz, s.w));
             if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
         }
-        if (smem_usable) {
-            // drain the queue when another round could overflow it, and at the end
-            __syncthreads();
-            const int nq = *qcount;
-            if (nq > G::QCAP - (int)blockDim.x || base + blockDim.x >= end) {
-                for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-                    int qi, qj;
-                    DepIn<NM> dq;
-                    queue_get<NM>(queue + G::QW * k, qi, qj, dq);
-                    deposit_general<NP>(sacc, a, qi, qj, dq);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) *qcount = 0;
-                __syncthreads();
-            }
+        return;
+    }
+    // ---- shared memory: accumulators, staged fields, crossing queue, particle buffers
+    unsigned long long *sJ = sraw;
+    float4 *sf = reinterpret_cast<float4 *>(sraw + G::JPAD);
+    float *queue = reinterpret_cast<float *>(sf + G::FVEC);
+    int *qcount = reinterpret_cast<int *>(queue + G::QCAP * G::QW);
+    // ---- each thread pushes kc consecutive particles of the tile; the next
+    // particle's words are copied to shared memory while one is pushed (the
+    // first copy overlaps the staging of the fields)
+    float *pbuf = reinterpret_cast<float *>(qcount + 4);
+    const int n = (int)(end - begin);
+    const int nch = tile_nchunks(n);
+    const int tid = threadIdx.x;
+    auto slot_of = [&](int ch, int k) -> long long {
+        const Chunk C = tile_chunk(n, ch);
+        const int cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
+        return k < cnt ? begin + C.q0 + tid * C.kc + k : -1;
+    };
+    auto prefetch = [&](int b, long long idx) {
+        if (idx >= 0) {
+            float *pb = pbuf + b * G::PB;
+            float4 *pr = reinterpret_cast<float4 *>(pb + GPD_T);
+            cp_async4(pb + tid, P.cell + idx);
+            cp_async16(pr + tid, P.rec + 2 * idx);
+            cp_async16(pr + GPD_T + tid, P.rec + 2 * idx + 1);
         }
+        cp_async_commit();
+    };
+    long long idx = slot_of(0, 0);
+    prefetch(0, idx);
+    // ---- stage E and Bbar of the tile and its halo; clear the accumulators
+    const int col0 = tz0 - G::H - 1;
+    const int row0 = tr0 - G::H - 1;
+    const SmemAcc<NP, TZ, TR> sacc{sf, sJ};
+    for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) sJ[k] = 0ull;
+    if (threadIdx.x == 0) *qcount = 0;
+    // one float4 word (up to 4 mode parts of one node) per thread and pass
+    for (int k = threadIdx.x; k < G::FVEC; k += blockDim.x) {
+        const int v = k % G::V, t1 = k / G::V;
+        const int li = t1 % G::FW, t2 = t1 / G::FW, lj = t2 % G::FR, fc = t2 / G::FR;
+        const int c = fc % 3, fb = fc / 3;
+        int col = col0 + li;
+        col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
+        float w4[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int p = 4 * v + e;
+            w4[e] = p < NP ? gsample_at(E, Bb, a, fb, c, p, row0 + lj, col) : 0.f;
+        }
+        sf[k] = make_float4(w4[0], w4[1], w4[2], w4[3]);
     }
-    if (smem_usable) {
-        // the tile's accumulators go to its own scratch block with plain stores;
-        // the gather kernel sums the (at most 4) tiles that cover each node
-        unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
-        for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) dst[k] = sacc.sJ[k];
-        if (threadIdx.x == 0) tstamp[blockIdx.x] = *d_epoch;
+    __syncthreads();
+    const float q20 = a.qscale * 9.5367431640625e-07f;            // qscale * 2^-20
+    FastSum<NP, TZ, TR> fs;
+    fs.clear();
+    int buf = 0;
+    for (int ch = 0; ch < nch; ch++) {
+        const int kc = tile_chunk(n, ch).kc;
+        for (int k = 0; k < kc; k++) {                             // block-uniform trip count
+            const long long nidx = k + 1 < kc ? slot_of(ch, k + 1) : (ch + 1 < nch ? slot_of(ch + 1, 0) : -1);
+            prefetch(buf ^ 1, nidx);
+            cp_async_wait_prev();                                  // this particle's words have landed
+            if (idx >= 0) {
+                const float *pb = pbuf + buf * G::PB;
+                const float4 *pr = reinterpret_cast<const float4 *>(pb + GPD_T);
+                const int cell = __float_as_int(pb[tid]);
+                const int iz = cell_iz(cell), jr = cell_jr(cell);
+                bool act = cell >= 0;
+                if (act && !a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
+                    P.cell[idx] = -1;                  // behind the moving window
+                    act = false;
+                }
+                if (act) {
+                    PState s;
+                    DepIn<NM> d;
+                    const float4 ra = pr[tid], rb = pr[GPD_T + tid];
+                    s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
+                    s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
+                    s.W0 = a.track_work ? P.W0[idx] : 0.f;
+                    s.W1 = a.track_work ? P.W1[idx] : 0.f;
+                    s.jr = jr;
+                    const int li = wrapn(iz - col0, a.nzp), lj = jr - row0;
+                    if (li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2) {
+                        push_move<NP>(sacc, a, li, lj, s, d);
+                        if (same_cell(d)) {
+                            const int key = (lj << 12) | li;
+                            if (key != fs.key) { fs.flush(sJ); fs.key = key; }
+                            fs.add(d, d.Q * q20);
+                        } else {
+                            // a move across a cell boundary waits in the queue (deposited
+                            // directly when the queue is full)
+                            const int slot = atomicAdd(qcount, 1);
+                            if (slot < G::QCAP) queue_put<NM>(queue + G::QW * slot, li, lj, d);
+                            else deposit_general<NP>(sacc, a, li, lj, d);
+                        }
+                    } else {                           // drifted beyond the staged halo
+                        push_move<NP>(gacc, a, iz, jr, s, d);
+                        deposit_general<NP>(gacc, a, iz, jr, d);
+                    }
+                    const int niz = wrapn(iz + s.diz, a.nzp);
+                    const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
+                    P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
+                    st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph),
+                           make_float4(s.ux, s.uy, s.uz, s.w));
+                    if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+                }
+            }
+            idx = nidx;
+            buf ^= 1;
+        }
+        fs.flush(sJ);
+        fs.key = -1;
     }
+    // the queued cell-crossing moves, spread over all threads
+    __syncthreads();
+    const int nq = imin(*qcount, G::QCAP);
+    for (int q = tid; q < nq; q += blockDim.x) {
+        int qi, qj;
+        DepIn<NM> dq;
+        queue_get<NM>(queue + G::QW * q, qi, qj, dq);
+        deposit_general<NP>(sacc, a, qi, qj, dq);
+    }
+    __syncthreads();
+    // the tile's accumulators go to its own scratch block with plain stores;
+    // the reduction kernel sums the tiles that cover each node
+    unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
+    for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) dst[k] = sJ[k];
+    if (threadIdx.x == 0) tstamp[blockIdx.x] = *d_epoch;
 }
 
 template <int NP, int TZ, int TR>
@@ -691,7 +848,7 @@ static void gpd_launch(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int ch
 {
     const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
     cudaFuncSetAttribute(k_gpd<NP, TZ, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gpd<NP, TZ, TR><<<grid, 256, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jtile,
+    k_gpd<NP, TZ, TR><<<grid, GPD_T, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jtile,
                                                     c->tstamp, c->d_epoch, c->offsets, c->d_count, a,
                                                     ntiles, chunk);
 }
@@ -963,9 +1120,10 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
         top = __shfl_sync(grp, top, leader);
         const int rank = __popc(grp & ((1u << lane) - 1u));
         const long long d = (long long)offsets[k] + top - n + rank;
-        dst.cell[d] = c; dst.oz[d] = src.oz[i]; dst.orr[d] = src.orr[i];
-        dst.cph[d] = src.cph[i]; dst.sph[d] = src.sph[i];
-        dst.ux[d] = src.ux[i]; dst.uy[d] = src.uy[i]; dst.uz[d] = src.uz[i]; dst.w[d] = src.w[i];
+        dst.cell[d] = c;
+        float4 ra, rb;
+        ld_rec(src.rec + 2 * i, ra, rb);
+        st_rec(dst.rec + 2 * d, ra, rb);
         if (a.track_work) { dst.W0[d] = src.W0[i]; dst.W1[d] = src.W1[i]; }
     }
 }
@@ -1059,10 +1217,9 @@ __global__ void k_load_plasma(Particles P, PlasmaArgs L, long long ntot, int tra
         long long d = base + t;
         int iz = (int)(((il + L.zoff) % L.nzp + L.nzp) % L.nzp);
         P.cell[d] = w > 0.0 ? make_cell(iz, jr) : -1;
-        P.oz[d] = (float)((a + 0.5) / L.pz);
-        P.orr[d] = (float)((b + 0.5) / L.pr);
-        P.cph[d] = (float)cos(phi); P.sph[d] = (float)sin(phi);
-        P.ux[d] = 0.f; P.uy[d] = 0.f; P.uz[d] = 0.f; P.w[d] = (float)w;
+        P.rec[2 * d] = make_float4((float)((a + 0.5) / L.pz), (float)((b + 0.5) / L.pr),
+                                   (float)cos(phi), (float)sin(phi));
+        P.rec[2 * d + 1] = make_float4(0.f, 0.f, 0.f, (float)w);
         if (track) { P.W0[d] = 0.f; P.W1[d] = 0.f; }
     }
 }
@@ -1133,10 +1290,8 @@ __global__ void k_load_particles(Particles P, long long n, const double *z, cons
         if (orf >= 1.f) orf = 0.99999994f;
         int iz = (int)(((il + L.zoff) % L.nzp + L.nzp) % L.nzp);
         P.cell[i] = (dead || !(w[i] > 0.0)) ? -1 : make_cell(iz, jr);
-        P.oz[i] = ozf; P.orr[i] = orf;
-        P.cph[i] = (float)cos(phi[i]); P.sph[i] = (float)sin(phi[i]);
-        P.ux[i] = (float)ux[i]; P.uy[i] = (float)uy[i]; P.uz[i] = (float)uz[i];
-        P.w[i] = (float)w[i];
+        P.rec[2 * i] = make_float4(ozf, orf, (float)cos(phi[i]), (float)sin(phi[i]));
+        P.rec[2 * i + 1] = make_float4((float)ux[i], (float)uy[i], (float)uz[i], (float)w[i]);
         if (track) { P.W0[i] = 0.f; P.W1[i] = 0.f; }
     }
 }
@@ -1181,13 +1336,14 @@ __global__ void k_export(Particles P, long long n, double *out, long long stride
         int iz = cell_iz(cell), jr = cell_jr(cell);
         int il = iz - (int)L.zoff;
         if (il < 0) il += L.nzp;
-        out[0 * stride + i] = L.zmin + ((double)il + (double)P.oz[i]) * L.dz;
-        out[1 * stride + i] = ((double)jr + (double)P.orr[i]) * L.dr;
-        out[2 * stride + i] = atan2((double)P.sph[i], (double)P.cph[i]);
-        out[3 * stride + i] = P.ux[i];
-        out[4 * stride + i] = P.uy[i];
-        out[5 * stride + i] = P.uz[i];
-        out[6 * stride + i] = dead ? 0.0 : (double)P.w[i];
+        const float4 ra = P.rec[2 * i], rb = P.rec[2 * i + 1];
+        out[0 * stride + i] = L.zmin + ((double)il + (double)ra.x) * L.dz;
+        out[1 * stride + i] = ((double)jr + (double)ra.y) * L.dr;
+        out[2 * stride + i] = atan2((double)ra.w, (double)ra.z);
+        out[3 * stride + i] = rb.x;
+        out[4 * stride + i] = rb.y;
+        out[5 * stride + i] = rb.z;
+        out[6 * stride + i] = dead ? 0.0 : (double)rb.w;
         out[7 * stride + i] = track ? P.W0[i] : 0.0;
         out[8 * stride + i] = track ? P.W1[i] : 0.0;
     }
@@ -1215,8 +1371,9 @@ __global__ void k_rho(Particles P, long long n, double *out, LoadArgs L, int nm)
         int iz = cell_iz(cell), jr = cell_jr(cell);
         int il = iz - (int)L.zoff;
         if (il < 0) il += L.nzp;
-        double oz = P.oz[i], orr = P.orr[i], Q = -(double)P.w[i];
-        double c1 = P.cph[i], s1 = -(double)P.sph[i];      // e^{-i phi}
+        const float4 ra = P.rec[2 * i];
+        double oz = ra.x, orr = ra.y, Q = -(double)P.rec[2 * i + 1].w;
+        double c1 = ra.z, s1 = -(double)ra.w;                // e^{-i phi}
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++) {
                 int ic = il + a;
@@ -1278,13 +1435,14 @@ __global__ void k_spectrum(Particles P, const long long *dcount, const double *e
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (P.cell[i] < 0) continue;
-        const float ux = P.ux[i], uy = P.uy[i], uz = P.uz[i];
+        const float4 rb = P.rec[2 * i + 1];
+        const float ux = rb.x, uy = rb.y, uz = rb.z;
         const float u2 = ux * ux + uy * uy + uz * uz;
         const double e = (double)(u2 / (1.f + sqrtf(1.f + u2))) * mec2;
         if (e < edges[0] || e >= edges[nb]) continue;
         int lo = 0, hi = nb;                                  // edges[lo] <= e < edges[hi]
         while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (e >= edges[mid]) lo = mid; else hi = mid; }
-        atomicAdd(&hist[lo], (unsigned long long)__double2ll_rn((double)P.w[i] * wscale));
+        atomicAdd(&hist[lo], (unsigned long long)__double2ll_rn((double)rb.w * wscale));
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += blockDim.x)
@@ -1309,11 +1467,12 @@ __global__ void k_psums_partial(Particles P, const long long *dcount, double *pa
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (P.cell[i] < 0) continue;
-        const float ux = P.ux[i], uy = P.uy[i], uz = P.uz[i];
+        const float4 rb = P.rec[2 * i + 1];
+        const float ux = rb.x, uy = rb.y, uz = rb.z;
         const float u2 = ux * ux + uy * uy + uz * uz;
         const float gm1 = u2 / (1.f + sqrtf(1.f + u2));          // gamma - 1 without cancellation
-        cnt += 1.0; chg -= (double)P.w[i];
-        ke += (double)P.w[i] * (double)gm1;
+        cnt += 1.0; chg -= (double)rb.w;
+        ke += (double)rb.w * (double)gm1;
     }
     s0[threadIdx.x] = cnt; s1[threadIdx.x] = chg; s2[threadIdx.x] = ke;
     __syncthreads();

@@ -37,11 +37,14 @@ struct FieldGeom {
     int periodic;
 };
 
+// FP32 particles: the cell index (iz << 16 | jr, -1 = dead) in its own array and
+// the eight floats of a particle as one 32-byte record of two float4 words,
+// (oz, orr, cos phi, sin phi) and (ux, uy, uz, w), so that moving a particle
+// writes whole 32-byte sectors
 struct Particles {
     int32_t *cell = nullptr;
-    float *oz = nullptr, *orr = nullptr, *cph = nullptr, *sph = nullptr;
-    float *ux = nullptr, *uy = nullptr, *uz = nullptr, *w = nullptr;
-    float *W0 = nullptr, *W1 = nullptr;
+    float4 *rec = nullptr;                 // [2 * capacity]
+    float *W0 = nullptr, *W1 = nullptr;    // modal work (when tracked)
 };
 
 struct Particles64 {  // plain FP64 path: lab z, Cartesian x, y
