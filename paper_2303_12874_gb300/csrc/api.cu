@@ -405,9 +405,10 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     if (!c->fp64) {
         const size_t tw = gpd_tile_words(g.nparts, c->TZ, c->TR) * (size_t)c->ntz * c->ntr;
         if (!alloc_arr(c, &c->Jtile, tw) || !alloc_arr(c, &c->tstamp, (size_t)c->ntz * c->ntr) ||
-            !alloc_arr(c, &c->d_epoch, 4))
+            !alloc_arr(c, &c->jdirty, (size_t)c->ntz * c->ntr) || !alloc_arr(c, &c->d_epoch, 4))
             return bad(QPIC_ENOMEM, "tile accumulators: device allocation failed");
         cudaMemsetAsync(c->tstamp, 0xff, (size_t)c->ntz * c->ntr * sizeof(int), c->stream);
+        cudaMemsetAsync(c->jdirty, 0, (size_t)c->ntz * c->ntr * sizeof(int), c->stream);
         cudaMemsetAsync(c->d_epoch, 0, 4 * sizeof(int), c->stream);
     }
     if (!alloc_arr(c, &c->counts, (size_t)c->nkeys + 1) ||

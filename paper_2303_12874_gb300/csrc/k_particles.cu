@@ -56,6 +56,8 @@ static PArgs pargs(const qpic_ctx *c)
     return a;
 }
 
+__host__ __device__ __forceinline__ int imin(int x, int y) { return x < y ? x : y; }
+
 __device__ __forceinline__ int pwrap(int i, int n)
 {
     int r = i % n;
@@ -151,6 +153,7 @@ template <int NP>
 struct GlobAcc {
     const float *E, *Bb;
     unsigned long long *J;
+    int *dirty;                  // per tile: its core received a global-path deposit
     PArgs a;
     __device__ __forceinline__ void node(int fb, int c, int j, int i, float out[NP]) const
     {
@@ -163,6 +166,8 @@ struct GlobAcc {
         int ic = pwrap(i, a.nzp);
         atomicAdd(&J[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic],
                   (unsigned long long)v);
+        const int tr = imin(j >> a.lTR, a.ntr - 1);
+        dirty[(ic >> a.lTZ) * a.ntr + tr] = 1;
     }
 };
 
@@ -575,8 +580,6 @@ constexpr int GPD_T = 256, GPD_K = 8, GPD_C = GPD_T * GPD_K;
 
 struct Chunk { int q0, rc, kc, nt, rem; };
 
-__host__ __device__ __forceinline__ int imin(int x, int y) { return x < y ? x : y; }
-
 __host__ __device__ __forceinline__ int tile_nchunks(int n) { return (n + GPD_C - 1) / GPD_C; }
 
 __host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c)
@@ -660,7 +663,7 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
                                                  const float *__restrict__ Bb,
                                                  unsigned long long *__restrict__ J,
                                                  unsigned long long *__restrict__ Jtile,
-                                                 int *__restrict__ tstamp,
+                                                 int *__restrict__ tstamp, int *__restrict__ jdirty,
                                                  const int *__restrict__ d_epoch,
                                                  const int32_t *__restrict__ offsets,
                                                  const long long *__restrict__ dcount, PArgs a,
@@ -685,7 +688,7 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
         end = min(begin + tail_chunk, np);
         if (begin >= end) return;
     }
-    GlobAcc<NP> gacc{E, Bb, J, a};
+    GlobAcc<NP> gacc{E, Bb, J, jdirty, a};
     const int zoff = (int)a.zoff;
     if (!tile_mode || a.nzp < 2 * G::JW) {
         // particles appended since the last sort, or a box too short for the
@@ -849,7 +852,7 @@ static void gpd_launch(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int ch
     const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
     cudaFuncSetAttribute(k_gpd<NP, TZ, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_gpd<NP, TZ, TR><<<grid, GPD_T, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jtile,
-                                                    c->tstamp, c->d_epoch, c->offsets, c->d_count, a,
+                                                    c->tstamp, c->jdirty, c->d_epoch, c->offsets, c->d_count, a,
                                                     ntiles, chunk);
 }
 
@@ -904,32 +907,37 @@ void launch_gpd(qpic_ctx *c)
 
 // ------------------------------------------------------------ current reduction + decode
 // One thread per node of a tile's core (its TZ x TR cells; the last tile row
-// also owns the wall row j = nr).  A node's current is the global-path
-// accumulator plus the word of every neighbouring tile block (3 x 3 candidates,
-// written this step, whose staged region covers the node), summed in a fixed
-// order in int64 and turned into FP32 current with the per-row finite-volume
-// factor.  The global-path accumulator is cleared.
-template <int TZ, int TR>
+// also owns the wall row j = nr).  A node's current is the word of every
+// neighbouring tile block (3 x 3 candidates, written this step, whose staged
+// region covers the node) plus, in tiles that received global-path deposits,
+// the global accumulator (then cleared), summed in a fixed order in int64 and
+// turned into FP32 current with the per-row finite-volume factor.  All NP
+// parts of the three components are loaded together (unrolled).
+template <int NP, int TZ, int TR>
 __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
                                                      const int *__restrict__ tstamp,
                                                      const int *__restrict__ d_epoch,
                                                      unsigned long long *__restrict__ Jacc,
+                                                     int *__restrict__ jdirty,
                                                      float *__restrict__ Jf,
                                                      const float *__restrict__ rowf, PArgs a,
                                                      long long tile_words, float inv_qscale,
                                                      int tiles_ok, int *err)
 {
-    constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3;
+    constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3, NPL = 3 * NP;
     const int c = threadIdx.x % TZ, r0 = threadIdx.x / TZ;
     const int t = blockIdx.x;
     const int tzi = t / a.ntr, tri = t - tzi * a.ntr;
     const int tz0 = tzi * TZ, tr0 = tri * TR;
+    const bool dirty = jdirty[t] != 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && dirty) jdirty[t] = 0;
     if (c >= a.nzp - tz0) return;                          // past the last (partial) column
     const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
     const int i = tz0 + c;
     const int epoch = *d_epoch;
     long long kbase[9];
-    int li[9], ljb[9];
+    int ljb[9];
     bool ok[9];
 #pragma unroll
     for (int d = 0; d < 9; d++) {
@@ -938,50 +946,71 @@ __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *_
         kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
         const int kr = tri + dr;
         ok[d] = false;
-        li[d] = 0; ljb[d] = 0; kbase[d] = 0;
+        ljb[d] = 0; kbase[d] = 0;
         if (tiles_ok && kr >= 0 && kr < a.ntr) {
             const int kt = kz * a.ntr + kr;
-            li[d] = wrapn(i - (kz * TZ - H - 1), a.nzp);
+            const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
             ljb[d] = tr0 - (kr * TR - H - 1);
-            kbase[d] = (long long)kt * tile_words + li[d];
-            ok[d] = li[d] < JW && tstamp[kt] == epoch;
+            kbase[d] = (long long)kt * tile_words + li;
+            ok[d] = li < JW && tstamp[kt] == epoch;
         }
     }
     int l = i - (int)a.zoff;
     l = l < 0 ? l + a.nzp : l;
     const bool gap = l >= a.nz;
-    const int NPL = 3 * a.nparts;
     for (int r = r0; r < CR; r += TR) {
         const int j = tr0 + r;
-        for (int pl = 0; pl < NPL; pl++) {
-            const size_t q = (size_t)pl * a.plane + (size_t)j * a.nzp + i;
-            long long v = (long long)Jacc[q];
-            Jacc[q] = 0ull;
+        const size_t q0 = (size_t)j * a.nzp + i;
+        long long v[NPL];
 #pragma unroll
-            for (int d = 0; d < 9; d++) {
-                const int lj = ljb[d] + r;
-                if (ok[d] && lj >= 0 && lj < JR)
-                    v += (long long)Jtile[kbase[d] + (long long)pl * (JR * JW) + lj * JW];
+        for (int pl = 0; pl < NPL; pl++) v[pl] = 0;
+        if (dirty) {
+#pragma unroll
+            for (int pl = 0; pl < NPL; pl++) {
+                v[pl] = (long long)Jacc[(size_t)pl * a.plane + q0];
+                Jacc[(size_t)pl * a.plane + q0] = 0ull;
             }
-            if (v > (1ll << 62) || v < -(1ll << 62)) atomicOr(err, 1);     // fixed-point headroom gone
-            const int comp = pl / a.nparts, part = pl - comp * a.nparts;
-            float f;
-            if (comp == 2) f = rowf[j];                                               // J_z
-            else if (comp == 0) f = rowf[(a.nr + 1) + j];                             // J_r
-            else f = part == 0 ? rowf[3 * (a.nr + 1) + j] : rowf[2 * (a.nr + 1) + j]; // J_phi
+        }
+#pragma unroll
+        for (int d = 0; d < 9; d++) {
+            const int lj = ljb[d] + r;
+            if (ok[d] && lj >= 0 && lj < JR) {
+                const unsigned long long *src = Jtile + kbase[d] + lj * JW;
+#pragma unroll
+                for (int pl = 0; pl < NPL; pl++) v[pl] += (long long)src[pl * (JR * JW)];
+            }
+        }
+        const float fz = rowf[j], fr = rowf[(a.nr + 1) + j];
+        const float fp = rowf[2 * (a.nr + 1) + j], fp0 = rowf[3 * (a.nr + 1) + j];
+#pragma unroll
+        for (int pl = 0; pl < NPL; pl++) {
+            if (v[pl] > (1ll << 62) || v[pl] < -(1ll << 62)) atomicOr(err, 1);   // fixed-point headroom gone
+            const int comp = pl / NP, part = pl - comp * NP;
+            const float f = comp == 2 ? fz : (comp == 0 ? fr : (part == 0 ? fp0 : fp));
             // int64 -> float from two 32-bit halves (integer conversions stay off the FP64 pipe)
-            const float fv = __int2float_rn((int)(v >> 32)) * 4294967296.f + __uint2float_rn((unsigned)v);
-            Jf[q] = gap ? 0.f : fv * inv_qscale * f;
+            const float fv = __int2float_rn((int)(v[pl] >> 32)) * 4294967296.f +
+                             __uint2float_rn((unsigned)v[pl]);
+            Jf[(size_t)pl * a.plane + q0] = gap ? 0.f : fv * inv_qscale * f;
         }
     }
 }
 
-template <int TZ, int TR>
+template <int NP, int TZ, int TR>
 static void jreduce_launch(qpic_ctx *c, const PArgs &a, int tiles_ok)
 {
-    k_jreduce<TZ, TR><<<c->ntz * c->ntr, TZ * TR, 0, c->stream>>>(
-        c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->Jf, c->rowf, a,
+    k_jreduce<NP, TZ, TR><<<c->ntz * c->ntr, TZ * TR, 0, c->stream>>>(
+        c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
         (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err);
+}
+
+template <int NP>
+static void jreduce_dispatch(qpic_ctx *c, const PArgs &a, int tiles_ok)
+{
+    if (c->TZ == 16 && c->TR == 8) jreduce_launch<NP, 16, 8>(c, a, tiles_ok);
+    else if (c->TZ == 32 && c->TR == 8) jreduce_launch<NP, 32, 8>(c, a, tiles_ok);
+    else if (c->TZ == 8 && c->TR == 8) jreduce_launch<NP, 8, 8>(c, a, tiles_ok);
+    else if (c->TZ == 16 && c->TR == 16) jreduce_launch<NP, 16, 16>(c, a, tiles_ok);
+    else jreduce_launch<NP, 32, 4>(c, a, tiles_ok);
 }
 
 void launch_jdecode(qpic_ctx *c)
@@ -990,11 +1019,12 @@ void launch_jdecode(qpic_ctx *c)
     const int JW = c->TZ + 2 * c->halo + 3;
     const int tiles_ok = c->g.nzp >= 2 * JW ? 1 : 0;
     prof_begin(c);
-    if (c->TZ == 16 && c->TR == 8) jreduce_launch<16, 8>(c, a, tiles_ok);
-    else if (c->TZ == 32 && c->TR == 8) jreduce_launch<32, 8>(c, a, tiles_ok);
-    else if (c->TZ == 8 && c->TR == 8) jreduce_launch<8, 8>(c, a, tiles_ok);
-    else if (c->TZ == 16 && c->TR == 16) jreduce_launch<16, 16>(c, a, tiles_ok);
-    else jreduce_launch<32, 4>(c, a, tiles_ok);
+    switch (c->g.nparts) {
+    case 1: jreduce_dispatch<1>(c, a, tiles_ok); break;
+    case 3: jreduce_dispatch<3>(c, a, tiles_ok); break;
+    case 5: jreduce_dispatch<5>(c, a, tiles_ok); break;
+    default: jreduce_dispatch<7>(c, a, tiles_ok); break;
+    }
     prof_end(c, KC_JDECODE);
 }
 

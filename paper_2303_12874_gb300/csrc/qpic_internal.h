@@ -81,6 +81,7 @@ struct qpic_ctx {
     unsigned long long *Jacc = nullptr;   // global-path deposits (int64 atomics)
     unsigned long long *Jtile = nullptr;  // per-tile accumulator blocks
     int *tstamp = nullptr;                // epoch at which each tile block was written
+    int *jdirty = nullptr;                // per tile: Jacc holds global-path deposits in its core
     int *d_epoch = nullptr;               // device counter stamping tile blocks
     float *rowf = nullptr;        // [4][nr+1]: J_z, J_r, J_phi(m>=1), J_phi(m=0)
     float *coef = nullptr;        // [cE (MAX_L) | cB (MAX_L) | taps (MAX_TAPS)] FP32
