@@ -365,10 +365,10 @@ def run_ours(args, w):
     # ---- CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, n, t = oracle_sample(w, dt_used, args.ref_nz, 2)
+        rate, n, t = oracle_sample(w, dt_used, args.ref_nz, args.cpu_steps)
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": "2 steps of a %d x %d periodic z-slab of the workload (%d particles), "
-                         "single-threaded FP64 C, %.1f s" % (args.ref_nz, w["nr"], n, t)}
+               "sample": "%d steps of a %d x %d periodic z-slab of the workload (%d particles), "
+                         "single-threaded FP64 C, %.1f s" % (args.cpu_steps, args.ref_nz, w["nr"], n, t)}
 
     if rank == 0:
         line = {
@@ -411,6 +411,8 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-nz", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=24,
+                    help="oracle steps timed for cpu_baseline (about 10 s on one core)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
