@@ -185,10 +185,10 @@ qpic_status qpic_set_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t m
 
 /* Charge density per mode like qpic_get_field(ctx, QPIC_FIELD_RHO, ...), but
  * without allocating any device memory.  The paper has no counterpart: this
- * entry point serves callers that cannot allocate -- code running while a
- * stream is being captured into a CUDA graph (cudaMalloc/cudaFree break a
- * capture), hosts that give the library a fixed memory budget, callers inside
- * an allocator's own callbacks.  The deposit uses a file-scope static device
+ * entry point serves callers that cannot allocate -- hosts that hand the
+ * library a fixed device-memory budget up front, code running inside a device
+ * allocator's own callbacks (which must not re-enter it), and loops that
+ * cannot afford the device-wide synchronisation of cudaFree.  The deposit uses a file-scope static device
  * array of 2^21 doubles (16 MiB) that every GPU loading the library holds until
  * exit; grids needing more than n_modes*2*(nr+1)*nz <= 2^21 doubles are
  * rejected with QPIC_EINVAL and a message.  The first call on a device looks

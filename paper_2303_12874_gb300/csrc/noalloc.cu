@@ -1,12 +1,12 @@
 // noalloc.cu -- charge density per mode without any device allocation.
 //
 // qpic_get_field(..., QPIC_FIELD_RHO, ...) deposits the density into a device
-// buffer it allocates for the call.  Some callers cannot allow that: code that
-// runs while a CUDA stream is being captured into a graph (cudaMalloc and
-// cudaFree are not capturable and would break the capture), hosts that hand
-// the library a fixed memory budget up front, and callers inside a device
-// memory allocator's own callbacks.  This entry point gives them the same
-// result using a file-scope static __device__ scratch array of fixed size.
+// buffer it allocates for the call.  Some callers cannot allow that: hosts
+// that hand the library a fixed device-memory budget up front, callers inside
+// a device memory allocator's own callbacks (which must not re-enter it), and
+// loops that cannot afford the device-wide synchronisation of cudaFree.  This
+// entry point gives them the same result using a file-scope static __device__
+// scratch array of fixed size.
 //
 // The array is part of the module: every GPU that loads the library holds its
 // 16 MiB until the process exits.  In host code the array's name is only a

@@ -1,7 +1,8 @@
 """The allocation-free charge-density entry point (qpic_charge_density_noalloc).
 
 It exists for callers that cannot allocate device memory during the call, for
-example while a stream is being captured into a CUDA graph.  Its result must
+example hosts with a fixed device-memory budget or code running inside a
+device allocator's callbacks.  Its result must
 equal the allocating path (qpic_get_field with QPIC_FIELD_RHO) -- on two calls
 in a row, so a second call does not add onto what the first left in the shared
 static array -- and grids too large for the static array are refused.
