@@ -336,6 +336,32 @@ def run_ours(args, w):
         sim2.close()
         del d
 
+    # ---- the FP32 float-atomic deposit variant on the same workload and GPU
+    fatomic = None
+    if not args.no_fatomic:
+        sim.close()
+        sfa = _make_sim(q, w, stream, precision=q.QPIC_FP32_FATOMIC)
+        _init_state(sfa, w)
+        sfa.step(args.warmup)
+        nfa = sfa.diag()["particles"]
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        sfa.step(args.fatomic_steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        msfa = g0.elapsed_time(g1)
+        sfa.profile(True, True)
+        sfa.step(2)
+        kfa = sfa.kernel_times()
+        sfa.profile(False, False)
+        gfa = kfa["gather_push_deposit"]
+        fatomic = {"value": nfa * args.fatomic_steps / (msfa / 1e3), "unit": "particle-steps/s",
+                   "ms_per_step": msfa / args.fatomic_steps, "steps": args.fatomic_steps,
+                   "gpd_ms": gfa[0] / max(gfa[1], 1), "dtype": "f32",
+                   "note": "same kernels, current summed by FP32 float atomics in global memory"}
+        sfa.close()
+
     # ---- the plain FP64 GPU path on the same workload and GPU
     fp64 = None
     if not args.no_fp64:
@@ -391,6 +417,7 @@ def run_ours(args, w):
                          "peak_source": peak_src + " (hbm_gbs, burst)",
                          "algorithmic_bytes_per_launch": gpd_bytes, "traffic": traffic},
             "fp64_gpu_path": fp64,
+            "fp32_float_atomic_path": fatomic,
             "batch_scan": batch,
             "fp32_over_fp64": (value / ws / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
@@ -411,6 +438,8 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-nz", type=int, default=100)
+    ap.add_argument("--no-fatomic", action="store_true")
+    ap.add_argument("--fatomic-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=24,
                     help="oracle steps timed for cpu_baseline (about 10 s on one core)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -74,7 +74,11 @@ typedef struct {
     int32_t solver;        /* QPIC_YEE or QPIC_DUAL */
     int32_t n_coef;        /* L coefficients per z-operator for QPIC_DUAL (Appendix A: 16) */
     double fit_band;       /* fit range k dz in (0, fit_band*pi] (a reading; default 0.8) */
-    int32_t precision;     /* QPIC_FP32_FIXED (default), QPIC_FP32_FATOMIC, QPIC_FP64 */
+    int32_t precision;     /* QPIC_FP32_FIXED (default): FP32 push and solve, int64 fixed-point
+                              current sums (bit-reproducible);
+                              QPIC_FP32_FATOMIC: the same with the current summed by FP32
+                              float atomics in global memory (order-dependent rounding);
+                              QPIC_FP64: plain FP64 path, one thread per particle */
     int32_t jz_filter;     /* 1: J_z correction so that Gauss's law holds in the dual form */
     double filter_tol;     /* filter taps kept down to |k_n| >= filter_tol |k_0| */
     int32_t periodic_z;    /* 1: periodic box; 0: open box (zero fields outside) */

@@ -14,6 +14,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqpic.so")
 SOURCES = ["api.cu", "k_fields.cu", "k_particles.cu", "host_numerics.cpp", "noalloc.cu", "k_fp64.cu"]
+# the particle kernel, one object per (mode parts, float-atomic deposit) so that
+# the instantiations compile in parallel: (object name, defines)
+GPD_OBJECTS = [("gpd_np%d_fa%d" % (np_, fa), ["-DGPD_NP=%d" % np_, "-DGPD_FA=%d" % fa])
+               for np_ in (1, 3, 5, 7) for fa in (0, 1)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -39,9 +43,10 @@ def build(force=False, verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, name, defs = job if isinstance(job, tuple) else (job, os.path.splitext(job)[0], [])
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [nvcc()] + ARCH + FLAGS + list(extra) + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd))
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,8 +56,9 @@ def build(force=False, verbose=False, extra=()):
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    jobs = [("gpd_inst.cu", name, defs) for name, defs in GPD_OBJECTS] + list(SOURCES)
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, jobs))
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -335,9 +335,11 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
         return bad(QPIC_EINVAL, "grid: need nz >= 4, nr >= 2, 1 <= n_modes <= 4");
     if (!(cfg->dz > 0) || !(cfg->dr > 0)) return bad(QPIC_EINVAL, "dz, dr must be positive");
     if (cfg->solver != QPIC_YEE && cfg->solver != QPIC_DUAL) return bad(QPIC_EINVAL, "solver");
-    if (cfg->precision != QPIC_FP32_FIXED && cfg->precision != QPIC_FP64)
-        return bad(QPIC_EINVAL, "precision: QPIC_FP32_FIXED or QPIC_FP64");
+    if (cfg->precision != QPIC_FP32_FIXED && cfg->precision != QPIC_FP64 &&
+        cfg->precision != QPIC_FP32_FATOMIC)
+        return bad(QPIC_EINVAL, "precision: QPIC_FP32_FIXED, QPIC_FP32_FATOMIC or QPIC_FP64");
     c->fp64 = cfg->precision == QPIC_FP64;
+    c->fatomic = cfg->precision == QPIC_FP32_FATOMIC;
     if (cfg->moving_window && cfg->periodic_z) return bad(QPIC_EINVAL, "moving window needs periodic_z = 0");
     c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     c->dz = cfg->dz;
@@ -389,9 +391,11 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     } else if (!alloc_arr(c, &c->E, nplanes * g.plane) || !alloc_arr(c, &c->B, nplanes * g.plane) ||
                !alloc_arr(c, &c->Bb, nplanes * g.plane) || !alloc_arr(c, &c->Jf, nplanes * g.plane) ||
                !alloc_arr(c, &c->Jzf, (size_t)g.nparts * g.plane) ||
-               !alloc_arr(c, &c->Jacc, nplanes * g.plane)) {
+               !alloc_arr(c, &c->Jacc, nplanes * g.plane) ||
+               (c->fatomic && !alloc_arr(c, &c->Jfa, nplanes * g.plane))) {
         return bad(QPIC_ENOMEM, "field buffers: device allocation failed");
     }
+    if (c->fatomic) cudaMemsetAsync(c->Jfa, 0, nplanes * g.plane * sizeof(float), c->stream);
     if (!alloc_arr(c, &c->rowf, (size_t)4 * (g.nr + 1)) ||
         !alloc_arr(c, &c->coef, (size_t)2 * MAX_L + MAX_TAPS) ||
         !alloc_arr(c, &c->coef64, (size_t)2 * MAX_L + MAX_TAPS) || !alloc_arr(c, &c->d_err, 4) ||

@@ -1,872 +1,11 @@
-// k_particles.cu -- the particle half of the quasi-3D PIC step (FP32 path).
-//
-// k_gpd: one CTA per particle tile (TZ x TR cells, particles sorted by tile).
-//   1. E^n and Bbar^n of the tile plus a halo are staged in shared memory
-//      (mode-parity images below the axis, even images beyond the wall, zeros
-//      in the gap of an open box), so the gather never branches on boundaries.
-//   2. per particle: bilinear gather of every mode at each component's own
-//      staggered point, modal sum F_0 + 2 Re(F_m e^{i m phi}) (Sec. III.B),
-//      rotation to x, y; relativistic Boris push with E^n and Bbar^n
-//      (Eq. 6 time-centred as in Eq. 12); Cartesian move and an update of
-//      (r, cos phi, sin phi) written with cancellation-free differences;
-//      optional modal work (Eq. 16).
-//   3. charge-conserving deposit per mode into int64 fixed-point shared
-//      accumulators.  The modal charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
-//      splits into (S1 - S0)(e0 + e1)/2, carried by 2D Esirkepov r/z fluxes,
-//      and (S0 + S1)/2 (e1 - e0), carried by J_phi through (i m / r) J_phi.
-//   4. the tile's accumulators go to global memory with int64 atomics; integer
-//      addition makes the step independent of particle order (bit-reproducible).
-//   Particles beyond the staged halo (drift between sorts, or injected by the
-//   moving window) run the same code against global memory.
+// k_particles.cu -- launchers of the particle kernels (gpd.cuh), the particle
+// sort, loading, export and the particle diagnostics (FP32 path).
 //
 // k_count / scan / k_scatter: counting sort of live particles by a tile-major
 // cell key; dead particles are dropped.
-#include <cuda_runtime.h>
-#include <math.h>
-#include <stdint.h>
-
-#include "qpic_internal.h"
+#include "gpd.cuh"
 
 namespace qpic {
-
-struct PArgs {
-    int nz, nr, nzp, nparts, nm;
-    long long zoff;
-    size_t plane;
-    float dz, dr, dt, inv_dz, inv_dr, R;
-    int periodic;
-    int TZ, TR, ntz, ntr, H, lTZ, lTR;
-    float qscale;
-    int track_work;
-};
-
-static PArgs pargs(const qpic_ctx *c)
-{
-    PArgs a;
-    a.nz = c->g.nz; a.nr = c->g.nr; a.nzp = c->g.nzp; a.nparts = c->g.nparts; a.nm = c->g.nm;
-    a.zoff = c->g.zoff % c->g.nzp; a.plane = c->g.plane;
-    a.dz = (float)c->dz; a.dr = (float)c->dr; a.dt = (float)c->dt;
-    a.inv_dz = (float)(1.0 / c->dz); a.inv_dr = (float)(1.0 / c->dr);
-    a.R = (float)(c->g.nr * c->dr);
-    a.periodic = c->g.periodic;
-    a.TZ = c->TZ; a.TR = c->TR; a.ntz = c->ntz; a.ntr = c->ntr; a.H = c->halo;
-    a.lTZ = __builtin_ctz(c->TZ); a.lTR = __builtin_ctz(c->TR);
-    a.qscale = c->qscale;
-    a.track_work = c->cfg.track_work;
-    return a;
-}
-
-__host__ __device__ __forceinline__ int imin(int x, int y) { return x < y ? x : y; }
-
-__device__ __forceinline__ int pwrap(int i, int n)
-{
-    int r = i % n;
-    return r < 0 ? r + n : r;
-}
-
-// staggering: E_r (0,1) E_phi (0,0) E_z (1,0); B_r (1,0) B_phi (1,1) B_z (0,1)
-__host__ __device__ __forceinline__ int hz_of(int fb, int c) { return fb == 0 ? (c == 2) : (c != 2); }
-__host__ __device__ __forceinline__ int hr_of(int fb, int c) { return fb == 0 ? (c == 0) : (c != 0); }
-
-// sample of plane (fb: 0 = E, 1 = Bbar; comp c; part p) at physical column col
-// (any integer, wrapped) and row j (any integer).  Half-r components continue
-// below the axis with the mode parity (radial/azimuthal (-1)^(m+1), B_z (-1)^m)
-// and beyond the wall with their even image; integer-r components are 0 outside.
-__device__ __forceinline__ float gsample_at(const float *E, const float *Bb, const PArgs &a, int fb,
-                                            int c, int p, int j, int ic);
-
-__device__ __forceinline__ float gsample(const float *E, const float *Bb, const PArgs &a, int fb,
-                                         int c, int p, int j, int col)
-{
-    return gsample_at(E, Bb, a, fb, c, p, j, pwrap(col, a.nzp));
-}
-
-// as gsample, for a column ic already in [0, nzp)
-__device__ __forceinline__ float gsample_at(const float *E, const float *Bb, const PArgs &a, int fb,
-                                            int c, int p, int j, int ic)
-{
-    const float *F = fb == 0 ? E : Bb;
-    float sgn = 1.f;
-    if (hr_of(fb, c)) {
-        if (j < 0) {
-            int m = (p + 1) >> 1;
-            bool longitudinal = (fb == 1 && c == 2);
-            bool odd = ((m & 1) != 0) != !longitudinal;   // radial: (-1)^(m+1); z: (-1)^m
-            sgn = odd ? -1.f : 1.f;
-            j = -1 - j;
-        }
-        if (j >= a.nr) j = 2 * a.nr - 1 - j;
-        if (j < 0 || j >= a.nr) return 0.f;
-    } else {
-        if (j < 0 || j > a.nr) return 0.f;
-    }
-    return sgn * F[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic];
-}
-
-// ------------------------------------------------------------ accessors
-// Staged tile of E and Bbar: per (field, component, row, column) node the NP
-// mode parts are packed in V = ceil(NP/4) float4 words, so a gather corner is
-// one (or two) 16-byte shared loads.  Current accumulators: int64 per
-// (component, part, row, column).
-template <int NP, int TZ, int TR>
-struct TileGeom {
-    static constexpr int H = 1;                    // halo of cells around the tile
-    static constexpr int FW = TZ + 2 * H + 2, FR = TR + 2 * H + 2;   // staged fields
-    static constexpr int JW = FW + 1, JR = FR + 1;                   // accumulators
-    static constexpr int V = (NP + 3) / 4;
-    static constexpr int JWORDS = 3 * NP * JW * JR;                   // int64 words
-    static constexpr int JPAD = (JWORDS + 1) & ~1;                    // keeps the float4 tile 16-B aligned
-    static constexpr int FVEC = 2 * 3 * FR * FW * V;                  // float4 words
-    static constexpr int NM = (NP + 1) / 2;
-    static constexpr int QW = 8 + 4 * (NM - 1);                       // words per queued move
-    static constexpr int QCAP = 512;                                  // queued cell-crossing moves
-    static constexpr int PB = 9 * 256;      // prefetched words per buffer: 256 cells, 2 x 256 float4
-    static constexpr size_t SMEM =
-        (size_t)JPAD * 8 + (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
-    static_assert((JPAD * 8) % 16 == 0, "float4 tile alignment");
-};
-
-template <int NP, int TZ, int TR>
-struct SmemAcc {
-    using G = TileGeom<NP, TZ, TR>;
-    const float4 *sf;            // [2][3][FR][FW][V]
-    unsigned long long *sJ;      // [3][NP][JR][JW]
-    __device__ __forceinline__ void node(int fb, int c, int lj, int li, float out[NP]) const
-    {
-        const float4 *q = sf + ((size_t)((fb * 3 + c) * G::FR + lj) * G::FW + li) * G::V;
-#pragma unroll
-        for (int v = 0; v < G::V; v++) {
-            const float4 t = q[v];
-            if (4 * v + 0 < NP) out[4 * v + 0] = t.x;
-            if (4 * v + 1 < NP) out[4 * v + 1] = t.y;
-            if (4 * v + 2 < NP) out[4 * v + 2] = t.z;
-            if (4 * v + 3 < NP) out[4 * v + 3] = t.w;
-        }
-    }
-    __device__ __forceinline__ void jadd(int c, int p, int lj, int li, long long v) const
-    {
-        if (v) atomicAdd(&sJ[((size_t)(c * NP + p) * G::JR + lj) * G::JW + li], (unsigned long long)v);
-    }
-};
-
-template <int NP>
-struct GlobAcc {
-    const float *E, *Bb;
-    unsigned long long *J;
-    int *dirty;                  // per tile: its core received a global-path deposit
-    PArgs a;
-    __device__ __forceinline__ void node(int fb, int c, int j, int i, float out[NP]) const
-    {
-#pragma unroll
-        for (int p = 0; p < NP; p++) out[p] = gsample(E, Bb, a, fb, c, p, j, i);
-    }
-    __device__ __forceinline__ void jadd(int c, int p, int j, int i, long long v) const
-    {
-        if (!v || j < 0 || j > a.nr) return;
-        int ic = pwrap(i, a.nzp);
-        atomicAdd(&J[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic],
-                  (unsigned long long)v);
-        const int tr = imin(j >> a.lTR, a.ntr - 1);
-        dirty[(ic >> a.lTZ) * a.ntr + tr] = 1;
-    }
-};
-
-// Exact round-to-nearest of a scaled contribution |v| < 2^42 into hi*2^20 + lo
-// (|lo| <= 2^19) using only FP32 adds: t + 1.5*2^23 has unit spacing, so its
-// bit pattern minus that of 1.5*2^23 is round(t).  (A float->int64 conversion
-// would run on the FP64 pipe, which is narrow on this part.)
-__device__ __forceinline__ void fx_split(float v, int &hi, int &lo)
-{
-    const float M = 12582912.0f;                       // 1.5 * 2^23
-    const float t = __fmul_rn(v, 9.5367431640625e-07f); // v * 2^-20 (exact)
-    const float tm = __fadd_rn(t, M);
-    hi = __float_as_int(tm) - 0x4B400000;
-    const float hf = __fsub_rn(tm, M);                  // round(t), exact
-    const float r = __fmaf_rn(-hf, 1048576.0f, v);      // v - hi * 2^20, exact
-    lo = __float_as_int(__fadd_rn(r, M)) - 0x4B400000;
-}
-
-__device__ __forceinline__ long long fx(float x, float qs)
-{
-    int hi, lo;
-    fx_split(x * qs, hi, lo);
-    return ((long long)hi << 20) + lo;
-}
-
-__device__ __forceinline__ int wrapn(int i, int n)      // for i in [-n, 2n)
-{
-    i = i < 0 ? i + n : i;
-    return i >= n ? i - n : i;
-}
-
-// Linear-shape values S0 and differences dS = S1 - S0 at nodes k = -1..2 (index
-// k+1) for a move x0 -> x0 + d in old-cell coordinates (x0 in [0,1), |d| < 1).
-// A move inside the cell gives dS = (-d, +d) exactly, without cancellation.
-__device__ __forceinline__ void shape_delta(float x0, float d, float S0[4], float dS[4], int &lo,
-                                            int &hi)
-{
-    float x1 = x0 + d;
-    S0[0] = 0.f; S0[1] = 1.f - x0; S0[2] = x0; S0[3] = 0.f;
-    if (x1 >= 1.f) {
-        dS[0] = 0.f; dS[1] = x0 - 1.f; dS[2] = (2.f - 2.f * x0) - d; dS[3] = (x0 - 1.f) + d;
-        lo = 1; hi = 3;
-    } else if (x1 < 0.f) {
-        dS[0] = -(x0 + d); dS[1] = 2.f * x0 + d; dS[2] = -x0; dS[3] = 0.f;
-        lo = 0; hi = 2;
-    } else {
-        dS[0] = 0.f; dS[1] = -d; dS[2] = d; dS[3] = 0.f;
-        lo = 1; hi = 2;
-    }
-}
-
-// approximate square root (PTX sqrt.approx, relative error ~2^-23); the move
-// needs no IEEE rounding (charge conservation uses the displacement as computed)
-__device__ __forceinline__ float sqrt_fast(float x)
-{
-    float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-struct PState {
-    float oz, orr, cph, sph, ux, uy, uz, w, W0, W1;
-    int jr;          // r cell (absolute)
-    int diz, djr;    // cell change of the move
-};
-
-// what the deposit needs from the move: old offsets, displacement in cells,
-// charge, e^{-i m phi} at the start and its change, and the m = 0 azimuthal
-// displacement (x0 dy - y0 dx)/(r_mid dr)
-template <int NM>
-struct DepIn {
-    float oz0, or0, dzc, drc, Q, aphi;
-    float e0r[NM], e0i[NM], der[NM], dei[NM];
-};
-
-// Gather, push and move one particle.  (bi, bj): accessor coordinates of its
-// cell.  On return s holds the new state and d the deposit inputs.
-template <int NP, class Acc>
-__device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi, int bj, PState &s,
-                                          DepIn<(NP + 1) / 2> &d)
-{
-    constexpr int NM = (NP + 1) / 2;
-    const float oz = s.oz, orr = s.orr, cph = s.cph, sph = s.sph;
-    // ---- interpolation weights on the integer and half grids
-    const int ozh = oz >= 0.5f ? 0 : -1, orh = orr >= 0.5f ? 0 : -1;
-    const float wzH = oz >= 0.5f ? oz - 0.5f : oz + 0.5f;
-    const float wrH = orr >= 0.5f ? orr - 0.5f : orr + 0.5f;
-    // bilinear weights of the four staggering classes (half z?, half r?)
-    const float tzs[2] = {oz, wzH}, trs[2] = {orr, wrH};
-    float W[2][2][4];
-#pragma unroll
-    for (int hz = 0; hz < 2; hz++)
-#pragma unroll
-        for (int hr = 0; hr < 2; hr++) {
-            const float tz = tzs[hz], tr = trs[hr], uz = 1.f - tz, ur = 1.f - tr;
-            W[hz][hr][0] = uz * ur; W[hz][hr][1] = tz * ur;
-            W[hz][hr][2] = uz * tr; W[hz][hr][3] = tz * tr;
-        }
-    float F[2][3][NP];
-#pragma unroll
-    for (int fb = 0; fb < 2; fb++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int hz = hz_of(fb, c), hr = hr_of(fb, c);
-            const int i0 = bi + (hz ? ozh : 0), j0 = bj + (hr ? orh : 0);
-            const float *w = W[hz][hr];
-            float v00[NP], v01[NP], v10[NP], v11[NP];
-            acc.node(fb, c, j0, i0, v00);
-            acc.node(fb, c, j0, i0 + 1, v01);
-            acc.node(fb, c, j0 + 1, i0, v10);
-            acc.node(fb, c, j0 + 1, i0 + 1, v11);
-#pragma unroll
-            for (int p = 0; p < NP; p++)
-                F[fb][c][p] = w[0] * v00[p] + w[1] * v01[p] + w[2] * v10[p] + w[3] * v11[p];
-        }
-    // ---- modal sum, rotation to Cartesian
-    float cm[NM], sm[NM];
-    cm[0] = 1.f; sm[0] = 0.f;
-#pragma unroll
-    for (int m = 1; m < NM; m++) {
-        cm[m] = cm[m - 1] * cph - sm[m - 1] * sph;
-        sm[m] = sm[m - 1] * cph + cm[m - 1] * sph;
-    }
-    float Ec[3], Bc[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        float e = F[0][c][0], b = F[1][c][0];
-#pragma unroll
-        for (int m = 1; m < NM; m++) {
-            e += 2.f * (F[0][c][2 * m - 1] * cm[m] - F[0][c][2 * m] * sm[m]);
-            b += 2.f * (F[1][c][2 * m - 1] * cm[m] - F[1][c][2 * m] * sm[m]);
-        }
-        Ec[c] = e; Bc[c] = b;
-    }
-    const float Ex = Ec[0] * cph - Ec[1] * sph, Ey = Ec[0] * sph + Ec[1] * cph, Ez = Ec[2];
-    const float Bx = Bc[0] * cph - Bc[1] * sph, By = Bc[0] * sph + Bc[1] * cph, Bz = Bc[2];
-    // ---- relativistic Boris push, q = -1
-    const float h = -0.5f * a.dt;
-    const float ux = s.ux, uy = s.uy, uz = s.uz;
-    float umx = ux + h * Ex, umy = uy + h * Ey, umz = uz + h * Ez;
-    float igm = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
-    float tx = h * Bx * igm, ty = h * By * igm, tz = h * Bz * igm;
-    float t2 = tx * tx + ty * ty + tz * tz;
-    float f2 = 2.f / (1.f + t2);
-    float sx = f2 * tx, sy = f2 * ty, sz = f2 * tz;
-    float upx = umx + (umy * tz - umz * ty);
-    float upy = umy + (umz * tx - umx * tz);
-    float upz = umz + (umx * ty - umy * tx);
-    float unx = umx + (upy * sz - upz * sy) + h * Ex;
-    float uny = umy + (upz * sx - upx * sz) + h * Ey;
-    float unz = umz + (upx * sy - upy * sx) + h * Ez;
-    const float ig = rsqrtf(1.f + unx * unx + uny * uny + unz * unz);
-    const float vx = unx * ig, vy = uny * ig, vz = unz * ig;
-    if (a.track_work) {
-        // Eq. 16: W_m += q dt E^m . v, v at time n the mean of u/gamma at n -+ 1/2
-        const float igo = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
-        float wx = 0.5f * (ux * igo + vx), wy = 0.5f * (uy * igo + vy), wz = 0.5f * (uz * igo + vz);
-        float E0x = F[0][0][0] * cph - F[0][1][0] * sph, E0y = F[0][0][0] * sph + F[0][1][0] * cph;
-        float p0 = E0x * wx + E0y * wy + F[0][2][0] * wz;
-        float pt = Ex * wx + Ey * wy + Ez * wz;
-        s.W0 -= a.dt * p0;
-        s.W1 -= a.dt * (pt - p0);
-    }
-    // ---- move in Cartesian x, y; r and angle with cancellation-free differences
-    const float ddz = a.dt * vz;
-    float ddx = a.dt * vx, ddy = a.dt * vy;
-    const float r0 = ((float)s.jr + orr) * a.dr;
-    const float x0 = r0 * cph, y0 = r0 * sph;
-    float x1 = x0 + ddx, y1 = y0 + ddy;
-    float r1 = sqrt_fast(x1 * x1 + y1 * y1);
-    float drr, c1, s1, dc, ds;
-    if (r1 <= a.R) {
-        float den = r0 + r1;
-        drr = den > 0.f ? __fdividef(ddx * (2.f * x0 + ddx) + ddy * (2.f * y0 + ddy), den) : 0.f;
-        if (r1 > 0.f) {
-            float ir = __fdividef(1.f, r1);
-            c1 = x1 * ir; s1 = y1 * ir;
-            dc = (ddx - cph * drr) * ir; ds = (ddy - sph * drr) * ir;
-        } else {
-            c1 = cph; s1 = sph; dc = 0.f; ds = 0.f;
-        }
-    } else {                               // specular reflection at the wall
-        float cr = x1 / r1, sr = y1 / r1;
-        float urad = unx * cr + uny * sr;
-        unx -= 2.f * urad * cr; uny -= 2.f * urad * sr;
-        float rn = 2.f * a.R - r1;
-        x1 = cr * rn; y1 = sr * rn; r1 = rn;
-        ddx = x1 - x0; ddy = y1 - y0;
-        drr = r1 - r0; c1 = cr; s1 = sr; dc = c1 - cph; ds = s1 - sph;
-    }
-    const float dzc = ddz * a.inv_dz, drc = drr * a.inv_dr;
-    // ---- deposit inputs
-    d.oz0 = oz; d.or0 = orr; d.dzc = dzc; d.drc = drc; d.Q = -s.w;
-    d.e0r[0] = 1.f; d.e0i[0] = 0.f; d.der[0] = 0.f; d.dei[0] = 0.f;
-    if (NM > 1) {
-        const float a0r = cph, a0i = -sph, adr = dc, adi = -ds;     // e0_1, de_1
-        const float a1r = a0r + adr, a1i = a0i + adi;                // e1_1
-        d.e0r[1] = a0r; d.e0i[1] = a0i; d.der[1] = adr; d.dei[1] = adi;
-#pragma unroll
-        for (int m = 2; m < NM; m++) {
-            // e0_m = e0_{m-1} e0_1 ; de_m = de_{m-1} e1_1 + e0_{m-1} de_1
-            d.e0r[m] = d.e0r[m - 1] * a0r - d.e0i[m - 1] * a0i;
-            d.e0i[m] = d.e0r[m - 1] * a0i + d.e0i[m - 1] * a0r;
-            d.der[m] = d.der[m - 1] * a1r - d.dei[m - 1] * a1i + d.e0r[m - 1] * adr - d.e0i[m - 1] * adi;
-            d.dei[m] = d.der[m - 1] * a1i + d.dei[m - 1] * a1r + d.e0r[m - 1] * adi + d.e0i[m - 1] * adr;
-        }
-    }
-    const float xm = x0 + 0.5f * ddx, ym = y0 + 0.5f * ddy;
-    const float rm = sqrt_fast(xm * xm + ym * ym);
-    d.aphi = rm > 0.f ? __fdividef(x0 * ddy - y0 * ddx, rm * a.dr) : 0.f;
-    // ---- new state: offsets renormalised into the cell
-    float nz_ = oz + dzc, nr_ = orr + drc;
-    int diz = 0, djr = 0;
-    if (nz_ >= 1.f) { nz_ -= 1.f; diz = 1; } else if (nz_ < 0.f) { nz_ += 1.f; diz = -1; }
-    if (nz_ >= 1.f) nz_ = 0.99999994f;          // rounding guard
-    if (nr_ >= 1.f) { nr_ -= 1.f; djr = 1; } else if (nr_ < 0.f) { nr_ += 1.f; djr = -1; }
-    if (nr_ >= 1.f) nr_ = 0.99999994f;
-    if (s.jr + djr >= a.nr) { djr = a.nr - 1 - s.jr; nr_ = 0.99999994f; }   // r = R exactly
-    if (s.jr + djr < 0) { djr = -s.jr; nr_ = 0.f; }
-    s.oz = nz_; s.orr = nr_; s.cph = c1; s.sph = s1;
-    s.ux = unx; s.uy = uny; s.uz = unz;
-    s.diz = diz; s.djr = djr;
-}
-
-// True when the move stays inside its cell in z and r (the common case).
-template <int NM>
-__device__ __forceinline__ bool same_cell(const DepIn<NM> &d)
-{
-    const float xz = d.oz0 + d.dzc, xr = d.or0 + d.drc;
-    return xz >= 0.f && xz < 1.f && xr >= 0.f && xr < 1.f;
-}
-
-// Charge-conserving deposit of one move, any cell crossing (2D Esirkepov fluxes
-// times (e0+e1)/2 per mode, J_phi from the phase change), direct atomics.
-template <int NP, class Acc>
-__device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, int bi, int bj,
-                                                const DepIn<(NP + 1) / 2> &d)
-{
-    constexpr int NM = (NP + 1) / 2;
-    float S0z[4], dSz[4], S0r[4], dSr[4];
-    int zlo, zhi, rlo, rhi;
-    shape_delta(d.oz0, d.dzc, S0z, dSz, zlo, zhi);
-    shape_delta(d.or0, d.drc, S0r, dSr, rlo, rhi);
-    const float Q = d.Q, qs = a.qscale;
-    // z fluxes through faces (i0+k+1/2, j0+kr): prefix sums of W^z along z
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-        if (b < rlo || b > rhi) continue;
-        const float srb = S0r[b] + 0.5f * dSr[b];
-        float accw = 0.f;
-#pragma unroll
-        for (int a2 = 0; a2 < 3; a2++) {
-            if (a2 < zlo || a2 >= zhi) continue;
-            accw += dSz[a2] * srb;
-            const float X = -Q * accw;
-            const int lj = bj + b - 1, li = bi + a2 - 1;
-            acc.jadd(2, 0, lj, li, fx(X, qs));
-#pragma unroll
-            for (int m = 1; m < NM; m++) {
-                float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
-                acc.jadd(2, 2 * m - 1, lj, li, fx(X * ebr, qs));
-                acc.jadd(2, 2 * m, lj, li, fx(X * ebi, qs));
-            }
-        }
-    }
-    // r fluxes through faces (i0+k, j0+kr+1/2): prefix sums of W^r along r
-#pragma unroll
-    for (int a2 = 0; a2 < 4; a2++) {
-        if (a2 < zlo || a2 > zhi) continue;
-        const float sza = S0z[a2] + 0.5f * dSz[a2];
-        float accw = 0.f;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            if (b < rlo || b >= rhi) continue;
-            accw += dSr[b] * sza;
-            const float X = -Q * accw;
-            const int lj = bj + b - 1, li = bi + a2 - 1;
-            acc.jadd(0, 0, lj, li, fx(X, qs));
-#pragma unroll
-            for (int m = 1; m < NM; m++) {
-                float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
-                acc.jadd(0, 2 * m - 1, lj, li, fx(X * ebr, qs));
-                acc.jadd(0, 2 * m, lj, li, fx(X * ebi, qs));
-            }
-        }
-    }
-    // azimuthal current at nodes: m = 0 from the mid-point azimuthal displacement,
-    // m >= 1 from i Q Sbar (e1 - e0) / m
-#pragma unroll
-    for (int a2 = 0; a2 < 4; a2++) {
-        if (a2 < zlo || a2 > zhi) continue;
-#pragma unroll
-        for (int b = 0; b < 4; b++) {
-            if (b < rlo || b > rhi) continue;
-            const float sb = S0z[a2] * S0r[b] +
-                             0.5f * (S0z[a2] * dSr[b] + dSz[a2] * S0r[b] + dSz[a2] * dSr[b]);
-            const int lj = bj + b - 1, li = bi + a2 - 1;
-            const float QS = Q * sb;
-            acc.jadd(1, 0, lj, li, fx(QS * d.aphi, qs));
-#pragma unroll
-            for (int m = 1; m < NM; m++) {
-                const float im = 1.f / (float)m;
-                acc.jadd(1, 2 * m - 1, lj, li, fx(-QS * d.dei[m] * im, qs));
-                acc.jadd(1, 2 * m, lj, li, fx(QS * d.der[m] * im, qs));
-            }
-        }
-    }
-}
-
-// Same-cell deposits summed in registers.  A thread takes consecutive particles
-// of its tile (see tile_slot), so successive moves mostly stay in one cell and
-// go to the same 8*NP accumulator words (J_z at 2 faces, J_r at 2 faces, J_phi
-// at 4 nodes, each per part).  Each contribution is rounded to the int64 fixed
-// point exactly as fx() does, kept as hi*2^20 + lo, and the two halves are
-// summed in 32-bit registers; the biased bit patterns of the rounding sums
-// (1.5*2^23 + hi) are added directly and the bias is removed once per flush.
-// Integer sums make the result independent of particle order.  A flush adds
-// the int64 totals to the tile's shared accumulators when the cell changes and
-// at the end of each chunk.  Tile geometry is compile-time, so every
-// accumulator offset is an immediate.
-template <int NP, int TZ, int TR>
-struct FastSum {
-    using G = TileGeom<NP, TZ, TR>;
-    static constexpr int NV = 8 * NP;
-    static constexpr int PL = G::JR * G::JW;           // words per accumulator plane
-    unsigned hs[NV], ls[NV];
-    unsigned n;                                         // moves summed since the last flush
-    int key;                                            // (lj << 12) | li of those moves
-
-    __device__ __forceinline__ void clear()
-    {
-#pragma unroll
-        for (int i = 0; i < NV; i++) { hs[i] = 0u; ls[i] = 0u; }
-        n = 0u;
-        key = -1;
-    }
-    // accumulator word of value i relative to the cell's (lj, li)
-    static __device__ __forceinline__ constexpr int off(int i)
-    {
-        const int p = i >> 3, e = i & 7;
-        return e == 0 ? (2 * NP + p) * PL
-             : e == 1 ? (2 * NP + p) * PL + G::JW
-             : e == 2 ? p * PL
-             : e == 3 ? p * PL + 1
-                      : (NP + p) * PL + ((e - 4) & 1) + ((e - 4) >> 1) * G::JW;
-    }
-    // t = contribution * qscale * 2^-20, |t| < 2^22
-    __device__ __forceinline__ void put(int i, float t)
-    {
-        const float M = 12582912.0f;                    // 1.5 * 2^23
-        const float tm = __fadd_rn(t, M);               // bits: 0x4B400000 + round(t)
-        hs[i] += __float_as_uint(tm);
-        const float r = __fsub_rn(t, __fsub_rn(tm, M)); // t - round(t), exact
-        ls[i] += __float_as_uint(__fmaf_rn(r, 1048576.0f, M));
-    }
-    __device__ __forceinline__ void add(const DepIn<(NP + 1) / 2> &d, float q20)
-    {
-        constexpr int NM = (NP + 1) / 2;
-        const float dz_ = d.dzc, dr_ = d.drc;
-        const float Sz0 = (1.f - d.oz0) - 0.5f * dz_, Sz1 = d.oz0 + 0.5f * dz_;
-        const float Sr0 = (1.f - d.or0) - 0.5f * dr_, Sr1 = d.or0 + 0.5f * dr_;
-        const float c4 = 0.25f * dz_ * dr_;
-        const float qz = q20 * dz_, qr = q20 * dr_;
-        const float Xz0 = qz * Sr0, Xz1 = qz * Sr1;    // J_z at (i0+1/2, j0+b)
-        const float Xr0 = qr * Sz0, Xr1 = qr * Sz1;    // J_r at (i0+a, j0+1/2)
-        // J_phi at (i0+a, j0+b): Sbar_ab = Sz_a Sr_b + (dSz_a dSr_b)/4
-        const float QS[4] = {q20 * (Sz0 * Sr0 + c4), q20 * (Sz1 * Sr0 - c4),
-                             q20 * (Sz0 * Sr1 - c4), q20 * (Sz1 * Sr1 + c4)};
-        put(0, Xz0); put(1, Xz1); put(2, Xr0); put(3, Xr1);
-#pragma unroll
-        for (int k = 0; k < 4; k++) put(4 + k, QS[k] * d.aphi);      // m = 0: azimuthal displacement
-#pragma unroll
-        for (int m = 1; m < NM; m++) {
-            const float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
-            const float im = 1.f / (float)m;
-            const int pr = 8 * (2 * m - 1), pi = 8 * (2 * m);
-            put(pr + 0, Xz0 * ebr); put(pr + 1, Xz1 * ebr); put(pr + 2, Xr0 * ebr); put(pr + 3, Xr1 * ebr);
-            put(pi + 0, Xz0 * ebi); put(pi + 1, Xz1 * ebi); put(pi + 2, Xr0 * ebi); put(pi + 3, Xr1 * ebi);
-#pragma unroll
-            for (int k = 0; k < 4; k++) {                            // m >= 1: i Q Sbar (e1 - e0)/m
-                put(pr + 4 + k, -QS[k] * d.dei[m] * im);
-                put(pi + 4 + k, QS[k] * d.der[m] * im);
-            }
-        }
-        n += 1u;
-    }
-    __device__ __forceinline__ void flush(unsigned long long *sJ)
-    {
-        if (n == 0u) return;
-        unsigned long long *b = sJ + (key >> 12) * G::JW + (key & 0xFFF);
-        const unsigned bias = 0x4B400000u * n;
-#pragma unroll
-        for (int i = 0; i < NV; i++) {
-            const long long w = ((long long)(int)(hs[i] - bias) << 20) + (long long)(int)(ls[i] - bias);
-            atomicAdd(b + off(i), (unsigned long long)w);
-            hs[i] = 0u; ls[i] = 0u;
-        }
-        n = 0u;
-    }
-};
-
-// ------------------------------------------------------------ the GPD kernel
-// Particle order inside a tile.  The n particles of a tile (sorted by cell) are
-// taken in chunks: full chunks of GPD_C = GPD_T * GPD_K, then the rest (rc <
-// GPD_C).  In a chunk every thread takes kc consecutive particles (GPD_K in a
-// full chunk, kc = ceil(rc / GPD_T) in the last; nt = rc / kc threads take kc,
-// thread nt the rem = rc - nt kc left), so one thread's moves mostly share a
-// cell (FastSum).  Thread t's k-th particle of a chunk is q0 + t kc + k.
-constexpr int GPD_T = 256, GPD_K = 8, GPD_C = GPD_T * GPD_K;
-
-struct Chunk { int q0, rc, kc, nt, rem; };
-
-__host__ __device__ __forceinline__ int tile_nchunks(int n) { return (n + GPD_C - 1) / GPD_C; }
-
-__host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c)
-{
-    const int nfull = n / GPD_C;
-    Chunk k;
-    if (c < nfull) {
-        k.q0 = c * GPD_C; k.rc = GPD_C; k.kc = GPD_K; k.nt = GPD_T; k.rem = 0;
-    } else {
-        k.q0 = nfull * GPD_C;
-        k.rc = n - k.q0;
-        k.kc = (k.rc + GPD_T - 1) / GPD_T;
-        k.nt = k.rc / k.kc;
-        k.rem = k.rc - k.nt * k.kc;
-    }
-    return k;
-}
-
-// Ampere-style asynchronous 4-byte global -> shared copies (one per thread and
-// word); a thread waits only for its own groups
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// one particle record (two float4 words, 32-byte aligned) in a single 256-bit access
-__device__ __forceinline__ void ld_rec(const float4 *p, float4 &a, float4 &b)
-{
-    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-                 : "l"(p));
-}
-__device__ __forceinline__ void st_rec(float4 *p, const float4 &a, const float4 &b)
-{
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y),
-                 "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// cell index of a particle: (iz_phys << 16) | jr
-__host__ __device__ __forceinline__ int cell_iz(int cell) { return cell >> 16; }
-__host__ __device__ __forceinline__ int cell_jr(int cell) { return cell & 0xFFFF; }
-__host__ __device__ __forceinline__ int make_cell(int iz, int jr) { return (iz << 16) | jr; }
-
-// queued cell-crossing move: local cell, offsets, displacement, charge,
-// azimuthal displacement, then e0/de per mode m >= 1
-template <int NM>
-__device__ __forceinline__ void queue_put(float *q, int li, int lj, const DepIn<NM> &d)
-{
-    q[0] = __int_as_float(li); q[1] = __int_as_float(lj);
-    q[2] = d.oz0; q[3] = d.or0; q[4] = d.dzc; q[5] = d.drc; q[6] = d.Q; q[7] = d.aphi;
-#pragma unroll
-    for (int m = 1; m < NM; m++) {
-        q[8 + 4 * (m - 1)] = d.e0r[m]; q[9 + 4 * (m - 1)] = d.e0i[m];
-        q[10 + 4 * (m - 1)] = d.der[m]; q[11 + 4 * (m - 1)] = d.dei[m];
-    }
-}
-
-template <int NM>
-__device__ __forceinline__ void queue_get(const float *q, int &li, int &lj, DepIn<NM> &d)
-{
-    li = __float_as_int(q[0]); lj = __float_as_int(q[1]);
-    d.oz0 = q[2]; d.or0 = q[3]; d.dzc = q[4]; d.drc = q[5]; d.Q = q[6]; d.aphi = q[7];
-    d.e0r[0] = 1.f; d.e0i[0] = 0.f; d.der[0] = 0.f; d.dei[0] = 0.f;
-#pragma unroll
-    for (int m = 1; m < NM; m++) {
-        d.e0r[m] = q[8 + 4 * (m - 1)]; d.e0i[m] = q[9 + 4 * (m - 1)];
-        d.der[m] = q[10 + 4 * (m - 1)]; d.dei[m] = q[11 + 4 * (m - 1)];
-    }
-}
-
-template <int NP, int TZ, int TR>
-__global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__restrict__ E,
-                                                 const float *__restrict__ Bb,
-                                                 unsigned long long *__restrict__ J,
-                                                 unsigned long long *__restrict__ Jtile,
-                                                 int *__restrict__ tstamp, int *__restrict__ jdirty,
-                                                 const int *__restrict__ d_epoch,
-                                                 const int32_t *__restrict__ offsets,
-                                                 const long long *__restrict__ dcount, PArgs a,
-                                                 int ntiles, int tail_chunk)
-{
-    using G = TileGeom<NP, TZ, TR>;
-    constexpr int NM = (NP + 1) / 2;
-    extern __shared__ __align__(16) unsigned long long sraw[];
-    long long begin, end;
-    const bool tile_mode = blockIdx.x < (unsigned)ntiles;
-    int tz0 = 0, tr0 = 0;
-    if (tile_mode) {
-        const int t = blockIdx.x;
-        begin = offsets[(size_t)t * (TZ * TR)];
-        end = offsets[(size_t)(t + 1) * (TZ * TR)];
-        if (begin == end) return;
-        tz0 = (t / a.ntr) * TZ;
-        tr0 = (t % a.ntr) * TR;
-    } else {
-        const long long nsorted = dcount[1], np = dcount[0];
-        begin = nsorted + (long long)(blockIdx.x - ntiles) * tail_chunk;
-        end = min(begin + tail_chunk, np);
-        if (begin >= end) return;
-    }
-    GlobAcc<NP> gacc{E, Bb, J, jdirty, a};
-    const int zoff = (int)a.zoff;
-    if (!tile_mode || a.nzp < 2 * G::JW) {
-        // particles appended since the last sort, or a box too short for the
-        // staged tile: every access goes to global memory
-        for (long long idx = begin + threadIdx.x; idx < end; idx += blockDim.x) {
-            const int cell = P.cell[idx];
-            if (cell < 0) continue;
-            const int iz = cell_iz(cell), jr = cell_jr(cell);
-            if (!a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) { P.cell[idx] = -1; continue; }
-            PState s;
-            DepIn<NM> d;
-            float4 ra, rb;
-            ld_rec(P.rec + 2 * idx, ra, rb);
-            s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
-            s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
-            s.W0 = a.track_work ? P.W0[idx] : 0.f;
-            s.W1 = a.track_work ? P.W1[idx] : 0.f;
-            s.jr = jr;
-            push_move<NP>(gacc, a, iz, jr, s, d);
-            deposit_general<NP>(gacc, a, iz, jr, d);
-            const int niz = wrapn(iz + s.diz, a.nzp);
-            const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
-            P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
-            st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph), make_float4(s.ux, s.uy, s.uz, s.w));
-            if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
-        }
-        return;
-    }
-    // ---- shared memory: accumulators, staged fields, crossing queue, particle buffers
-    unsigned long long *sJ = sraw;
-    float4 *sf = reinterpret_cast<float4 *>(sraw + G::JPAD);
-    float *queue = reinterpret_cast<float *>(sf + G::FVEC);
-    int *qcount = reinterpret_cast<int *>(queue + G::QCAP * G::QW);
-    // ---- each thread pushes kc consecutive particles of the tile; the next
-    // particle's words are copied to shared memory while one is pushed (the
-    // first copy overlaps the staging of the fields)
-    float *pbuf = reinterpret_cast<float *>(qcount + 4);
-    const int n = (int)(end - begin);
-    const int nch = tile_nchunks(n);
-    const int tid = threadIdx.x;
-    auto slot_of = [&](int ch, int k) -> long long {
-        const Chunk C = tile_chunk(n, ch);
-        const int cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
-        return k < cnt ? begin + C.q0 + tid * C.kc + k : -1;
-    };
-    auto prefetch = [&](int b, long long idx) {
-        if (idx >= 0) {
-            float *pb = pbuf + b * G::PB;
-            float4 *pr = reinterpret_cast<float4 *>(pb + GPD_T);
-            cp_async4(pb + tid, P.cell + idx);
-            cp_async16(pr + tid, P.rec + 2 * idx);
-            cp_async16(pr + GPD_T + tid, P.rec + 2 * idx + 1);
-        }
-        cp_async_commit();
-    };
-    long long idx = slot_of(0, 0);
-    prefetch(0, idx);
-    // ---- stage E and Bbar of the tile and its halo; clear the accumulators
-    const int col0 = tz0 - G::H - 1;
-    const int row0 = tr0 - G::H - 1;
-    const SmemAcc<NP, TZ, TR> sacc{sf, sJ};
-    for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) sJ[k] = 0ull;
-    if (threadIdx.x == 0) *qcount = 0;
-    // one float4 word (up to 4 mode parts of one node) per thread and pass
-    for (int k = threadIdx.x; k < G::FVEC; k += blockDim.x) {
-        const int v = k % G::V, t1 = k / G::V;
-        const int li = t1 % G::FW, t2 = t1 / G::FW, lj = t2 % G::FR, fc = t2 / G::FR;
-        const int c = fc % 3, fb = fc / 3;
-        int col = col0 + li;
-        col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
-        float w4[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int p = 4 * v + e;
-            w4[e] = p < NP ? gsample_at(E, Bb, a, fb, c, p, row0 + lj, col) : 0.f;
-        }
-        sf[k] = make_float4(w4[0], w4[1], w4[2], w4[3]);
-    }
-    __syncthreads();
-    const float q20 = a.qscale * 9.5367431640625e-07f;            // qscale * 2^-20
-    FastSum<NP, TZ, TR> fs;
-    fs.clear();
-    int buf = 0;
-    for (int ch = 0; ch < nch; ch++) {
-        const int kc = tile_chunk(n, ch).kc;
-        for (int k = 0; k < kc; k++) {                             // block-uniform trip count
-            const long long nidx = k + 1 < kc ? slot_of(ch, k + 1) : (ch + 1 < nch ? slot_of(ch + 1, 0) : -1);
-            prefetch(buf ^ 1, nidx);
-            cp_async_wait_prev();                                  // this particle's words have landed
-            if (idx >= 0) {
-                const float *pb = pbuf + buf * G::PB;
-                const float4 *pr = reinterpret_cast<const float4 *>(pb + GPD_T);
-                const int cell = __float_as_int(pb[tid]);
-                const int iz = cell_iz(cell), jr = cell_jr(cell);
-                bool act = cell >= 0;
-                if (act && !a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
-                    P.cell[idx] = -1;                  // behind the moving window
-                    act = false;
-                }
-                if (act) {
-                    PState s;
-                    DepIn<NM> d;
-                    const float4 ra = pr[tid], rb = pr[GPD_T + tid];
-                    s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
-                    s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
-                    s.W0 = a.track_work ? P.W0[idx] : 0.f;
-                    s.W1 = a.track_work ? P.W1[idx] : 0.f;
-                    s.jr = jr;
-                    const int li = wrapn(iz - col0, a.nzp), lj = jr - row0;
-                    if (li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2) {
-                        push_move<NP>(sacc, a, li, lj, s, d);
-                        if (same_cell(d)) {
-                            const int key = (lj << 12) | li;
-                            if (key != fs.key) { fs.flush(sJ); fs.key = key; }
-                            fs.add(d, d.Q * q20);
-                        } else {
-                            // a move across a cell boundary waits in the queue (deposited
-                            // directly when the queue is full)
-                            const int slot = atomicAdd(qcount, 1);
-                            if (slot < G::QCAP) queue_put<NM>(queue + G::QW * slot, li, lj, d);
-                            else deposit_general<NP>(sacc, a, li, lj, d);
-                        }
-                    } else {                           // drifted beyond the staged halo
-                        push_move<NP>(gacc, a, iz, jr, s, d);
-                        deposit_general<NP>(gacc, a, iz, jr, d);
-                    }
-                    const int niz = wrapn(iz + s.diz, a.nzp);
-                    const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
-                    P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
-                    st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph),
-                           make_float4(s.ux, s.uy, s.uz, s.w));
-                    if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
-                }
-            }
-            idx = nidx;
-            buf ^= 1;
-        }
-        fs.flush(sJ);
-        fs.key = -1;
-    }
-    // the queued cell-crossing moves, spread over all threads
-    __syncthreads();
-    const int nq = imin(*qcount, G::QCAP);
-    for (int q = tid; q < nq; q += blockDim.x) {
-        int qi, qj;
-        DepIn<NM> dq;
-        queue_get<NM>(queue + G::QW * q, qi, qj, dq);
-        deposit_general<NP>(sacc, a, qi, qj, dq);
-    }
-    __syncthreads();
-    // the tile's accumulators go to its own scratch block with plain stores;
-    // the reduction kernel sums the tiles that cover each node
-    unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
-    for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) dst[k] = sJ[k];
-    if (threadIdx.x == 0) tstamp[blockIdx.x] = *d_epoch;
-}
-
-template <int NP, int TZ, int TR>
-static void gpd_launch(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk)
-{
-    const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
-    cudaFuncSetAttribute(k_gpd<NP, TZ, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gpd<NP, TZ, TR><<<grid, GPD_T, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jtile,
-                                                    c->tstamp, c->jdirty, c->d_epoch, c->offsets, c->d_count, a,
-                                                    ntiles, chunk);
-}
-
-template <int NP>
-static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk)
-{
-    if (c->TZ == 16 && c->TR == 8) gpd_launch<NP, 16, 8>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 32 && c->TR == 8) gpd_launch<NP, 32, 8>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 8 && c->TR == 8) gpd_launch<NP, 8, 8>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 16 && c->TR == 16) gpd_launch<NP, 16, 16>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 32 && c->TR == 4) gpd_launch<NP, 32, 4>(c, a, grid, ntiles, chunk);
-    else return false;
-    return true;
-}
 
 bool gpd_tile_supported(int tz, int tr)
 {
@@ -896,138 +35,61 @@ void launch_gpd(qpic_ctx *c)
     int ntail = (int)((tail + TAIL_CHUNK - 1) / TAIL_CHUNK);
     int grid = ntiles + ntail;
     prof_begin(c);
+    const bool fa = c->fatomic;
     switch (c->g.nparts) {
-    case 1: gpd_dispatch_tile<1>(c, a, grid, ntiles, TAIL_CHUNK); break;
-    case 3: gpd_dispatch_tile<3>(c, a, grid, ntiles, TAIL_CHUNK); break;
-    case 5: gpd_dispatch_tile<5>(c, a, grid, ntiles, TAIL_CHUNK); break;
-    default: gpd_dispatch_tile<7>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    case 1: fa ? gpd_run<1, true>(c, a, grid, ntiles, TAIL_CHUNK) : gpd_run<1, false>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    case 3: fa ? gpd_run<3, true>(c, a, grid, ntiles, TAIL_CHUNK) : gpd_run<3, false>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    case 5: fa ? gpd_run<5, true>(c, a, grid, ntiles, TAIL_CHUNK) : gpd_run<5, false>(c, a, grid, ntiles, TAIL_CHUNK); break;
+    default: fa ? gpd_run<7, true>(c, a, grid, ntiles, TAIL_CHUNK) : gpd_run<7, false>(c, a, grid, ntiles, TAIL_CHUNK); break;
     }
     prof_end(c, KC_GPD);
 }
 
 // ------------------------------------------------------------ current reduction + decode
-// One thread per node of a tile's core (its TZ x TR cells; the last tile row
-// also owns the wall row j = nr).  A node's current is the word of every
-// neighbouring tile block (3 x 3 candidates, written this step, whose staged
-// region covers the node) plus, in tiles that received global-path deposits,
-// the global accumulator (then cleared), summed in a fixed order in int64 and
-// turned into FP32 current with the per-row finite-volume factor.  All NP
-// parts of the three components are loaded together (unrolled).
-template <int NP, int TZ, int TR>
-__global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
-                                                     const int *__restrict__ tstamp,
-                                                     const int *__restrict__ d_epoch,
-                                                     unsigned long long *__restrict__ Jacc,
-                                                     int *__restrict__ jdirty,
-                                                     float *__restrict__ Jf,
-                                                     const float *__restrict__ rowf, PArgs a,
-                                                     long long tile_words, float inv_qscale,
-                                                     int tiles_ok, int *err)
+// FP32 float-atomic variant: the current was summed in FP32 in Jfa; apply the
+// per-row finite-volume factor, zero the gap of an open box, clear Jfa.
+__global__ void k_jdecode_float(float *__restrict__ Jfa, float *__restrict__ Jf,
+                                const float *__restrict__ rowf, PArgs a)
 {
-    constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3, NPL = 3 * NP;
-    const int c = threadIdx.x % TZ, r0 = threadIdx.x / TZ;
-    const int t = blockIdx.x;
-    const int tzi = t / a.ntr, tri = t - tzi * a.ntr;
-    const int tz0 = tzi * TZ, tr0 = tri * TR;
-    const bool dirty = jdirty[t] != 0;
-    __syncthreads();
-    if (threadIdx.x == 0 && dirty) jdirty[t] = 0;
-    if (c >= a.nzp - tz0) return;                          // past the last (partial) column
-    const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
-    const int i = tz0 + c;
-    const int epoch = *d_epoch;
-    long long kbase[9];
-    int ljb[9];
-    bool ok[9];
-#pragma unroll
-    for (int d = 0; d < 9; d++) {
-        const int dz = d / 3 - 1, dr = d % 3 - 1;
-        int kz = tzi + dz;
-        kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
-        const int kr = tri + dr;
-        ok[d] = false;
-        ljb[d] = 0; kbase[d] = 0;
-        if (tiles_ok && kr >= 0 && kr < a.ntr) {
-            const int kt = kz * a.ntr + kr;
-            const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
-            ljb[d] = tr0 - (kr * TR - H - 1);
-            kbase[d] = (long long)kt * tile_words + li;
-            ok[d] = li < JW && tstamp[kt] == epoch;
+    const long long nnode = (long long)(a.nr + 1) * a.nzp;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnode;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / a.nzp), i = (int)(q - (long long)j * a.nzp);
+        int l = i - (int)a.zoff;
+        l = l < 0 ? l + a.nzp : l;
+        const bool gap = l >= a.nz;
+        for (int pl = 0; pl < 3 * a.nparts; pl++) {
+            const int comp = pl / a.nparts, part = pl - comp * a.nparts;
+            const float f = comp == 2 ? rowf[j]
+                          : comp == 0 ? rowf[(a.nr + 1) + j]
+                                      : (part == 0 ? rowf[3 * (a.nr + 1) + j] : rowf[2 * (a.nr + 1) + j]);
+            const size_t k = (size_t)pl * a.plane + q;
+            Jf[k] = gap ? 0.f : Jfa[k] * f;
+            Jfa[k] = 0.f;
         }
     }
-    int l = i - (int)a.zoff;
-    l = l < 0 ? l + a.nzp : l;
-    const bool gap = l >= a.nz;
-    for (int r = r0; r < CR; r += TR) {
-        const int j = tr0 + r;
-        const size_t q0 = (size_t)j * a.nzp + i;
-        long long v[NPL];
-#pragma unroll
-        for (int pl = 0; pl < NPL; pl++) v[pl] = 0;
-        if (dirty) {
-#pragma unroll
-            for (int pl = 0; pl < NPL; pl++) {
-                v[pl] = (long long)Jacc[(size_t)pl * a.plane + q0];
-                Jacc[(size_t)pl * a.plane + q0] = 0ull;
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < 9; d++) {
-            const int lj = ljb[d] + r;
-            if (ok[d] && lj >= 0 && lj < JR) {
-                const unsigned long long *src = Jtile + kbase[d] + lj * JW;
-#pragma unroll
-                for (int pl = 0; pl < NPL; pl++) v[pl] += (long long)src[pl * (JR * JW)];
-            }
-        }
-        const float fz = rowf[j], fr = rowf[(a.nr + 1) + j];
-        const float fp = rowf[2 * (a.nr + 1) + j], fp0 = rowf[3 * (a.nr + 1) + j];
-#pragma unroll
-        for (int pl = 0; pl < NPL; pl++) {
-            if (v[pl] > (1ll << 62) || v[pl] < -(1ll << 62)) atomicOr(err, 1);   // fixed-point headroom gone
-            const int comp = pl / NP, part = pl - comp * NP;
-            const float f = comp == 2 ? fz : (comp == 0 ? fr : (part == 0 ? fp0 : fp));
-            // int64 -> float from two 32-bit halves (integer conversions stay off the FP64 pipe)
-            const float fv = __int2float_rn((int)(v[pl] >> 32)) * 4294967296.f +
-                             __uint2float_rn((unsigned)v[pl]);
-            Jf[(size_t)pl * a.plane + q0] = gap ? 0.f : fv * inv_qscale * f;
-        }
-    }
-}
-
-template <int NP, int TZ, int TR>
-static void jreduce_launch(qpic_ctx *c, const PArgs &a, int tiles_ok)
-{
-    k_jreduce<NP, TZ, TR><<<c->ntz * c->ntr, TZ * TR, 0, c->stream>>>(
-        c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
-        (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err);
-}
-
-template <int NP>
-static void jreduce_dispatch(qpic_ctx *c, const PArgs &a, int tiles_ok)
-{
-    if (c->TZ == 16 && c->TR == 8) jreduce_launch<NP, 16, 8>(c, a, tiles_ok);
-    else if (c->TZ == 32 && c->TR == 8) jreduce_launch<NP, 32, 8>(c, a, tiles_ok);
-    else if (c->TZ == 8 && c->TR == 8) jreduce_launch<NP, 8, 8>(c, a, tiles_ok);
-    else if (c->TZ == 16 && c->TR == 16) jreduce_launch<NP, 16, 16>(c, a, tiles_ok);
-    else jreduce_launch<NP, 32, 4>(c, a, tiles_ok);
 }
 
 void launch_jdecode(qpic_ctx *c)
 {
     PArgs a = pargs(c);
+    if (c->fatomic) {
+        prof_begin(c);
+        k_jdecode_float<<<152 * 8, 256, 0, c->stream>>>(c->Jfa, c->Jf, c->rowf, a);
+        prof_end(c, KC_JDECODE);
+        return;
+    }
     const int JW = c->TZ + 2 * c->halo + 3;
     const int tiles_ok = c->g.nzp >= 2 * JW ? 1 : 0;
     prof_begin(c);
     switch (c->g.nparts) {
-    case 1: jreduce_dispatch<1>(c, a, tiles_ok); break;
-    case 3: jreduce_dispatch<3>(c, a, tiles_ok); break;
-    case 5: jreduce_dispatch<5>(c, a, tiles_ok); break;
-    default: jreduce_dispatch<7>(c, a, tiles_ok); break;
+    case 1: jreduce_run<1>(c, a, tiles_ok); break;
+    case 3: jreduce_run<3>(c, a, tiles_ok); break;
+    case 5: jreduce_run<5>(c, a, tiles_ok); break;
+    default: jreduce_run<7>(c, a, tiles_ok); break;
     }
     prof_end(c, KC_JDECODE);
 }
-
 // ------------------------------------------------------------ sort
 // tile-major key: tile (tz, tr), then row and column inside the tile (TZ, TR powers of 2)
 __device__ __forceinline__ int sort_key(int cell, const PArgs &a)

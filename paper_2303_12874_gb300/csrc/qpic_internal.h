@@ -64,6 +64,7 @@ struct qpic_ctx {
     std::string err;
     cudaStream_t stream = nullptr;
     bool fp64 = false;
+    bool fatomic = false;                 // FP32 path with float-atomic deposit (precision variant)
 
     // grid and solver
     qpic::FieldGeom g;
@@ -79,6 +80,7 @@ struct qpic_ctx {
     // FP32 fields
     float *E = nullptr, *B = nullptr, *Bb = nullptr, *Jf = nullptr, *Jzf = nullptr;
     unsigned long long *Jacc = nullptr;   // global-path deposits (int64 atomics)
+    float *Jfa = nullptr;                 // float-atomic variant: FP32 current sums
     unsigned long long *Jtile = nullptr;  // per-tile accumulator blocks
     int *tstamp = nullptr;                // epoch at which each tile block was written
     int *jdirty = nullptr;                // per tile: Jacc holds global-path deposits in its core
