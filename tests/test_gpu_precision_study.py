@@ -1,0 +1,74 @@
+"""Precision study: the three GPU arithmetic variants against the FP64 oracle
+on one 100-step run of the 256 x 32 plasma and laser (65,536 particles).
+
+- (a) QPIC_FP64: plain FP64 GPU path;
+- (b) QPIC_FP32_FIXED: FP32 push and solve, int64 fixed-point current sums;
+- (c) QPIC_FP32_FATOMIC: FP32 with float-atomic current sums.
+
+All four start from the same state: the plasma of the oracle's generator
+(FP64) and the paper's laser (Eq. 18), each side adding the laser itself.
+Every 10 steps the relative L2 of E, B and J against the oracle is recorded,
+together with the field energy per mode.  The table is printed (run with -s
+to see it).  Checks:
+- after the first step the FP32 variants are within the per-step target
+  (1e-5) and FP64 within 1e-11;
+- after 100 steps all field energies per mode and the kinetic energy are
+  within 1% of the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_12874_gb300 as q
+import synth
+from oracle import coeffs as C
+from oracle import diag
+from oracle import setup
+from pairs import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = (("fp64", q.QPIC_FP64, 1e-11), ("fp32_fixed", q.QPIC_FP32_FIXED, 1e-5),
+            ("fp32_fatomic", q.QPIC_FP32_FATOMIC, 1e-5))
+
+
+def test_precision_study_config1():
+    w = synth.workload("cfg1_small")
+    nz, nr, dz, dr = w["nz"], w["nr"], w["dz"], w["dr"]
+    pl, la = w["plasma"], w["laser"]
+    dt = 0.9 * C.cfl_dt(dz, dr, nr, 2, "dual")
+    cE, cB = C.dual_coefficients(dt, dz)
+    parts = setup.plasma_cells(np.arange(nz), nr, dz, dr, pl["n0"], pl["z_start"],
+                               pl["ramp_len"], pl["ppc"], pl["seed"])
+    o = oracle.Oracle(nz, nr, 2, dz, dr, dt, cE, cB, C.filter_taps(cB), periodic=True)
+    o.load_particles(**parts)
+    setup.add_laser(o, cE, cB, la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
+    sims = {}
+    for name, prec, _ in VARIANTS:
+        s = q.Sim(nz, nr, dz, dr, dt=dt, precision=prec)
+        s.load_particles(**parts)
+        s.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
+        sims[name] = s
+    rows = []
+    done = 0
+    for target in (1, 10, 20, 40, 60, 80, 100):
+        o.step(target - done)
+        ref = {k: o.fields(k) for k in ("E", "B", "J")}
+        fe_o = diag.field_energy(o)
+        for name, _, _ in VARIANTS:
+            s = sims[name]
+            s.step(target - done)
+            err = {k: rel_l2(s.fields(k), ref[k]) for k in ("E", "B", "J")}
+            fe = s.diag()["field_energy"]
+            rows.append((name, target, err["E"], err["B"], err["J"],
+                         fe[0] / fe_o[0] - 1, fe[1] / fe_o[1] - 1))
+        done = target
+    print("\nvariant        step   relL2(E)  relL2(B)  relL2(J)  dFE0      dFE1")
+    for r in rows:
+        print("%-13s %5d  %.2e  %.2e  %.2e  %+.1e  %+.1e" % r)
+    for name, _, tol in VARIANTS:
+        first = [r for r in rows if r[0] == name and r[1] == 1][0]
+        assert max(first[2:5]) <= tol, (name, first)
+        last = [r for r in rows if r[0] == name and r[1] == 100][0]
+        assert abs(last[5]) < 0.01 and abs(last[6]) < 0.01, (name, last)
+        ke = diag.kinetic_energy(sims[name].particles())
+        assert abs(ke / diag.kinetic_energy(o.particles()) - 1) < 0.01, name
