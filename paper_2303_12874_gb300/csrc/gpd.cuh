@@ -789,7 +789,11 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
     for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) sJ[k] = 0ull;
     if (threadIdx.x == 0) *qcount = 0;
     // one float4 word (up to 4 mode parts of one node) per thread and pass
-    for (int k = threadIdx.x; k < G::FVEC; k += blockDim.x) {
+    // (compile-time trip count: the loop unrolls and its global loads overlap)
+#pragma unroll
+    for (int it = 0; it < (G::FVEC + GPD_T - 1) / GPD_T; it++) {
+        const int k = it * GPD_T + (int)threadIdx.x;
+        if (k >= G::FVEC) break;
         const int v = k % G::V, t1 = k / G::V;
         const int li = t1 % G::FW, t2 = t1 / G::FW, lj = t2 % G::FR, fc = t2 / G::FR;
         const int c = fc % 3, fb = fc / 3;
@@ -912,35 +916,51 @@ static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles,
 }
 // ------------------------------------------------------------ current reduction + decode
 // One thread per node of a tile's core (its TZ x TR cells; the last tile row
-// also owns the wall row j = nr).  A node's current is the word of every
-// neighbouring tile block (3 x 3 candidates, written this step, whose staged
-// region covers the node) plus, in tiles that received global-path deposits,
-// the global accumulator (then cleared), summed in a fixed order in int64 and
-// turned into FP32 current with the per-row finite-volume factor.  All NP
-// parts of the three components are loaded together (unrolled).
+// also owns the wall row j = nr) and current component, all NP parts of that
+// component unrolled.  A node's current is the word of every neighbouring
+// tile block (3 x 3 candidates, written this step, whose staged region covers
+// the node) plus, in tiles that received global-path deposits, the global
+// accumulator (then cleared), summed in a fixed order in int64 and turned into
+// FP32 current with the per-row finite-volume factor.
 template <int NP, int TZ, int TR>
-__global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
-                                                     const int *__restrict__ tstamp,
-                                                     const int *__restrict__ d_epoch,
-                                                     unsigned long long *__restrict__ Jacc,
-                                                     int *__restrict__ jdirty,
-                                                     float *__restrict__ Jf,
-                                                     const float *__restrict__ rowf, PArgs a,
-                                                     long long tile_words, float inv_qscale,
-                                                     int tiles_ok, int *err)
+__global__ void __launch_bounds__(3 * TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
+                                                         const int *__restrict__ tstamp,
+                                                         const int *__restrict__ d_epoch,
+                                                         unsigned long long *__restrict__ Jacc,
+                                                         int *__restrict__ jdirty,
+                                                         float *__restrict__ Jf,
+                                                         const float *__restrict__ rowf, PArgs a,
+                                                         long long tile_words, float inv_qscale,
+                                                         int tiles_ok, int *err)
 {
-    constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3, NPL = 3 * NP;
-    const int c = threadIdx.x % TZ, r0 = threadIdx.x / TZ;
+    constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3, NN = TZ * TR;
+    __shared__ int s_ok[9], s_kt[9], s_dirty;
     const int t = blockIdx.x;
     const int tzi = t / a.ntr, tri = t - tzi * a.ntr;
     const int tz0 = tzi * TZ, tr0 = tri * TR;
-    const bool dirty = jdirty[t] != 0;
+    if (threadIdx.x < 9) {                                  // the candidate tile blocks
+        const int d = threadIdx.x, dz = d / 3 - 1, dr = d % 3 - 1;
+        int kz = tzi + dz;
+        kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
+        const int kr = tri + dr;
+        int ok = 0, kt = 0;
+        if (tiles_ok && kr >= 0 && kr < a.ntr) {
+            kt = kz * a.ntr + kr;
+            ok = tstamp[kt] == *d_epoch;
+        }
+        s_ok[d] = ok;
+        s_kt[d] = kt;
+    } else if (threadIdx.x == 9) {
+        s_dirty = jdirty[t];
+    }
     __syncthreads();
+    const bool dirty = s_dirty != 0;
     if (threadIdx.x == 0 && dirty) jdirty[t] = 0;
+    const int comp = threadIdx.x / NN, node = threadIdx.x - comp * NN;
+    const int c = node % TZ, r0 = node / TZ;
     if (c >= a.nzp - tz0) return;                          // past the last (partial) column
     const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
     const int i = tz0 + c;
-    const int epoch = *d_epoch;
     long long kbase[9];
     int ljb[9];
     bool ok[9];
@@ -949,16 +969,10 @@ __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *_
         const int dz = d / 3 - 1, dr = d % 3 - 1;
         int kz = tzi + dz;
         kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
-        const int kr = tri + dr;
-        ok[d] = false;
-        ljb[d] = 0; kbase[d] = 0;
-        if (tiles_ok && kr >= 0 && kr < a.ntr) {
-            const int kt = kz * a.ntr + kr;
-            const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
-            ljb[d] = tr0 - (kr * TR - H - 1);
-            kbase[d] = (long long)kt * tile_words + li;
-            ok[d] = li < JW && tstamp[kt] == epoch;
-        }
+        const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
+        ljb[d] = tr0 - ((tri + dr) * TR - H - 1);
+        kbase[d] = (long long)s_kt[d] * tile_words + (long long)(comp * NP) * (JR * JW) + li;
+        ok[d] = s_ok[d] && li < JW;
     }
     int l = i - (int)a.zoff;
     l = l < 0 ? l + a.nzp : l;
@@ -966,14 +980,15 @@ __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *_
     for (int r = r0; r < CR; r += TR) {
         const int j = tr0 + r;
         const size_t q0 = (size_t)j * a.nzp + i;
-        long long v[NPL];
+        long long v[NP];
 #pragma unroll
-        for (int pl = 0; pl < NPL; pl++) v[pl] = 0;
+        for (int p = 0; p < NP; p++) v[p] = 0;
         if (dirty) {
 #pragma unroll
-            for (int pl = 0; pl < NPL; pl++) {
-                v[pl] = (long long)Jacc[(size_t)pl * a.plane + q0];
-                Jacc[(size_t)pl * a.plane + q0] = 0ull;
+            for (int p = 0; p < NP; p++) {
+                const size_t q = (size_t)(comp * NP + p) * a.plane + q0;
+                v[p] = (long long)Jacc[q];
+                Jacc[q] = 0ull;
             }
         }
 #pragma unroll
@@ -982,20 +997,18 @@ __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *_
             if (ok[d] && lj >= 0 && lj < JR) {
                 const unsigned long long *src = Jtile + kbase[d] + lj * JW;
 #pragma unroll
-                for (int pl = 0; pl < NPL; pl++) v[pl] += (long long)src[pl * (JR * JW)];
+                for (int p = 0; p < NP; p++) v[p] += (long long)src[p * (JR * JW)];
             }
         }
-        const float fz = rowf[j], fr = rowf[(a.nr + 1) + j];
-        const float fp = rowf[2 * (a.nr + 1) + j], fp0 = rowf[3 * (a.nr + 1) + j];
+        const float f0 = comp == 2 ? rowf[j] : (comp == 0 ? rowf[(a.nr + 1) + j] : rowf[3 * (a.nr + 1) + j]);
+        const float f1 = comp == 1 ? rowf[2 * (a.nr + 1) + j] : f0;   // J_phi, modes m >= 1
 #pragma unroll
-        for (int pl = 0; pl < NPL; pl++) {
-            if (v[pl] > (1ll << 62) || v[pl] < -(1ll << 62)) atomicOr(err, 1);   // fixed-point headroom gone
-            const int comp = pl / NP, part = pl - comp * NP;
-            const float f = comp == 2 ? fz : (comp == 0 ? fr : (part == 0 ? fp0 : fp));
+        for (int p = 0; p < NP; p++) {
+            if (v[p] > (1ll << 62) || v[p] < -(1ll << 62)) atomicOr(err, 1);   // fixed-point headroom gone
             // int64 -> float from two 32-bit halves (integer conversions stay off the FP64 pipe)
-            const float fv = __int2float_rn((int)(v[pl] >> 32)) * 4294967296.f +
-                             __uint2float_rn((unsigned)v[pl]);
-            Jf[(size_t)pl * a.plane + q0] = gap ? 0.f : fv * inv_qscale * f;
+            const float fv = __int2float_rn((int)(v[p] >> 32)) * 4294967296.f +
+                             __uint2float_rn((unsigned)v[p]);
+            Jf[(size_t)(comp * NP + p) * a.plane + q0] = gap ? 0.f : fv * inv_qscale * (p == 0 ? f0 : f1);
         }
     }
 }
@@ -1003,7 +1016,7 @@ __global__ void __launch_bounds__(TZ * TR) k_jreduce(const unsigned long long *_
 template <int NP, int TZ, int TR>
 static void jreduce_launch(qpic_ctx *c, const PArgs &a, int tiles_ok)
 {
-    k_jreduce<NP, TZ, TR><<<c->ntz * c->ntr, TZ * TR, 0, c->stream>>>(
+    k_jreduce<NP, TZ, TR><<<c->ntz * c->ntr, 3 * TZ * TR, 0, c->stream>>>(
         c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
         (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err);
 }

@@ -487,7 +487,7 @@ __global__ void k_energy_partial(const T *E, const T *B, GridArgs a, double *par
     __shared__ double red[256];
     const int j = blockIdx.y, m = blockIdx.z;
     const double PI = 3.14159265358979323846;
-    const double dr = a.dr, dz = a.dz, R = a.nr * dr;
+    const double dr = a.dr64, dz = a.dz64, R = a.nr * dr;
     double Vi, Vh;
     if (j == 0) Vi = PI * 0.25 * dr * dr * dz;
     else if (j == a.nr) Vi = PI * (R * R - (R - 0.5 * dr) * (R - 0.5 * dr)) * dz;

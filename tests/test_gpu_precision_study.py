@@ -13,7 +13,7 @@ to see it).  Checks:
 - after the first step the FP32 variants are within the per-step target
   (1e-5) and FP64 within 1e-11;
 - after 100 steps all field energies per mode and the kinetic energy are
-  within 1% of the oracle."""
+  within 1% of the oracle (the FP64 path's field energies to 1e-10)."""
 import numpy as np
 import pytest
 
@@ -70,5 +70,7 @@ def test_precision_study_config1():
         assert max(first[2:5]) <= tol, (name, first)
         last = [r for r in rows if r[0] == name and r[1] == 100][0]
         assert abs(last[5]) < 0.01 and abs(last[6]) < 0.01, (name, last)
+        if name == "fp64":                  # same fields to 1e-13: same energies to round-off
+            assert abs(last[5]) < 1e-10 and abs(last[6]) < 1e-10, last
         ke = diag.kinetic_energy(sims[name].particles())
         assert abs(ke / diag.kinetic_energy(o.particles()) - 1) < 0.01, name
