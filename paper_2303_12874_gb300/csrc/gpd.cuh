@@ -311,8 +311,17 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
             acc.node(fb, c, j0 + 1, i0, v10);
             acc.node(fb, c, j0 + 1, i0 + 1, v11);
 #pragma unroll
-            for (int p = 0; p < NP; p++)
-                F[fb][c][p] = w[0] * v00[p] + w[1] * v01[p] + w[2] * v10[p] + w[3] * v11[p];
+            for (int p = 0; p + 1 < NP; p += 2) {          // two mode parts per paired FP32 op
+                float2 f = __fmul2_rn(make_float2(w[0], w[0]), make_float2(v00[p], v00[p + 1]));
+                f = __ffma2_rn(make_float2(w[1], w[1]), make_float2(v01[p], v01[p + 1]), f);
+                f = __ffma2_rn(make_float2(w[2], w[2]), make_float2(v10[p], v10[p + 1]), f);
+                f = __ffma2_rn(make_float2(w[3], w[3]), make_float2(v11[p], v11[p + 1]), f);
+                F[fb][c][p] = f.x;
+                F[fb][c][p + 1] = f.y;
+            }
+            if (NP & 1)
+                F[fb][c][NP - 1] = w[0] * v00[NP - 1] + w[1] * v01[NP - 1] + w[2] * v10[NP - 1] +
+                                   w[3] * v11[NP - 1];
         }
     // ---- modal sum, rotation to Cartesian
     float cm[NM], sm[NM];
@@ -545,15 +554,22 @@ struct FastSum {
              : e == 3 ? p * PL + 1
                       : (NP + p) * PL + ((e - 4) & 1) + ((e - 4) >> 1) * G::JW;
     }
-    // t = contribution * qscale * 2^-20, |t| < 2^22
-    __device__ __forceinline__ void put(int i, float t)
+    // two contributions t = value * qscale * 2^-20 (|t| < 2^22) at once, on the
+    // paired FP32 units: the same roundings as fx() for each lane
+    __device__ __forceinline__ void put2(int i, float2 t)
     {
-        const float M = 12582912.0f;                    // 1.5 * 2^23
-        const float tm = __fadd_rn(t, M);               // bits: 0x4B400000 + round(t)
-        hs[i] += __float_as_uint(tm);
-        const float r = __fsub_rn(t, __fsub_rn(tm, M)); // t - round(t), exact
-        ls[i] += __float_as_uint(__fmaf_rn(r, 1048576.0f, M));
+        const float2 M2 = make_float2(12582912.0f, 12582912.0f);     // 1.5 * 2^23
+        const float2 nM2 = make_float2(-12582912.0f, -12582912.0f);
+        const float2 tm = __fadd2_rn(t, M2);                          // bits: 0x4B400000 + round(t)
+        hs[i] += __float_as_uint(tm.x);
+        hs[i + 1] += __float_as_uint(tm.y);
+        const float2 hf = __fadd2_rn(tm, nM2);                        // round(t), exact
+        const float2 r = __ffma2_rn(hf, make_float2(-1.f, -1.f), t);  // t - round(t), exact
+        const float2 lm = __ffma2_rn(r, make_float2(1048576.0f, 1048576.0f), M2);
+        ls[i] += __float_as_uint(lm.x);
+        ls[i + 1] += __float_as_uint(lm.y);
     }
+    static __device__ __forceinline__ float2 mul2(float2 a, float b) { return __fmul2_rn(a, make_float2(b, b)); }
     __device__ __forceinline__ void add(const DepIn<(NP + 1) / 2> &d, float q20)
     {
         constexpr int NM = (NP + 1) / 2;
@@ -561,27 +577,23 @@ struct FastSum {
         const float Sz0 = (1.f - d.oz0) - 0.5f * dz_, Sz1 = d.oz0 + 0.5f * dz_;
         const float Sr0 = (1.f - d.or0) - 0.5f * dr_, Sr1 = d.or0 + 0.5f * dr_;
         const float c4 = 0.25f * dz_ * dr_;
-        const float qz = q20 * dz_, qr = q20 * dr_;
-        const float Xz0 = qz * Sr0, Xz1 = qz * Sr1;    // J_z at (i0+1/2, j0+b)
-        const float Xr0 = qr * Sz0, Xr1 = qr * Sz1;    // J_r at (i0+a, j0+1/2)
+        const float2 Xz = mul2(make_float2(Sr0, Sr1), q20 * dz_);   // J_z at (i0+1/2, j0+b)
+        const float2 Xr = mul2(make_float2(Sz0, Sz1), q20 * dr_);   // J_r at (i0+a, j0+1/2)
         // J_phi at (i0+a, j0+b): Sbar_ab = Sz_a Sr_b + (dSz_a dSr_b)/4
-        const float QS[4] = {q20 * (Sz0 * Sr0 + c4), q20 * (Sz1 * Sr0 - c4),
-                             q20 * (Sz0 * Sr1 - c4), q20 * (Sz1 * Sr1 + c4)};
-        put(0, Xz0); put(1, Xz1); put(2, Xr0); put(3, Xr1);
-#pragma unroll
-        for (int k = 0; k < 4; k++) put(4 + k, QS[k] * d.aphi);      // m = 0: azimuthal displacement
+        const float2 Q01 = mul2(make_float2(Sz0 * Sr0 + c4, Sz1 * Sr0 - c4), q20);
+        const float2 Q23 = mul2(make_float2(Sz0 * Sr1 - c4, Sz1 * Sr1 + c4), q20);
+        put2(0, Xz); put2(2, Xr);
+        put2(4, mul2(Q01, d.aphi)); put2(6, mul2(Q23, d.aphi));   // m = 0: azimuthal displacement
 #pragma unroll
         for (int m = 1; m < NM; m++) {
             const float ebr = d.e0r[m] + 0.5f * d.der[m], ebi = d.e0i[m] + 0.5f * d.dei[m];
             const float im = 1.f / (float)m;
             const int pr = 8 * (2 * m - 1), pi = 8 * (2 * m);
-            put(pr + 0, Xz0 * ebr); put(pr + 1, Xz1 * ebr); put(pr + 2, Xr0 * ebr); put(pr + 3, Xr1 * ebr);
-            put(pi + 0, Xz0 * ebi); put(pi + 1, Xz1 * ebi); put(pi + 2, Xr0 * ebi); put(pi + 3, Xr1 * ebi);
-#pragma unroll
-            for (int k = 0; k < 4; k++) {                            // m >= 1: i Q Sbar (e1 - e0)/m
-                put(pr + 4 + k, -QS[k] * d.dei[m] * im);
-                put(pi + 4 + k, QS[k] * d.der[m] * im);
-            }
+            put2(pr + 0, mul2(Xz, ebr)); put2(pr + 2, mul2(Xr, ebr));
+            put2(pi + 0, mul2(Xz, ebi)); put2(pi + 2, mul2(Xr, ebi));
+            const float wr = -d.dei[m] * im, wi = d.der[m] * im;     // m >= 1: i Q Sbar (e1 - e0)/m
+            put2(pr + 4, mul2(Q01, wr)); put2(pr + 6, mul2(Q23, wr));
+            put2(pi + 4, mul2(Q01, wi)); put2(pi + 6, mul2(Q23, wi));
         }
         n += 1u;
     }
