@@ -346,17 +346,27 @@ class Sim:
         self._check(self.L.qpic_num_particles(self.h, ctypes.byref(n)), "num_particles")
         return n.value
 
-    def particles(self):
+    def particles(self, out=None):
+        """Live particles as FP64 arrays z, r, phi, ux, uy, uz, w, W0, W1.  out: an
+        optional caller-owned float64 buffer of at least 9 * num_particles()
+        (for example in pinned host memory); the arrays returned are then views
+        into it, valid until the buffer is reused."""
         n = self.num_particles()
         cap = max(n, 1)
-        out = np.zeros(9 * cap)
+        keys = ("z", "r", "phi", "ux", "uy", "uz", "w", "W0", "W1")
+        if out is not None:
+            out = np.ascontiguousarray(out, dtype=np.float64).reshape(-1)
+            if out.size < 9 * cap:
+                raise QpicError("particles: out holds %d doubles, need %d" % (out.size, 9 * cap))
+            cap = out.size // 9
+        else:
+            out = np.zeros(9 * cap)
         nout = ctypes.c_int64()
         self._check(self.L.qpic_get_particles(self.h, _dp(out), cap, ctypes.byref(nout)),
                     "get_particles")
         n = nout.value
-        out = out.reshape(9, cap)[:, :n]
-        keys = ("z", "r", "phi", "ux", "uy", "uz", "w", "W0", "W1")
-        return {k: out[i].copy() for i, k in enumerate(keys)}
+        v = out[:9 * cap].reshape(9, cap)[:, :n]
+        return {k: v[i] for i, k in enumerate(keys)}
 
     def particles_raw(self):
         """buffer-order export (no sort): same order across particle stages"""
