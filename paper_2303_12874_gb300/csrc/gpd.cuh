@@ -157,7 +157,8 @@ template <int NP>
 struct GlobAcc {
     const float *E, *Bb;
     unsigned long long *J;
-    int *dirty;                  // per tile: its core received a global-path deposit
+    int *dirty;                  // per tile: epoch of the last global-path deposit into its core
+    const int *epoch;            // this step's epoch (read on this rare path only)
     PArgs a;
     __device__ __forceinline__ void node(int fb, int c, int j, int i, float out[NP]) const
     {
@@ -171,7 +172,7 @@ struct GlobAcc {
         atomicAdd(&J[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic],
                   (unsigned long long)v);
         const int tr = imin(j >> a.lTR, a.ntr - 1);
-        dirty[(ic >> a.lTZ) * a.ntr + tr] = 1;
+        dirty[(ic >> a.lTZ) * a.ntr + tr] = *epoch;
     }
     __device__ __forceinline__ void put(int c, int p, int j, int i, float x) const;
 };
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
         end = min(begin + tail_chunk, np);
         if (begin >= end) return;
     }
-    GlobAcc<NP> gacc{E, Bb, J, jdirty, a};
+    GlobAcc<NP> gacc{E, Bb, J, jdirty, d_epoch, a};
     const FloatAcc facc{Jfa, a};
     const int zoff = (int)a.zoff;
     if (!tile_mode || a.nzp < 2 * G::JW) {
@@ -931,61 +932,52 @@ static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles,
 // also owns the wall row j = nr) and current component, all NP parts of that
 // component unrolled.  A node's current is the word of every neighbouring
 // tile block (3 x 3 candidates, written this step, whose staged region covers
-// the node) plus, in tiles that received global-path deposits, the global
-// accumulator (then cleared), summed in a fixed order in int64 and turned into
-// FP32 current with the per-row finite-volume factor.
+// the node) plus, in tiles that received global-path deposits this step (their
+// mark equals the step's epoch), the global accumulator (then cleared), summed
+// in a fixed order in int64 and turned into FP32 current with the per-row
+// finite-volume factor.
 template <int NP, int TZ, int TR>
 __global__ void __launch_bounds__(3 * TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
                                                          const int *__restrict__ tstamp,
                                                          const int *__restrict__ d_epoch,
                                                          unsigned long long *__restrict__ Jacc,
-                                                         int *__restrict__ jdirty,
+                                                         const int *__restrict__ jdirty,
                                                          float *__restrict__ Jf,
                                                          const float *__restrict__ rowf, PArgs a,
                                                          long long tile_words, float inv_qscale,
                                                          int tiles_ok, int *err)
 {
     constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3, NN = TZ * TR;
-    __shared__ int s_ok[9], s_kt[9], s_dirty;
     const int t = blockIdx.x;
     const int tzi = t / a.ntr, tri = t - tzi * a.ntr;
     const int tz0 = tzi * TZ, tr0 = tri * TR;
-    if (threadIdx.x < 9) {                                  // the candidate tile blocks
-        const int d = threadIdx.x, dz = d / 3 - 1, dr = d % 3 - 1;
-        int kz = tzi + dz;
-        kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
-        const int kr = tri + dr;
-        int ok = 0, kt = 0;
-        if (tiles_ok && kr >= 0 && kr < a.ntr) {
-            kt = kz * a.ntr + kr;
-            ok = tstamp[kt] == *d_epoch;
-        }
-        s_ok[d] = ok;
-        s_kt[d] = kt;
-    } else if (threadIdx.x == 9) {
-        s_dirty = jdirty[t];
-    }
-    __syncthreads();
-    const bool dirty = s_dirty != 0;
-    if (threadIdx.x == 0 && dirty) jdirty[t] = 0;
     const int comp = threadIdx.x / NN, node = threadIdx.x - comp * NN;
     const int c = node % TZ, r0 = node / TZ;
     if (c >= a.nzp - tz0) return;                          // past the last (partial) column
     const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
     const int i = tz0 + c;
+    const int epoch = *d_epoch;
+    const bool dirty = jdirty[t] == epoch;
+    // candidate blocks: geometry first; their words are loaded together with
+    // the stamps that say whether they were written this step (no wait between)
     long long kbase[9];
-    int ljb[9];
-    bool ok[9];
+    int ljb[9], kt[9];
+    bool geo[9];
 #pragma unroll
     for (int d = 0; d < 9; d++) {
         const int dz = d / 3 - 1, dr = d % 3 - 1;
         int kz = tzi + dz;
         kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
+        const int kr = tri + dr;
         const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
-        ljb[d] = tr0 - ((tri + dr) * TR - H - 1);
-        kbase[d] = (long long)s_kt[d] * tile_words + (long long)(comp * NP) * (JR * JW) + li;
-        ok[d] = s_ok[d] && li < JW;
+        kt[d] = kz * a.ntr + kr;
+        ljb[d] = tr0 - (kr * TR - H - 1);
+        kbase[d] = (long long)kt[d] * tile_words + (long long)(comp * NP) * (JR * JW) + li;
+        geo[d] = tiles_ok && kr >= 0 && kr < a.ntr && li < JW;
     }
+    bool ok[9];
+#pragma unroll
+    for (int d = 0; d < 9; d++) ok[d] = geo[d] && tstamp[kt[d]] == epoch;
     int l = i - (int)a.zoff;
     l = l < 0 ? l + a.nzp : l;
     const bool gap = l >= a.nz;
@@ -1006,10 +998,15 @@ __global__ void __launch_bounds__(3 * TZ * TR) k_jreduce(const unsigned long lon
 #pragma unroll
         for (int d = 0; d < 9; d++) {
             const int lj = ljb[d] + r;
-            if (ok[d] && lj >= 0 && lj < JR) {
+            if (geo[d] && lj >= 0 && lj < JR) {
                 const unsigned long long *src = Jtile + kbase[d] + lj * JW;
+                unsigned long long w[NP];
 #pragma unroll
-                for (int p = 0; p < NP; p++) v[p] += (long long)src[p * (JR * JW)];
+                for (int p = 0; p < NP; p++) w[p] = src[p * (JR * JW)];
+                if (ok[d]) {
+#pragma unroll
+                    for (int p = 0; p < NP; p++) v[p] += (long long)w[p];
+                }
             }
         }
         const float f0 = comp == 2 ? rowf[j] : (comp == 0 ? rowf[(a.nr + 1) + j] : rowf[3 * (a.nr + 1) + j]);
