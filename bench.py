@@ -450,7 +450,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
-    ap.add_argument("--batch-runs", type=int, default=0)
+    ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
