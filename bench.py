@@ -233,6 +233,20 @@ def run_reference(args, w):
     return 0
 
 
+def aggregate_ranks(ms, particles, steps, ws, device):
+    """Whole-job throughput over ranks: the slowest rank's time (max) and all
+    ranks' particles (sum).  Returns (ms_max, particles_all, particle-steps/s)."""
+    import torch
+    ms_t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    tot_p = torch.tensor([float(particles)], device=device, dtype=torch.float64)
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tot_p)
+    ms_max = float(ms_t.item())
+    particles_all = float(tot_p.item())
+    return ms_max, particles_all, particles_all * steps / (ms_max / 1e3)
+
+
 def run_ours(args, w):
     import torch
     import paper_2303_12874_gb300 as q
@@ -273,14 +287,7 @@ def run_ours(args, w):
     launches = sim.launch_count() - launches0
     n1 = sim.diag()["particles"]
     n_avg = 0.5 * (n0 + n1)
-    ms_t = torch.tensor([ms], device="cuda")
-    tot_p = torch.tensor([n_avg], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tot_p)
-    ms_max = float(ms_t.item())
-    particles_all = float(tot_p.item())
-    value = particles_all * args.steps / (ms_max / 1e3)
+    ms_max, particles_all, value = aggregate_ranks(ms, n_avg, args.steps, ws, "cuda")
     cells = w["nz"] * w["nr"]
     cell_updates = ws * cells * args.steps / (ms_max / 1e3)
 
