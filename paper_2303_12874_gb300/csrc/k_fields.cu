@@ -63,6 +63,13 @@ __device__ __forceinline__ int wrapz(int i, int nzp)
     return r < 0 ? r + nzp : r;
 }
 
+// column index for i in [-nzp, 2 nzp): one wrap (staging uses it when the box
+// is at least a block plus both halos wide, else wrapz)
+__device__ __forceinline__ int wrap1(int i, int nzp)
+{
+    return i < 0 ? i + nzp : (i >= nzp ? i - nzp : i);
+}
+
 // true when the physical column lies in the gap of an open box
 __device__ __forceinline__ bool in_gap(int col, const GridArgs &a)
 {
@@ -73,12 +80,16 @@ __device__ __forceinline__ bool in_gap(int col, const GridArgs &a)
 
 // mode number of a part and the (i m / r) coupling: returns the value of part p
 // of (i m / r) F given both parts of F (re = F[pr], im = F[pi])
-__device__ __forceinline__ int part_mode(int p) { return (p + 1) >> 1; }
+__host__ __device__ __forceinline__ int part_mode(int p) { return (p + 1) >> 1; }
+__host__ __device__ __forceinline__ constexpr int imin_f(int x, int y) { return x < y ? x : y; }
 
 // ---------------------------------------------------------------- Faraday
 // dB/dt = -curl E:  B_r: -(i m/r) E_z + D^E_z E_phi;  B_phi: -D^E_z E_r + d_r E_z;
-// B_z: -(1/r) d_r(r E_phi) + (i m/r) E_r.  Writes B^{n+1/2} and Bbar^n.
-template <typename T>
+// B_z: -(1/r) d_r(r E_phi) + (i m/r) E_r.  Writes B^{n+1/2} and Bbar^n.  One
+// block per row segment; E_phi and E_r of the row are staged with the stencil
+// halo.  Each thread loads its other operands (B, E_z, row j+1) before the
+// staging barrier, so both loads overlap.  P: parts (2M+1), compile time.
+template <typename T, int P>
 __global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *__restrict__ B,
                                                   T *__restrict__ Bb, GridArgs a)
 {
@@ -87,90 +98,101 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *_
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * FTILE;
     const int W = FTILE + 2 * a.L;
-    const int P = a.nparts;
     T *sC = sh;                      // [L] C^E
     T *sEphi = sh + MAX_L;           // [P][W]
     T *sEr = sEphi + P * W;          // [P][W]
+    const int i = i0 + threadIdx.x;
+    const bool live = i < a.nzp;
+    const bool up = j < a.nr;        // row j + 1 exists
+    const size_t base = (size_t)j * a.nzp + (live ? i : 0);
+    T br[P], bp[P], bz[P], ez[P], ez1[P], ep1[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        br[p] = B[(size_t)(0 * P + p) * a.plane + base];
+        bp[p] = B[(size_t)(1 * P + p) * a.plane + base];
+        bz[p] = B[(size_t)(2 * P + p) * a.plane + base];
+        ez[p] = E[(size_t)(2 * P + p) * a.plane + base];
+        ez1[p] = up ? E[(size_t)(2 * P + p) * a.plane + base + a.nzp] : (T)0;
+        ep1[p] = up ? E[(size_t)(1 * P + p) * a.plane + base + a.nzp] : (T)0;
+    }
     for (int k = threadIdx.x; k < a.L; k += FTILE)
         sC[k] = sizeof(T) == 8 ? (T)a.coef64[k] : (T)a.coef[k];
+    const bool wide = a.nzp >= W;
     for (int k = threadIdx.x; k < W; k += FTILE) {
-        int col = wrapz(i0 - a.L + k, a.nzp);
+        const int col = wide ? wrap1(i0 - a.L + k, a.nzp) : wrapz(i0 - a.L + k, a.nzp);
+#pragma unroll
         for (int p = 0; p < P; p++) {
             sEphi[p * W + k] = E[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
             sEr[p * W + k] = E[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
         }
     }
     __syncthreads();
-    const int i = i0 + threadIdx.x;
-    if (i >= a.nzp) return;
+    if (!live) return;
     const bool gap = in_gap(i, a);
     const T dr = (T)a.dr64, dz = (T)a.dz64, dt = (T)a.dt64;
     const T rj = j * dr, rh = (j + (T)0.5) * dr, rj1 = (j + 1) * dr;
     const int s = threadIdx.x + a.L;   // smem index of column i
+#pragma unroll
     for (int p = 0; p < P; p++) {
         const int m = part_mode(p);
         const bool isim = (p > 0) && !(p & 1);
-        const int pr = isim ? p - 1 : p, pim = isim ? p : p + 1;   // re / im partner
+        const int pr = isim ? p - 1 : p, pim = isim ? p : imin_f(p + 1, P - 1);   // re / im partner
         // D^E_z of E_phi and E_r at i + 1/2
         T dEphi = 0, dEr = 0;
         for (int l = 1; l <= a.L; l++) {
-            T cl = sC[l - 1];
+            const T cl = sC[l - 1];
             dEphi += cl * (sEphi[p * W + s + l] - sEphi[p * W + s + 1 - l]);
             dEr += cl * (sEr[p * W + s + l] - sEr[p * W + s + 1 - l]);
         }
         dEphi /= dz; dEr /= dz;
-        const size_t base = (size_t)j * a.nzp + i;
         // B_r at (i+1/2, j)
         T d;
         if (j == 0) {
-            if (m == 1) {
-                // -(i/r) E_z -> -i E_z^1(dr)/dr on the axis
-                const T *Ez = E + (size_t)(2 * P) * a.plane + (size_t)1 * a.nzp + i;
-                T ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
-                d = (isim ? -ezr : ezi) / dr + dEphi;
-            } else {
-                d = 0;
-            }
+            // m = 1: -(i/r) E_z -> -i E_z^1(dr)/dr on the axis; m != 1: 0
+            d = m == 1 ? (isim ? -ez1[pr] : ez1[pim]) / dr + dEphi : (T)0;
         } else {
-            T imr = 0;
-            if (m > 0) {
-                const T *Ez = E + (size_t)(2 * P) * a.plane + base;
-                T ezr = Ez[(size_t)pr * a.plane], ezi = Ez[(size_t)pim * a.plane];
-                imr = (isim ? ezr : -ezi) * (T)m / rj;      // part of (i m / r) E_z
-            }
+            const T imr = m > 0 ? (isim ? ez[pr] : -ez[pim]) * (T)m / rj : (T)0;   // (i m / r) E_z
             d = -imr + dEphi;
         }
         {
-            size_t q = (size_t)(0 * P + p) * a.plane + base;
-            T bo = B[q], bn = gap ? (T)0 : bo + dt * d;
-            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bo + bn);
+            const size_t q = (size_t)(0 * P + p) * a.plane + base;
+            const T bn = gap ? (T)0 : br[p] + dt * d;
+            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (br[p] + bn);
         }
-        if (j < a.nr) {
+        if (up) {
             // B_phi at (i+1/2, j+1/2)
-            const T *Ez = E + (size_t)(2 * P + p) * a.plane + base;
-            d = -dEr + (Ez[a.nzp] - Ez[0]) / dr;
+            d = -dEr + (ez1[p] - ez[p]) / dr;
             size_t q = (size_t)(1 * P + p) * a.plane + base;
-            T bo = B[q], bn = gap ? (T)0 : bo + dt * d;
-            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bo + bn);
-            // B_z at (i, j+1/2)
-            const T *Ep = E + (size_t)(1 * P + p) * a.plane + base;
-            T imr = 0;
-            if (m > 0) {
-                const T *Er = E + (size_t)(0 * P) * a.plane + base;
-                T err_ = Er[(size_t)pr * a.plane], eri = Er[(size_t)pim * a.plane];
-                imr = (isim ? err_ : -eri) * (T)m / rh;
-            }
-            d = -(rj1 * Ep[a.nzp] - rj * Ep[0]) / (rh * dr) + imr;
+            T bn = gap ? (T)0 : bp[p] + dt * d;
+            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bp[p] + bn);
+            // B_z at (i, j+1/2); E_phi(j) and E_r(j) from the staged row
+            const T imr = m > 0 ? (isim ? sEr[pr * W + s] : -sEr[pim * W + s]) * (T)m / rh : (T)0;
+            d = -(rj1 * ep1[p] - rj * sEphi[p * W + s]) / (rh * dr) + imr;
             q = (size_t)(2 * P + p) * a.plane + base;
-            bo = B[q]; bn = gap ? (T)0 : bo + dt * d;
-            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bo + bn);
+            bn = gap ? (T)0 : bz[p] + dt * d;
+            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bz[p] + bn);
         } else {
             // half-r row beyond the wall: not advanced; its average is the value itself
-            size_t q = (size_t)(1 * P + p) * a.plane + base;
-            Bb[q] = gap ? (T)0 : B[q];
-            q = (size_t)(2 * P + p) * a.plane + base;
-            Bb[q] = gap ? (T)0 : B[q];
+            Bb[(size_t)(1 * P + p) * a.plane + base] = gap ? (T)0 : bp[p];
+            Bb[(size_t)(2 * P + p) * a.plane + base] = gap ? (T)0 : bz[p];
         }
+    }
+}
+
+template <typename T, int P>
+static void faraday_launch(const GridArgs &a, dim3 grid, size_t sm, cudaStream_t st, const T *E, T *B, T *Bb)
+{
+    k_faraday<T, P><<<grid, FTILE, sm, st>>>(E, B, Bb, a);
+}
+
+template <typename T>
+static void faraday_dispatch(const GridArgs &a, dim3 grid, size_t sm, cudaStream_t st, const T *E, T *B, T *Bb)
+{
+    switch (a.nparts) {
+    case 1: faraday_launch<T, 1>(a, grid, sm, st, E, B, Bb); break;
+    case 3: faraday_launch<T, 3>(a, grid, sm, st, E, B, Bb); break;
+    case 5: faraday_launch<T, 5>(a, grid, sm, st, E, B, Bb); break;
+    default: faraday_launch<T, 7>(a, grid, sm, st, E, B, Bb); break;
     }
 }
 
@@ -181,10 +203,10 @@ void launch_faraday(qpic_ctx *c)
     prof_begin(c);
     if (c->fp64) {
         size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(double);
-        k_faraday<double><<<grid, FTILE, sm, c->stream>>>(c->E64, c->B64, c->Bb64, a);
+        faraday_dispatch<double>(a, grid, sm, c->stream, c->E64, c->B64, c->Bb64);
     } else {
         size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
-        k_faraday<float><<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Bb, a);
+        faraday_dispatch<float>(a, grid, sm, c->stream, c->E, c->B, c->Bb);
     }
     prof_end(c, KC_FARADAY);
 }
@@ -237,7 +259,9 @@ void launch_jfilter(qpic_ctx *c)
 // E_phi: D^B_z B_r - d_r B_z - J_phi;  E_z: (1/r) d_r(r B_phi) - (i m/r) B_r - J_z.
 // Axis: m = 0: E_phi = 0, E_z uses 4 B_phi(dr/2)/dr; m = 1: E_z = 0,
 // d_r B_z(0) = 2 B_z(dr/2)/dr; m >= 2: 0.  Wall: E_phi = E_z = 0.
-template <typename T>
+// B_phi and B_r of the row are staged with the stencil halo; each thread loads
+// its other operands (E, J, B_z, row j - 1) before the staging barrier.
+template <typename T, int P>
 __global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__restrict__ B,
                                                  const T *__restrict__ Jf,
                                                  const T *__restrict__ Jz, GridArgs a)
@@ -247,90 +271,103 @@ __global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * FTILE;
     const int W = FTILE + 2 * a.L;
-    const int P = a.nparts;
     T *sC = sh;                          // [L] C^B
     T *sBphi = sh + MAX_L, *sBr = sBphi + P * W;
+    const int i = i0 + threadIdx.x;
+    const bool live = i < a.nzp;
+    const bool down = j > 0;             // row j - 1 exists
+    const size_t base = (size_t)j * a.nzp + (live ? i : 0);
+    T er[P], ep[P], ez[P], jr[P], jp[P], jz[P], bz[P], bzm[P], bpm[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) {
+        er[p] = E[(size_t)(0 * P + p) * a.plane + base];
+        ep[p] = E[(size_t)(1 * P + p) * a.plane + base];
+        ez[p] = E[(size_t)(2 * P + p) * a.plane + base];
+        jr[p] = Jf[(size_t)(0 * P + p) * a.plane + base];
+        jp[p] = Jf[(size_t)(1 * P + p) * a.plane + base];
+        jz[p] = Jz[(size_t)p * a.plane + base];
+        bz[p] = B[(size_t)(2 * P + p) * a.plane + base];
+        bzm[p] = down ? B[(size_t)(2 * P + p) * a.plane + base - a.nzp] : (T)0;
+        bpm[p] = down ? B[(size_t)(1 * P + p) * a.plane + base - a.nzp] : (T)0;
+    }
     for (int k = threadIdx.x; k < a.L; k += FTILE)
         sC[k] = sizeof(T) == 8 ? (T)a.coef64[MAX_L + k] : (T)a.coef[MAX_L + k];
+    const bool wide = a.nzp >= W;
     for (int k = threadIdx.x; k < W; k += FTILE) {
-        int col = wrapz(i0 - a.L + k, a.nzp);
+        const int col = wide ? wrap1(i0 - a.L + k, a.nzp) : wrapz(i0 - a.L + k, a.nzp);
+#pragma unroll
         for (int p = 0; p < P; p++) {
             sBphi[p * W + k] = B[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
             sBr[p * W + k] = B[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
         }
     }
     __syncthreads();
-    const int i = i0 + threadIdx.x;
-    if (i >= a.nzp) return;
+    if (!live) return;
     const bool gap = in_gap(i, a);
     const T dr = (T)a.dr64, dz = (T)a.dz64, dt = (T)a.dt64;
     const T rj = j * dr, rh = (j + (T)0.5) * dr, rl = (j - (T)0.5) * dr;
     const int s = threadIdx.x + a.L;
-    const size_t base = (size_t)j * a.nzp + i;
+#pragma unroll
     for (int p = 0; p < P; p++) {
         const int m = part_mode(p);
         const bool isim = (p > 0) && !(p & 1);
-        const int pr = isim ? p - 1 : p, pim = isim ? p : p + 1;
+        const int pr = isim ? p - 1 : p, pim = isim ? p : imin_f(p + 1, P - 1);
         // D^B_z of B_phi and B_r at integer i: sum_l C_l (f_{i+l-1/2} - f_{i-l+1/2})
         T dBphi = 0, dBr = 0;
         for (int l = 1; l <= a.L; l++) {
-            T cl = sC[l - 1];
+            const T cl = sC[l - 1];
             dBphi += cl * (sBphi[p * W + s + l - 1] - sBphi[p * W + s - l]);
             dBr += cl * (sBr[p * W + s + l - 1] - sBr[p * W + s - l]);
         }
         dBphi /= dz; dBr /= dz;
         // E_r at (i, j+1/2)
         if (j < a.nr) {
-            T imr = 0;
-            if (m > 0) {
-                const T *Bz = B + (size_t)(2 * P) * a.plane + base;
-                T bzr = Bz[(size_t)pr * a.plane], bzi = Bz[(size_t)pim * a.plane];
-                imr = (isim ? bzr : -bzi) * (T)m / rh;
-            }
-            size_t q = (size_t)(0 * P + p) * a.plane + base;
-            T d = imr - dBphi - Jf[q];
-            E[q] = gap ? (T)0 : E[q] + dt * d;
+            const T imr = m > 0 ? (isim ? bz[pr] : -bz[pim]) * (T)m / rh : (T)0;
+            const T d = imr - dBphi - jr[p];
+            E[(size_t)(0 * P + p) * a.plane + base] = gap ? (T)0 : er[p] + dt * d;
         }
         // E_phi at (i, j)
         {
-            size_t q = (size_t)(1 * P + p) * a.plane + base;
             T v;
-            if (j == a.nr || (j == 0 && m != 1)) {
-                v = 0;
-            } else if (j == 0) {
-                const T *Bz = B + (size_t)(2 * P + p) * a.plane + base;
-                T d = dBr - (T)2 * Bz[0] / dr - Jf[q];
-                v = E[q] + dt * d;
-            } else {
-                const T *Bz = B + (size_t)(2 * P + p) * a.plane + base;
-                T d = dBr - (Bz[0] - Bz[-(long long)a.nzp]) / dr - Jf[q];
-                v = E[q] + dt * d;
-            }
-            E[q] = gap ? (T)0 : v;
+            if (j == a.nr || (j == 0 && m != 1)) v = 0;
+            else if (j == 0) v = ep[p] + dt * (dBr - (T)2 * bz[p] / dr - jp[p]);
+            else v = ep[p] + dt * (dBr - (bz[p] - bzm[p]) / dr - jp[p]);
+            E[(size_t)(1 * P + p) * a.plane + base] = gap ? (T)0 : v;
         }
-        // E_z at (i+1/2, j)
+        // E_z at (i+1/2, j); B_phi(j) and B_r(j) from the staged row
         {
-            size_t q = (size_t)(2 * P + p) * a.plane + base;
-            size_t qz = (size_t)p * a.plane + base;
+            const T bp0 = sBphi[p * W + s];
             T v;
             if (j == a.nr || (j == 0 && m != 0)) {
                 v = 0;
             } else if (j == 0) {
-                const T *Bp = B + (size_t)(1 * P + p) * a.plane + base;
-                v = E[q] + dt * ((T)4 * Bp[0] / dr - Jz[qz]);
+                v = ez[p] + dt * ((T)4 * bp0 / dr - jz[p]);
             } else {
-                const T *Bp = B + (size_t)(1 * P + p) * a.plane + base;
-                T imr = 0;
-                if (m > 0) {
-                    const T *Br = B + (size_t)(0 * P) * a.plane + base;
-                    T brr = Br[(size_t)pr * a.plane], bri = Br[(size_t)pim * a.plane];
-                    imr = (isim ? brr : -bri) * (T)m / rj;
-                }
-                T d = (rh * Bp[0] - rl * Bp[-(long long)a.nzp]) / (rj * dr) - imr - Jz[qz];
-                v = E[q] + dt * d;
+                const T imr = m > 0 ? (isim ? sBr[pr * W + s] : -sBr[pim * W + s]) * (T)m / rj : (T)0;
+                const T d = (rh * bp0 - rl * bpm[p]) / (rj * dr) - imr - jz[p];
+                v = ez[p] + dt * d;
             }
-            E[q] = gap ? (T)0 : v;
+            E[(size_t)(2 * P + p) * a.plane + base] = gap ? (T)0 : v;
         }
+    }
+}
+
+template <typename T, int P>
+static void ampere_launch(const GridArgs &a, dim3 grid, size_t sm, cudaStream_t st, T *E, const T *B,
+                          const T *J, const T *Jz)
+{
+    k_ampere<T, P><<<grid, FTILE, sm, st>>>(E, B, J, Jz, a);
+}
+
+template <typename T>
+static void ampere_dispatch(const GridArgs &a, dim3 grid, size_t sm, cudaStream_t st, T *E, const T *B,
+                            const T *J, const T *Jz)
+{
+    switch (a.nparts) {
+    case 1: ampere_launch<T, 1>(a, grid, sm, st, E, B, J, Jz); break;
+    case 3: ampere_launch<T, 3>(a, grid, sm, st, E, B, J, Jz); break;
+    case 5: ampere_launch<T, 5>(a, grid, sm, st, E, B, J, Jz); break;
+    default: ampere_launch<T, 7>(a, grid, sm, st, E, B, J, Jz); break;
     }
 }
 
@@ -342,11 +379,11 @@ void launch_ampere(qpic_ctx *c)
     if (c->fp64) {
         size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(double);
         const double *jz = c->taps.empty() ? c->J64 + (size_t)2 * a.nparts * a.plane : c->Jz64;
-        k_ampere<double><<<grid, FTILE, sm, c->stream>>>(c->E64, c->B64, c->J64, jz, a);
+        ampere_dispatch<double>(a, grid, sm, c->stream, c->E64, c->B64, c->J64, jz);
     } else {
         size_t sm = (MAX_L + (size_t)2 * a.nparts * (FTILE + 2 * a.L)) * sizeof(float);
         const float *jz = c->taps.empty() ? c->Jf + (size_t)2 * a.nparts * a.plane : c->Jzf;
-        k_ampere<float><<<grid, FTILE, sm, c->stream>>>(c->E, c->B, c->Jf, jz, a);
+        ampere_dispatch<float>(a, grid, sm, c->stream, c->E, c->B, c->Jf, jz);
     }
     prof_end(c, KC_AMPERE);
 }
