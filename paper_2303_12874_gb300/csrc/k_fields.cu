@@ -214,6 +214,10 @@ void launch_faraday(qpic_ctx *c)
 // ---------------------------------------------------------------- J_z filter
 // J_z <- K * J_z along z (symbol [k]_Yee/[k]_B): keeps Gauss's law in the dual
 // form when the deposit satisfies the two-point continuity equation.
+// Each thread filters JR consecutive columns, keeping the two sides of the
+// symmetric stencil in sliding register windows: two shared loads per tap for
+// all JR outputs.  A block covers JTILE * JR columns of one row and part.
+static const int JR4 = 4;
 template <typename T>
 __global__ void __launch_bounds__(JTILE) k_jfilter(const T *__restrict__ Jf, T *__restrict__ Jzf,
                                                   GridArgs a, int nk)
@@ -221,34 +225,60 @@ __global__ void __launch_bounds__(JTILE) k_jfilter(const T *__restrict__ Jf, T *
     extern __shared__ __align__(16) unsigned char shraw2[];
     T *sh2 = reinterpret_cast<T *>(shraw2);
     const int j = blockIdx.y, p = blockIdx.z;
-    const int i0 = blockIdx.x * JTILE;
-    const int H = nk - 1, W = JTILE + 2 * H;
+    const int i0 = blockIdx.x * (JTILE * JR4);
+    const int H = nk - 1, W = JTILE * JR4 + 2 * H;
     T *sT = sh2, *sh = sh2 + MAX_TAPS;
     for (int k = threadIdx.x; k < nk; k += JTILE)
         sT[k] = sizeof(T) == 8 ? (T)a.coef64[2 * MAX_L + k] : (T)a.coef[2 * MAX_L + k];
     const T *src = Jf + (size_t)(2 * a.nparts + p) * a.plane + (size_t)j * a.nzp;
-    for (int k = threadIdx.x; k < W; k += JTILE) sh[k] = src[wrapz(i0 - H + k, a.nzp)];
+    const bool wide = a.nzp >= W;
+    for (int k = threadIdx.x; k < W; k += JTILE)
+        sh[k] = src[wide ? wrap1(i0 - H + k, a.nzp) : wrapz(i0 - H + k, a.nzp)];
     __syncthreads();
-    const int i = i0 + threadIdx.x;
-    if (i >= a.nzp) return;
-    const int s = threadIdx.x + H;
-    T acc = sT[0] * sh[s];
-    for (int q = 1; q < nk; q++) acc += sT[q] * (sh[s + q] + sh[s - q]);
-    Jzf[(size_t)p * a.plane + (size_t)j * a.nzp + i] = in_gap(i, a) ? (T)0 : acc;
+    const int ib = i0 + threadIdx.x * JR4;
+    if (ib >= a.nzp) return;
+    const int s = threadIdx.x * JR4 + H;              // smem index of column ib
+    T acc[JR4], R[JR4], L[JR4];
+    const T c0 = sT[0];
+#pragma unroll
+    for (int r = 0; r < JR4; r++) {
+        acc[r] = c0 * sh[s + r];
+        R[r] = nk > 1 ? sh[s + r + 1] : (T)0;          // sh[s + r + q] at q = 1
+        L[r] = nk > 1 ? sh[s + r - 1] : (T)0;          // sh[s + r - q] at q = 1
+    }
+    for (int q = 1; q < nk; q++) {
+        const T cq = sT[q];
+#pragma unroll
+        for (int r = 0; r < JR4; r++) acc[r] += cq * (R[r] + L[r]);
+        if (q + 1 == nk) break;                        // the windows' next values lie in the halo
+        const T rn = sh[s + JR4 + q], ln = sh[s - q - 1];
+#pragma unroll
+        for (int r = 0; r < JR4 - 1; r++) R[r] = R[r + 1];
+        R[JR4 - 1] = rn;
+#pragma unroll
+        for (int r = JR4 - 1; r > 0; r--) L[r] = L[r - 1];
+        L[0] = ln;
+    }
+    T *dst = Jzf + (size_t)p * a.plane + (size_t)j * a.nzp;
+#pragma unroll
+    for (int r = 0; r < JR4; r++) {
+        const int i = ib + r;
+        if (i < a.nzp) dst[i] = in_gap(i, a) ? (T)0 : acc[r];
+    }
 }
 
 void launch_jfilter(qpic_ctx *c)
 {
     GridArgs a = grid_args(c);
     int nk = (int)c->taps.size();
-    dim3 grid((a.nzp + JTILE - 1) / JTILE, a.nr + 1, a.nparts);
+    dim3 grid((a.nzp + JTILE * JR4 - 1) / (JTILE * JR4), a.nr + 1, a.nparts);
     prof_begin(c);
     if (c->fp64) {
-        size_t sm = (size_t)(MAX_TAPS + JTILE + 2 * (nk - 1)) * sizeof(double);
+        size_t sm = (size_t)(MAX_TAPS + JTILE * JR4 + 2 * (nk - 1)) * sizeof(double);
         cudaFuncSetAttribute(k_jfilter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_jfilter<double><<<grid, JTILE, sm, c->stream>>>(c->J64, c->Jz64, a, nk);
     } else {
-        size_t sm = (size_t)(MAX_TAPS + JTILE + 2 * (nk - 1)) * sizeof(float);
+        size_t sm = (size_t)(MAX_TAPS + JTILE * JR4 + 2 * (nk - 1)) * sizeof(float);
         k_jfilter<float><<<grid, JTILE, sm, c->stream>>>(c->Jf, c->Jzf, a, nk);
     }
     prof_end(c, KC_JFILTER);
