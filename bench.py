@@ -138,8 +138,22 @@ def _init_state(sim, w):
 def batch_scan(q, torch, stream, nruns, steps, seed=5):
     """Parameter scan of independent periodic runs (grids 256-1024 x 32-128,
     n 0.003-0.02, a0 1-4, ppc 8/16/32; run k draws from a generator seeded
-    (seed, k)).  The same runs are stepped one after another, then together as
-    one graph-launched batch.  Returns aggregate particle-steps/s of both."""
+    (seed, k)).  The tile shape of each particles-per-cell class comes from the
+    autotuner (a 512 x 64 run of that class, sort period 2 for all).  The same
+    runs are stepped one after another, then together as one graph-launched
+    batch.  Returns aggregate particle-steps/s of both."""
+    from paper_2303_12874_gb300 import autotune
+    tiles = {}
+    for ppc_ in ((2, 2, 2), (2, 2, 4), (2, 2, 8)):
+        def make(tz, tr, sp):
+            return q.Sim(512, 64, 0.2, 0.5, stream=stream, tile_z=tz, tile_r=tr, sort_period=sp)
+
+        def init(sim, ppc_=ppc_):
+            sim.load_plasma(0.01, 0.0, 0.0, ppc_)
+            sim.add_laser(2.0, 8.0, 15.0, 51.2, 51.2)
+        tz, tr, _, _ = autotune.tune(make, init, 512, 64, 2, int(np.prod(ppc_)), steps=4, warmup=2,
+                                     sort_periods=(2,))
+        tiles[ppc_] = (tz, tr)
     sims, npart = [], []
     for k in range(nruns):
         rng = np.random.default_rng([seed, k])
@@ -148,7 +162,8 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
         n0 = float(rng.uniform(0.003, 0.02))
         a0 = float(rng.uniform(1.0, 4.0))
         ppc = [(2, 2, 2), (2, 2, 4), (2, 2, 8)][int(rng.integers(0, 3))]
-        sim = q.Sim(nz, nr, 0.2, 0.5, stream=stream, seed=seed * 1000 + k)
+        sim = q.Sim(nz, nr, 0.2, 0.5, stream=stream, seed=seed * 1000 + k, tile_z=tiles[ppc][0],
+                    tile_r=tiles[ppc][1])
         sim.load_plasma(n0, 0.0, 0.0, ppc)
         zc = 0.5 * nz * 0.2
         sim.add_laser(a0, 8.0, 15.0, zc, zc)
@@ -177,6 +192,7 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
     for sm in sims:
         sm.close()
     return {"runs": nruns, "particles": int(total), "steps": steps,
+            "tiles": {"ppc %d" % int(np.prod(k)): "%dx%d" % v for k, v in tiles.items()},
             "sequential": total * steps / (seq_ms / 1e3), "batched_graph": total * steps / (bat_ms / 1e3),
             "speedup": seq_ms / bat_ms, "unit": "particle-steps/s"}
 
@@ -458,7 +474,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--batch-runs", type=int, default=64)
-    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-steps", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -36,11 +36,15 @@ def _save_cache(cache):
 
 
 def tune(make_sim, init_state, nz, nr, n_modes, ppc, periodic=True, steps=8, warmup=2,
-         use_cache=True):
+         use_cache=True, sort_periods=None):
     """make_sim(tile_z, tile_r, sort_period) -> Sim; init_state(sim) loads the
-    run's plasma and laser.  Returns (tile_z, tile_r, sort_period, ms_per_step)."""
+    run's plasma and laser.  sort_periods: the periods to try (default 1 and
+    2; a batch needs one common period).  Returns (tile_z, tile_r,
+    sort_period, ms_per_step)."""
     import torch
-    key = _key(nz, nr, n_modes, ppc, periodic)
+    periods = list(sort_periods) if sort_periods else SORT_PERIODS
+    key = _key(nz, nr, n_modes, ppc, periodic) + ("" if periods == SORT_PERIODS else
+                                                  "_sp" + "-".join(map(str, periods)))
     cache = _load_cache() if use_cache else {}
     if key in cache:
         c = cache[key]
@@ -48,7 +52,7 @@ def tune(make_sim, init_state, nz, nr, n_modes, ppc, periodic=True, steps=8, war
     best = None
     stream = torch.cuda.current_stream()
     for tz, tr in TILES:
-        for sp in SORT_PERIODS:
+        for sp in periods:
             sim = make_sim(tz, tr, sp)
             init_state(sim)
             sim.step(warmup)
