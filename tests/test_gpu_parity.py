@@ -169,3 +169,27 @@ def test_multi_step_config1_tracks_oracle():
     o.step(20)
     compare_fields(sim, o, "E", 1e-4)
     compare_fields(sim, o, "B", 1e-4)
+
+
+@pytest.mark.parametrize("n_modes,tile", [(1, (16, 8)), (2, (32, 8)), (2, (8, 8)), (2, (16, 16)),
+                                          (2, (32, 4)), (3, (16, 8)), (4, (16, 8))])
+def test_particle_stage_tiled(n_modes, tile):
+    """particles sorted into tiles first, so the deposit runs through the staged
+    shared-memory tiles (register sums for moves inside a cell, the queue for
+    moves across cells) rather than the global-memory path of fresh particles;
+    nz = 100 and nr = 19 leave ragged tiles for every shape"""
+    nz, nr = 100, 19
+    from oracle import coeffs as C
+    dt = min(0.13, 0.9 * C.cfl_dt(DZ, DR, nr, n_modes, "dual"))    # higher m lowers the limit
+    sim, o = make_pair(nz, nr, DZ, DR, dt, n_modes=n_modes, tile=tile)
+    set_random_fields(sim, 5, amp=0.5)
+    sync_fields(sim, o)
+    load_same_particles(sim, o, _random_particles(30000, nz, nr, 6))
+    sim.run_stages(16)                   # sort into tiles
+    sim.run_stages(2)                    # gather + push + deposit (+ reduction)
+    o.push_deposit()
+    compare_fields(sim, o, "J", TOL)
+    ke_g = sim.diag()["kinetic"]
+    pr = o.particles()
+    ke_o = float(np.sum(pr["w"] * (np.sqrt(1 + pr["ux"] ** 2 + pr["uy"] ** 2 + pr["uz"] ** 2) - 1)))
+    assert abs(ke_g / ke_o - 1) < 1e-5
