@@ -125,6 +125,15 @@ long long phys_col(const qpic_ctx *c, long long il)
     return p < 0 ? p + c->g.nzp : p;
 }
 
+// logical columns [0, nz) map onto physical columns by a rotation: columns
+// [0, split) start at physical column c0, the rest at column 0
+struct ColMap { long long c0, split; };
+ColMap col_map(const qpic_ctx *c)
+{
+    const long long c0 = phys_col(c, 0);
+    return {c0, std::min<long long>(c->g.nz, c->g.nzp - c0)};
+}
+
 double *field_base64(qpic_ctx *c, int which)
 {
     switch (which) {
@@ -405,7 +414,7 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->ntr = (g.nr + c->TR - 1) / c->TR;
     c->nkeys = (long long)c->ntz * c->ntr * c->TZ * c->TR;
     const int nb = (int)((c->nkeys + 1 + 4095) / 4096);
-    c->red_cap = std::max(4 * (g.nr + 1) * g.nm + 64, 8 + 3 * 305);
+    c->red_cap = std::max(4 * (g.nr + 1) * g.nm + 64, 8 + 3 * 609);
     if (!c->fp64) {
         const size_t tw = gpd_tile_words(g.nparts, c->TZ, c->TR) * (size_t)c->ntz * c->ntr;
         if (!alloc_arr(c, &c->Jtile, tw) || !alloc_arr(c, &c->tstamp, (size_t)c->ntz * c->ntr) ||
@@ -554,9 +563,6 @@ qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const d
         return fail(c, QPIC_EINVAL, "load_particles arguments");
     qpic_status s = ensure_capacity(c, n);
     if (s != QPIC_OK) return s;
-    double qmax = 0.0;
-    for (long long i = 0; i < n; i++) qmax = std::max(qmax, std::fabs(w[i]));
-    set_qscale(c, qmax);
     double *tmp = nullptr;
     if (n > 0) {
         if (!alloc_arr(c, &tmp, (size_t)7 * n)) return fail(c, QPIC_ENOMEM, "staging buffer");
@@ -565,6 +571,8 @@ qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const d
             cudaMemcpyAsync(tmp + (size_t)k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
     }
+    // fixed-point scale from the largest weight (a device reduction over the copy)
+    set_qscale(c, n > 0 ? launch_absmax(c, tmp + (size_t)6 * n, n) : 0.0);
     if (c->fp64) {
         fp64_load_particles(c, n, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n, tmp + 5 * n,
                             tmp + 6 * n);
@@ -622,6 +630,7 @@ qpic_status qpic_get_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
         return fail(c, QPIC_EINVAL, "get_field arguments");
     const FieldGeom &g = c->g;
     const size_t nout = (size_t)(g.nr + 1) * g.nz;
+    const ColMap cm = col_map(c);
     if (which == QPIC_FIELD_RHO) {
         double *d = nullptr;
         size_t sz = (size_t)g.nm * 2 * nout;
@@ -651,7 +660,7 @@ qpic_status qpic_get_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "get_field");
         for (int j = 0; j <= g.nr; j++)
             for (int il = 0; il < g.nz; il++) {
-                size_t q = (size_t)j * g.nzp + phys_col(c, il);
+                size_t q = (size_t)j * g.nzp + (il < cm.split ? cm.c0 + il : il - cm.split);
                 re[(size_t)j * g.nz + il] = dre[q];
                 if (im) im[(size_t)j * g.nz + il] = dim[q];
             }
@@ -672,7 +681,7 @@ qpic_status qpic_get_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "get_field");
     for (int j = 0; j <= g.nr; j++)
         for (int il = 0; il < g.nz; il++) {
-            size_t q = (size_t)j * g.nzp + phys_col(c, il);
+            size_t q = (size_t)j * g.nzp + (il < cm.split ? cm.c0 + il : il - cm.split);
             re[(size_t)j * g.nz + il] = hre[q];
             if (im) im[(size_t)j * g.nz + il] = him[q];
         }
@@ -686,11 +695,12 @@ qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
         (which != QPIC_FIELD_E && which != QPIC_FIELD_B && which != QPIC_FIELD_BBAR))
         return fail(c, QPIC_EINVAL, "set_field arguments");
     const FieldGeom &g = c->g;
+    const ColMap cm = col_map(c);
     if (c->fp64) {
         std::vector<double> dre(g.plane, 0.0), dim(g.plane, 0.0);
         for (int j = 0; j <= g.nr; j++)
             for (int il = 0; il < g.nz; il++) {
-                size_t q = (size_t)j * g.nzp + phys_col(c, il);
+                size_t q = (size_t)j * g.nzp + (il < cm.split ? cm.c0 + il : il - cm.split);
                 dre[q] = re[(size_t)j * g.nz + il];
                 dim[q] = im ? im[(size_t)j * g.nz + il] : 0.0;
             }
@@ -704,13 +714,19 @@ qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
         cudaStreamSynchronize(c->stream);
         return cuda_check(c, "set_field");
     }
-    std::vector<float> hre(g.plane, 0.f), him(g.plane, 0.f);
-    for (int j = 0; j <= g.nr; j++)
-        for (int il = 0; il < g.nz; il++) {
-            size_t q = (size_t)j * g.nzp + phys_col(c, il);
-            hre[q] = (float)re[(size_t)j * g.nz + il];
-            him[q] = im ? (float)im[(size_t)j * g.nz + il] : 0.f;
+    std::vector<float> hre(g.plane, 0.f), him(mode ? g.plane : 0, 0.f);
+    for (int j = 0; j <= g.nr; j++) {
+        const double *rr = re + (size_t)j * g.nz;
+        float *dr_ = hre.data() + (size_t)j * g.nzp;
+        for (long long il = 0; il < cm.split; il++) dr_[cm.c0 + il] = (float)rr[il];
+        for (long long il = cm.split; il < g.nz; il++) dr_[il - cm.split] = (float)rr[il];
+        if (mode && im) {
+            const double *ri = im + (size_t)j * g.nz;
+            float *di = him.data() + (size_t)j * g.nzp;
+            for (long long il = 0; il < cm.split; il++) di[cm.c0 + il] = (float)ri[il];
+            for (long long il = cm.split; il < g.nz; il++) di[il - cm.split] = (float)ri[il];
         }
+    }
     float *base = field_base(c, which);
     int pre = mode == 0 ? 0 : 2 * mode - 1;
     cudaMemcpyAsync(base + (size_t)(comp * g.nparts + pre) * g.plane, hre.data(),

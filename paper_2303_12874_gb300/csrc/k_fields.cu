@@ -561,17 +561,36 @@ __global__ void k_energy_partial(const T *E, const T *B, GridArgs a, double *par
     else Vi = 2.0 * PI * j * dr * dr * dz;
     Vh = (j < a.nr) ? 2.0 * PI * (j + 0.5) * dr * dr * dz : 0.0;
     double s = 0.0;
-    for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < a.nz; il += gridDim.x * blockDim.x) {
-        int col = wrapz(il + (int)a.zoff, a.nzp);
-        size_t base = (size_t)j * a.nzp + col;
-        for (int k = 0; k < (m ? 2 : 1); k++) {
-            int p = m ? 2 * m - 1 + k : 0;
-            auto v2 = [&](const T *F, int comp) {
-                double x = F[(size_t)(comp * a.nparts + p) * a.plane + base];
-                return x * x;
-            };
-            s += Vh * (v2(E, 0) + v2(B, 1) + v2(B, 2)) + Vi * (v2(E, 1) + v2(E, 2) + v2(B, 0));
+    if constexpr (sizeof(T) == 8) {
+        for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < a.nz; il += gridDim.x * blockDim.x) {
+            int col = wrapz(il + (int)a.zoff, a.nzp);
+            size_t base = (size_t)j * a.nzp + col;
+            for (int k = 0; k < (m ? 2 : 1); k++) {
+                int p = m ? 2 * m - 1 + k : 0;
+                auto v2 = [&](const T *F, int comp) {
+                    double x = F[(size_t)(comp * a.nparts + p) * a.plane + base];
+                    return x * x;
+                };
+                s += Vh * (v2(E, 0) + v2(B, 1) + v2(B, 2)) + Vi * (v2(E, 1) + v2(E, 2) + v2(B, 0));
+            }
         }
+    } else {
+        // FP32 fields: squares summed per row class in double-float (FP64-grade,
+        // on the FP32 pipe), weighted by the row's volumes in FP64 at the end
+        DFAcc sh_, si_;
+        for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < a.nz; il += gridDim.x * blockDim.x) {
+            const int col = wrapz(il + (int)a.zoff, a.nzp);
+            const size_t base = (size_t)j * a.nzp + col;
+            for (int k = 0; k < (m ? 2 : 1); k++) {
+                const int p = m ? 2 * m - 1 + k : 0;
+                auto f = [&](const T *F, int comp) { return (float)F[(size_t)(comp * a.nparts + p) * a.plane + base]; };
+                const float er = f(E, 0), bp = f(B, 1), bz = f(B, 2);
+                const float ep = f(E, 1), ez = f(E, 2), br = f(B, 0);
+                sh_.add_prod(er, er); sh_.add_prod(bp, bp); sh_.add_prod(bz, bz);
+                si_.add_prod(ep, ep); si_.add_prod(ez, ez); si_.add_prod(br, br);
+            }
+        }
+        s = Vh * sh_.value() + Vi * si_.value();
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -583,14 +602,21 @@ __global__ void k_energy_partial(const T *E, const T *B, GridArgs a, double *par
         part[((size_t)m * gridDim.y + j) * gridDim.x + blockIdx.x] = red[0] * (m ? 1.0 : 0.5);
 }
 
+// one block per segment: each thread sums a fixed strided subset, then a
+// fixed-shape tree (the order of every addition is fixed: deterministic)
 __global__ void k_sum_ordered(const double *part, int n_per, int nseg, double *out)
 {
-    // one thread per segment, sums in index order (deterministic)
-    int sgm = threadIdx.x;
-    if (sgm >= nseg) return;
+    __shared__ double red[256];
+    const int sgm = blockIdx.x;
     double s = 0.0;
-    for (int k = 0; k < n_per; k++) s += part[(size_t)sgm * n_per + k];
-    out[sgm] = s;
+    for (int k = threadIdx.x; k < n_per; k += 256) s += part[(size_t)sgm * n_per + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[sgm] = red[0];
 }
 
 void launch_field_energy(qpic_ctx *c, double *out_modes)
@@ -603,7 +629,7 @@ void launch_field_energy(qpic_ctx *c, double *out_modes)
     prof_begin(c);
     if (c->fp64) k_energy_partial<double><<<grid, 256, 0, c->stream>>>(c->E64, c->B64, a, c->d_red);
     else k_energy_partial<float><<<grid, 256, 0, c->stream>>>(c->E, c->B, a, c->d_red);
-    k_sum_ordered<<<1, 32, 0, c->stream>>>(c->d_red, nbx * (a.nr + 1), nm, c->d_red + need - nm);
+    k_sum_ordered<<<nm, 256, 0, c->stream>>>(c->d_red, nbx * (a.nr + 1), nm, c->d_red + need - nm);
     prof_end(c, KC_DIAG, 2);
     cudaMemcpyAsync(out_modes, c->d_red + need - nm, nm * sizeof(double), cudaMemcpyDeviceToHost,
                     c->stream);

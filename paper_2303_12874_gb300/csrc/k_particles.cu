@@ -3,6 +3,8 @@
 //
 // k_count / scan / k_scatter: counting sort of live particles by a tile-major
 // cell key; dead particles are dropped.
+#include <string.h>
+
 #include "gpd.cuh"
 
 namespace qpic {
@@ -501,6 +503,40 @@ void launch_rho(qpic_ctx *c, double *dplanes)
     if (n > 0) k_rho<<<nblk, 256, 0, c->stream>>>(c->p, n, dplanes, L, c->g.nm);
 }
 
+// max |w| of n doubles: block maxima of the bit patterns (non-negative doubles
+// order like their unsigned patterns), then one atomicMax per block
+__global__ void k_absmax(const double *w, long long n, unsigned long long *out)
+{
+    __shared__ unsigned long long red[256];
+    unsigned long long mx = 0ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double a = fabs(w[i]);
+        const unsigned long long b = isfinite(a) ? (unsigned long long)__double_as_longlong(a) : 0ull;
+        mx = b > mx ? b : mx;
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k && red[threadIdx.x + k] > red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out, red[0]);
+}
+
+double launch_absmax(qpic_ctx *c, const double *w, long long n)
+{
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(c->d_red);
+    cudaMemsetAsync(d, 0, sizeof(unsigned long long), c->stream);
+    if (n > 0) k_absmax<<<152 * 4, 256, 0, c->stream>>>(w, n, d);
+    unsigned long long h = 0ull;
+    cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    double v;
+    memcpy(&v, &h, sizeof(v));
+    return v;
+}
+
 __global__ void k_scale(double *buf, size_t n, double s)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -551,22 +587,37 @@ void launch_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale, un
 }
 
 // ------------------------------------------------------------ particle sums
+// per-thread sums as an integer count and double-float charge and kinetic
+// energy (FP64-grade, on the FP32 pipe); the block and grid sums are FP64
 __global__ void k_psums_partial(Particles P, const long long *dcount, double *part)
 {
     __shared__ double s0[256], s1[256], s2[256];
     const long long n = dcount[0];
-    double cnt = 0, chg = 0, ke = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (P.cell[i] < 0) continue;
-        const float4 rb = P.rec[2 * i + 1];
-        const float ux = rb.x, uy = rb.y, uz = rb.z;
-        const float u2 = ux * ux + uy * uy + uz * uz;
-        const float gm1 = u2 / (1.f + sqrtf(1.f + u2));          // gamma - 1 without cancellation
-        cnt += 1.0; chg -= (double)rb.w;
-        ke += (double)rb.w * (double)gm1;
+    long long cnt = 0;
+    DFAcc chg, ke;
+    // four particles per pass, all loads issued before any is used
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        int cl[4];
+        float4 rb[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = i0 + u * stride;
+            cl[u] = i < n ? P.cell[i] : -1;
+            rb[u] = i < n ? P.rec[2 * i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (cl[u] < 0) continue;
+            const float ux = rb[u].x, uy = rb[u].y, uz = rb[u].z;
+            const float u2 = ux * ux + uy * uy + uz * uz;
+            const float gm1 = u2 / (1.f + sqrtf(1.f + u2));      // gamma - 1 without cancellation
+            cnt += 1;
+            chg.add(rb[u].w);
+            ke.add_prod(rb[u].w, gm1);
+        }
     }
-    s0[threadIdx.x] = cnt; s1[threadIdx.x] = chg; s2[threadIdx.x] = ke;
+    s0[threadIdx.x] = (double)cnt; s1[threadIdx.x] = -chg.value(); s2[threadIdx.x] = ke.value();
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
@@ -582,22 +633,30 @@ __global__ void k_psums_partial(Particles P, const long long *dcount, double *pa
     }
 }
 
+// one block per quantity: fixed strided subsets, then a fixed-shape tree (deterministic)
 __global__ void k_psums_final(const double *part, int nb, double *out)
 {
-    if (threadIdx.x >= 3) return;
+    __shared__ double red[256];
+    const int qn = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nb; b++) s += part[3 * b + threadIdx.x];
-    out[threadIdx.x] = s;
+    for (int b = threadIdx.x; b < nb; b += 256) s += part[3 * b + qn];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[qn] = red[0];
 }
 
 void launch_particle_sums(qpic_ctx *c, double *out3)
 {
-    const int nb = 304;
+    const int nb = 608;
     double *part = c->d_red + 8;
     long long *dcount = c->d_count;
     prof_begin(c);
     k_psums_partial<<<nb, 256, 0, c->stream>>>(c->p, dcount, part);
-    k_psums_final<<<1, 32, 0, c->stream>>>(part, nb, part + 3 * nb);
+    k_psums_final<<<3, 256, 0, c->stream>>>(part, nb, part + 3 * nb);
     prof_end(c, KC_DIAG, 2);
     cudaMemcpyAsync(out3, part + 3 * nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaStreamSynchronize(c->stream);

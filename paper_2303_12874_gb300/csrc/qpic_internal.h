@@ -57,6 +57,32 @@ enum KernelClass {
     KC_INJECT, KC_DIAG, KC_OTHER, KC_COUNT
 };
 
+#ifdef __CUDACC__
+// Double-float accumulator for FP64-grade sums of FP32 terms on the FP32 pipe
+// (FP64 arithmetic is slow on this part): hi + lo, each addition exact through
+// TwoSum (Knuth), products split exactly with an FMA.  Relative error of a sum
+// of n terms about n * 2^-48; read out in FP64.
+struct DFAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = __fadd_rn(hi, x);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);       // a b - p, exact
+        add(p);
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+#endif
+
 }  // namespace qpic
 
 struct qpic_ctx {
@@ -164,6 +190,7 @@ void launch_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale,
 void launch_gpd(qpic_ctx *c);
 bool gpd_tile_supported(int tile_z, int tile_r);
 size_t gpd_tile_words(int nparts, int tile_z, int tile_r);   // accumulator words per tile
+double launch_absmax(qpic_ctx *c, const double *w, long long n);  // max |w[i]| (device array; syncs)
 void launch_sort(qpic_ctx *c);
 int launch_load_plasma(qpic_ctx *c, long long first_logical_col, int ncols, bool append);
 void launch_load_particles(qpic_ctx *c, long long n, const double *dz_, const double *dr_,
