@@ -221,6 +221,12 @@ def oracle_sample(w, dt, nz_sample, steps):
     return n * steps / t, n, t
 
 
+def _config(args, w, ws):
+    """the workload keys both arms report"""
+    return {"workload": args.workload, "nz": w["nz"], "nr": w["nr"], "modes": w["n_modes"],
+            "ppc": list(w["plasma"]["ppc"]), "solver": "dual L=16", "parallelism": "replicas x%d" % ws}
+
+
 def run_reference(args, w):
     """--impl reference: the FP64 CPU oracle (this repository's reference
     implementation of the method) on the host cores, bounded per step."""
@@ -234,11 +240,12 @@ def run_reference(args, w):
     rate, n, t = oracle_sample(w, dt, nz_s, args.steps)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "particle-steps/s",
-        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": "z-slab of %d of %d columns" % (nz_s, w["nz"]),
-                   "particles": n, "nr": w["nr"], "ppc": list(w["plasma"]["ppc"])},
+        "config": dict(_config(args, w, ws), dt=dt,
+                       sample="each step: a periodic z-slab of %d of the %d columns (%d particles)"
+                              % (nz_s, w["nz"], n)),
         "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "%d steps of a %d x %d periodic slab (%d particles)"
                                    % (args.steps, nz_s, w["nr"], n)},
@@ -428,12 +435,9 @@ def run_ours(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "nz": w["nz"], "nr": w["nr"],
-                       "modes": w["n_modes"], "ppc": list(w["plasma"]["ppc"]),
-                       "particles_per_gpu": int(n_avg), "solver": "dual L=16",
-                       "dt": dt_used, "deposit": "int64 fixed point",
-                       "l2": "inputs larger than L2 (particles %.1f GB)" % (n_avg * 36 / 1e9),
-                       "parallelism": "replicas x%d" % ws},
+            "config": dict(_config(args, w, ws), particles_per_gpu=int(n_avg), dt=dt_used,
+                           deposit="int64 fixed point",
+                           l2="inputs larger than L2 (particles %.1f GB)" % (n_avg * 36 / 1e9)),
             "cell_updates_per_s": cell_updates,
             "solver_cell_updates_per_s": cells * args.prof_steps / (solver_ms / 1e3) if solver_ms else None,
             "gpd_particle_steps_per_s": n_avg / (gpd_avg / 1e3),
