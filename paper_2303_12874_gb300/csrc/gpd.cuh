@@ -15,10 +15,16 @@
 //      accumulators.  The modal charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
 //      splits into (S1 - S0)(e0 + e1)/2, carried by 2D Esirkepov r/z fluxes,
 //      and (S0 + S1)/2 (e1 - e0), carried by J_phi through (i m / r) J_phi.
-//   4. the tile's accumulators go to global memory with int64 atomics; integer
-//      addition makes the step independent of particle order (bit-reproducible).
+//      Moves inside a cell are summed in registers per thread (FastSum) and
+//      added once per run of moves; moves across cells are queued and
+//      deposited once per tile.
+//   4. the tile's accumulators are stored to its own block of global memory;
+//      k_jreduce sums the blocks that cover each node.  Integer addition makes
+//      the step independent of particle order (bit-reproducible).
 //   Particles beyond the staged halo (drift between sorts, or injected by the
-//   moving window) run the same code against global memory.
+//   moving window) run the same code against global memory (int64 atomics).
+//   The FA variant adds every contribution to a global FP32 current with float
+//   atomics instead (precision QPIC_FP32_FATOMIC).
 //
 // k_jreduce: per node, the sum of the tile blocks that cover it, decoded to
 // FP32 current.
