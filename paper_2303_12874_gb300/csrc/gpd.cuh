@@ -942,8 +942,10 @@ static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles,
 // mark equals the step's epoch), the global accumulator (then cleared), summed
 // in a fixed order in int64 and turned into FP32 current with the per-row
 // finite-volume factor.
+// as many blocks per SM as its 2048 threads allow: the kernel is latency
+// bound, and occupancy matters more than the few registers it then spills
 template <int NP, int TZ, int TR>
-__global__ void __launch_bounds__(3 * TZ * TR) k_jreduce(const unsigned long long *__restrict__ Jtile,
+__global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(const unsigned long long *__restrict__ Jtile,
                                                          const int *__restrict__ tstamp,
                                                          const int *__restrict__ d_epoch,
                                                          unsigned long long *__restrict__ Jacc,
