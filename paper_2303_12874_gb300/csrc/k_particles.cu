@@ -109,14 +109,23 @@ __global__ void k_count(const int32_t *__restrict__ cell, const long long *dcoun
     const long long np = dcount[0];
     const long long stride = (long long)gridDim.x * blockDim.x;
     const unsigned lane = threadIdx.x & 31;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < np; i0 += stride) {
-        const long long i = i0 + threadIdx.x;
-        const int c = i < np ? cell[i] : -1;
-        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
-        if (c >= 0) {
-            const int k = sort_key(c, a);
-            const unsigned grp = __match_any_sync(act, k);
-            if (lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&counts[k], __popc(grp));
+    // four warp-wide passes per iteration, their loads issued first
+    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < np; i0 += 4 * stride) {
+        int cu[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = i0 + u * stride + threadIdx.x;
+            cu[u] = i < np ? cell[i] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int c = cu[u];
+            const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+            if (c >= 0) {
+                const int k = sort_key(c, a);
+                const unsigned grp = __match_any_sync(act, k);
+                if (lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&counts[k], __popc(grp));
+            }
         }
     }
 }
