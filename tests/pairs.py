@@ -1,8 +1,10 @@
 """Helpers for GPU-vs-oracle parity tests: build a CUDA context and an oracle
 box with the same grid and time step (each side fits its own coefficients),
-and inject one identical state into both.  The state is first written to the
-GPU and read back, so the oracle starts from exactly the FP32-rounded values
-the kernels see; a comparison after one step then measures that step only."""
+and give both the same state.  Data only flow towards the GPU: both sides get
+the same FP64 seeded inputs (the GPU rounds them to FP32), or the oracle
+evolves a state that is then loaded into the GPU.  Nothing read back from the
+GPU is ever an oracle input; a one-step comparison therefore includes the FP32
+rounding of the inputs (about 1e-7, well inside the 1e-5 tolerance)."""
 import numpy as np
 
 import oracle
@@ -25,32 +27,73 @@ def make_pair(nz, nr, dz, dr, dt, n_modes=2, solver="dual", periodic=True, jz_fi
     return sim, o
 
 
-def sync_fields(sim, o, which_list=("E", "B", "Bbar")):
-    """copy the GPU's (FP32-rounded) fields into the oracle"""
-    for which in which_list:
-        for c in COMPS:
-            for m in range(sim.nm):
-                o.set_field(which, c, m, sim.get_field(which, c, m))
-
-
-def set_random_fields(sim, seed, amp=0.3, which_list=("E", "B", "Bbar")):
+def random_field_arrays(nz, nr, nm, seed, amp=0.3, which_list=("E", "B", "Bbar")):
+    """seeded FP64 field planes {(which, comp, mode): [nr+1][nz]} (complex for m >= 1)"""
     rng = np.random.default_rng(seed)
+    out = {}
     for which in which_list:
         for c in COMPS:
-            for m in range(sim.nm):
-                v = rng.standard_normal((sim.nr + 1, sim.nz))
+            for m in range(nm):
+                v = rng.standard_normal((nr + 1, nz))
                 if m:
-                    v = v + 1j * rng.standard_normal((sim.nr + 1, sim.nz))
-                sim.set_field(which, c, m, amp * v)
+                    v = v + 1j * rng.standard_normal((nr + 1, nz))
+                out[(which, c, m)] = amp * v
+    return out
+
+
+def set_same_fields(sim, o, arrays):
+    for (which, c, m), v in arrays.items():
+        sim.set_field(which, c, m, v)
+        o.set_field(which, c, m, v)
+
+
+def set_same_random_fields(sim, o, seed, amp=0.3, which_list=("E", "B", "Bbar")):
+    set_same_fields(sim, o, random_field_arrays(sim.nz, sim.nr, sim.nm, seed, amp, which_list))
 
 
 def load_same_particles(sim, o, parts):
-    sim.load_particles(**parts)
-    p = sim.particles_raw()
+    """the same FP64 particle arrays into both sides"""
+    keys = ("z", "r", "phi", "ux", "uy", "uz", "w")
+    sim.load_particles(**{k: parts[k] for k in keys})
+    o.load_particles(*(np.asarray(parts[k], dtype=np.float64) for k in keys))
+
+
+def oracle_state_to_gpu(o, sim, which_list=("E", "B")):
+    """load the oracle's fields and particles into the GPU context"""
+    for which in which_list:
+        for c in COMPS:
+            for m in range(sim.nm):
+                sim.set_field(which, c, m, o.get_field(which, c, m))
+    p = o.particles()
     live = p["w"] > 0
-    o.load_particles(p["z"][live], p["r"][live], p["phi"][live], p["ux"][live], p["uy"][live],
-                     p["uz"][live], p["w"][live])
-    return p, live
+    sim.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
+
+
+def oracle_config1_state(o, w, dt):
+    """the config-1 plasma (the oracle's generator) and laser on the oracle"""
+    from oracle import setup
+    pl, la = w["plasma"], w["laser"]
+    parts = setup.plasma_cells(np.arange(w["nz"]), w["nr"], w["dz"], w["dr"], pl["n0"], pl["z_start"],
+                               pl["ramp_len"], pl["ppc"], pl["seed"])
+    o.load_particles(**parts)
+    cE, cB = C.solver_coefficients(w.get("solver", "dual"), dt, w["dz"])
+    setup.add_laser(o, cE, cB, la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
+    return parts
+
+
+def distinct_weights(n, seed):
+    """n weights in (0.5, 1.5), pairwise distinct in FP32 (particles can then be
+    matched by weight across buffer orders: the push never changes w)"""
+    rng = np.random.default_rng(seed)
+    return 0.5 + (rng.permutation(n) + 0.5) / n
+
+
+def match_by_weight(g, r):
+    """index arrays (ig, ir) pairing GPU and oracle particles with equal weights"""
+    ig = np.argsort(np.asarray(g["w"], dtype=np.float32), kind="stable")
+    ir = np.argsort(np.asarray(r["w"], dtype=np.float32), kind="stable")
+    assert np.array_equal(np.asarray(g["w"], np.float32)[ig], np.asarray(r["w"], np.float32)[ir])
+    return ig, ir
 
 
 def rel_l2(a, b):

@@ -16,7 +16,7 @@ import paper_2303_12874_gb300 as q
 import synth
 from oracle import coeffs as C
 from oracle import diag
-from pairs import COMPS, sync_fields
+from pairs import oracle_config1_state, oracle_state_to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -46,15 +46,20 @@ def test_spectrum_matches_histogram():
     sim.load_particles(**p)
     edges = np.linspace(0.0, 1.2, 25)
     got = sim.spectrum(edges)
-    g = sim.particles()
-    ref = diag.spectrum(g, edges)
-    assert np.max(np.abs(got - ref)) <= 1e-8 * ref.max()
-    # and the same on the plain FP64 path
+    # expected: the oracle's histogram of the same seeded FP64 particles.  The
+    # GPU holds them in FP32, so a particle within FP32 rounding of a bin edge
+    # may land in the next bin: each bin may differ by the weight of those.
+    ref = diag.spectrum(p, edges)
+    e = (np.sqrt(1 + p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2) - 1) * diag.MEC2_MEV
+    near = np.min(np.abs(e[:, None] - edges[None, :]), axis=1) <= 1e-5 * np.maximum(e, 1e-3)
+    slack = p["w"][near].sum()
+    assert np.max(np.abs(got - ref)) <= 1e-8 * ref.max() + slack
+    assert abs(got.sum() - ref.sum()) <= 1e-8 * ref.sum() + slack
+    # and the same on the plain FP64 path (no rounding of the particles)
     s64 = q.Sim(nz, nr, dz, dr, dt=0.13, precision=q.QPIC_FP64)
     s64.load_particles(**p)
     got64 = s64.spectrum(edges)
-    ref64 = diag.spectrum(s64.particles(), edges)
-    assert np.max(np.abs(got64 - ref64)) <= 1e-8 * ref64.max()
+    assert np.max(np.abs(got64 - ref)) <= 1e-8 * ref.max() + slack
 
 
 def test_full_run_config1_within_one_percent():
@@ -62,15 +67,10 @@ def test_full_run_config1_within_one_percent():
     nz, nr, dz, dr = w["nz"], w["nr"], w["dz"], w["dr"]
     dt = 0.9 * C.cfl_dt(dz, dr, nr, 2, "dual")
     sim = q.Sim(nz, nr, dz, dr, dt=dt)
-    pl, la = w["plasma"], w["laser"]
-    sim.load_plasma(pl["n0"], pl["z_start"], pl["ramp_len"], pl["ppc"])
-    sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
     cE, cB = C.dual_coefficients(dt, dz)
     o = oracle.Oracle(nz, nr, 2, dz, dr, dt, cE, cB, C.filter_taps(cB), periodic=True)
-    sync_fields(sim, o, ("E", "B"))
-    p = sim.particles_raw()
-    live = p["w"] > 0
-    o.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
+    oracle_config1_state(o, w, dt)           # the oracle's plasma and laser, copied to the GPU
+    oracle_state_to_gpu(o, sim)
     nsteps = w["steps"]
     sim.step(nsteps)
     o.step(nsteps)

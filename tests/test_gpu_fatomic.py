@@ -12,7 +12,7 @@ import pytest
 import paper_2303_12874_gb300 as q
 import synth
 from oracle import coeffs as C
-from pairs import compare_fields, make_pair, rel_l2, sync_fields
+from pairs import compare_fields, make_pair, oracle_config1_state, oracle_state_to_gpu, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -26,13 +26,6 @@ def _state(sim):
     sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
 
 
-def _inject(sim, o):
-    sync_fields(sim, o, ("E", "B"))
-    p = sim.particles_raw()
-    live = p["w"] > 0
-    o.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
-
-
 @pytest.mark.parametrize("sort_period", [2, 3])
 def test_fatomic_full_step_matches_oracle(sort_period):
     """sort period 3 also exercises the global-memory path of the same kernel"""
@@ -41,11 +34,12 @@ def test_fatomic_full_step_matches_oracle(sort_period):
     dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], nr, 2, "dual")
     sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, sort_period=sort_period,
                        precision=q.QPIC_FP32_FATOMIC)
-    _state(sim)
-    sim.step(4 if sort_period == 3 else 3)
-    _inject(sim, o)
-    sim.step(1)
-    o.step(1)
+    oracle_config1_state(o, w, dt)
+    o.step(3)                            # the oracle's evolved state goes to the GPU
+    oracle_state_to_gpu(o, sim)
+    nst = 3 if sort_period == 3 else 1
+    sim.step(nst)
+    o.step(nst)
     for which in ("E", "B", "J"):
         compare_fields(sim, o, which, TOL)
 
@@ -53,8 +47,8 @@ def test_fatomic_full_step_matches_oracle(sort_period):
 def test_fatomic_tracks_oracle_over_20_steps():
     w = synth.workload("cfg1_small")
     sim, o = make_pair(w["nz"], w["nr"], w["dz"], w["dr"], 0.13, precision=q.QPIC_FP32_FATOMIC)
-    _state(sim)
-    _inject(sim, o)
+    oracle_config1_state(o, w, 0.13)
+    oracle_state_to_gpu(o, sim)
     sim.step(20)
     o.step(20)
     compare_fields(sim, o, "E", 1e-4)

@@ -1,5 +1,6 @@
-"""CUDA path vs the FP64 oracle, stage by stage and step by step, from
-identical states (tests/pairs.py).  Tolerance: relative L2 <= 1e-5 per field,
+"""CUDA path vs the FP64 oracle, stage by stage and step by step, from the
+same FP64 inputs or from a state the oracle evolved (tests/pairs.py; nothing
+read back from the GPU feeds the oracle).  Tolerance: relative L2 <= 1e-5 per field,
 component and mode for one step (the FP32 + int64 fixed-point target), particle
 coordinates to FP32 precision.  Sizes span several 16 x 8 particle tiles and a
 ragged tail (nz, nr not multiples of the tile)."""
@@ -8,8 +9,9 @@ import pytest
 
 import synth
 from oracle import setup
-from pairs import (COMPS, angle_diff, compare_fields, load_same_particles, make_pair,
-                   rel_l2, set_random_fields, sync_fields)
+from pairs import (COMPS, angle_diff, compare_fields, distinct_weights, load_same_particles,
+                   make_pair, match_by_weight, oracle_config1_state, oracle_state_to_gpu, rel_l2,
+                   set_same_random_fields)
 
 pytestmark = pytest.mark.gpu
 
@@ -18,13 +20,14 @@ TOL = 1e-5
 
 
 def _random_particles(n, nz, nr, seed, umax=1.0):
-    return synth.random_particles(seed, n, nz, nr, DZ, DR, umax=umax)
+    p = synth.random_particles(seed, n, nz, nr, DZ, DR, umax=umax)
+    p["w"] = distinct_weights(n, seed)          # lets particles be matched across buffer orders
+    return p
 
 
 def test_faraday_stage():
     sim, o = make_pair(100, 21, DZ, DR, 0.13)
-    set_random_fields(sim, 1)
-    sync_fields(sim, o)
+    set_same_random_fields(sim, o, 1)
     sim.run_stages(1)
     o.faraday()
     compare_fields(sim, o, "B", 1e-6)
@@ -35,15 +38,18 @@ def test_faraday_stage():
 def test_particle_stage(n_modes):
     nz, nr = 70, 19
     sim, o = make_pair(nz, nr, DZ, DR, 0.13, n_modes=n_modes)
-    set_random_fields(sim, 2, amp=0.5)
-    sync_fields(sim, o)
-    p0, live = load_same_particles(sim, o, _random_particles(20000, nz, nr, 3))
+    set_same_random_fields(sim, o, 2, amp=0.5)
+    load_same_particles(sim, o, _random_particles(20000, nz, nr, 3))
     sim.run_stages(2)                    # gather + push + deposit (+ decode)
     o.push_deposit()
     compare_fields(sim, o, "J", TOL)
     g = sim.particles_raw()
+    live = g["w"] > 0
+    g = {k: v[live] for k, v in g.items()}
     r = o.particles()
-    gl = {k: v[live] for k, v in g.items()}
+    ig, ir = match_by_weight(g, r)
+    gl = {k: v[ig] for k, v in g.items()}
+    r = {k: v[ir] for k, v in r.items()}
     Lz = nz * DZ
     dzz = np.abs((gl["z"] - r["z"] + 0.5 * Lz) % Lz - 0.5 * Lz)
     assert np.max(dzz) < 2e-5 * DZ * 50
@@ -57,8 +63,7 @@ def test_particle_stage(n_modes):
 def test_ampere_stage():
     nz, nr = 70, 19
     sim, o = make_pair(nz, nr, DZ, DR, 0.13)
-    set_random_fields(sim, 4, amp=0.5)
-    sync_fields(sim, o)
+    set_same_random_fields(sim, o, 4, amp=0.5)
     load_same_particles(sim, o, _random_particles(20000, nz, nr, 5))
     sim.run_stages(2 | 4)
     o.push_deposit()
@@ -123,15 +128,14 @@ def test_full_step_config1(solver, sort_period):
     from oracle import coeffs as C
     dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], nr, 2, solver)
     sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, solver=solver, sort_period=sort_period)
-    _config1_state(sim, o)
-    # a few GPU steps to build up currents and plasma motion, then inject that state
-    sim.step(4 if sort_period == 3 else 3)
-    sync_fields(sim, o, ("E", "B"))
-    p = sim.particles_raw()
-    live = p["w"] > 0
-    o.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
-    sim.step(1)
-    o.step(1)
+    oracle_config1_state(o, dict(w, solver=solver), dt)
+    # the oracle builds up currents and plasma motion; its state goes to the GPU
+    o.step(3)
+    oracle_state_to_gpu(o, sim)
+    # sort period 3: steps 2 and 3 run with particles drifted beyond their tiles
+    nst = 3 if sort_period == 3 else 1
+    sim.step(nst)
+    o.step(nst)
     for which in ("E", "B", "J"):
         compare_fields(sim, o, which, TOL)
 
@@ -160,11 +164,8 @@ def test_multi_step_config1_tracks_oracle():
     w = synth.workload("cfg1_small")
     nz, nr = w["nz"], w["nr"]
     sim, o = make_pair(nz, nr, w["dz"], w["dr"], 0.13)
-    _config1_state(sim, o)
-    sync_fields(sim, o, ("E", "B"))
-    p = sim.particles_raw()
-    live = p["w"] > 0
-    o.load_particles(*(p[k][live] for k in ("z", "r", "phi", "ux", "uy", "uz", "w")))
+    oracle_config1_state(o, w, 0.13)
+    oracle_state_to_gpu(o, sim)
     sim.step(20)
     o.step(20)
     compare_fields(sim, o, "E", 1e-4)
@@ -174,16 +175,15 @@ def test_multi_step_config1_tracks_oracle():
 @pytest.mark.parametrize("n_modes,tile", [(1, (16, 8)), (2, (32, 8)), (2, (8, 8)), (2, (16, 16)),
                                           (2, (32, 4)), (3, (16, 8)), (4, (16, 8))])
 def test_particle_stage_tiled(n_modes, tile):
-    """particles sorted into tiles first, so the deposit runs through the staged
-    shared-memory tiles (register sums for moves inside a cell, the queue for
-    moves across cells) rather than the global-memory path of fresh particles;
-    nz = 100 and nr = 19 leave ragged tiles for every shape"""
+    """the deposit through the staged shared-memory tiles (register sums for
+    moves inside a cell, the queue for moves across cells) for every tile shape
+    and one to four modes; nz = 100 and nr = 19 leave ragged tiles for every
+    shape"""
     nz, nr = 100, 19
     from oracle import coeffs as C
     dt = min(0.13, 0.9 * C.cfl_dt(DZ, DR, nr, n_modes, "dual"))    # higher m lowers the limit
     sim, o = make_pair(nz, nr, DZ, DR, dt, n_modes=n_modes, tile=tile)
-    set_random_fields(sim, 5, amp=0.5)
-    sync_fields(sim, o)
+    set_same_random_fields(sim, o, 5, amp=0.5)
     load_same_particles(sim, o, _random_particles(30000, nz, nr, 6))
     sim.run_stages(16)                   # sort into tiles
     sim.run_stages(2)                    # gather + push + deposit (+ reduction)
