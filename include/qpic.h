@@ -220,7 +220,10 @@ qpic_status qpic_get_particles_raw(qpic_ctx *ctx, double *out, int64_t capacity,
 
 /* FP64 diagnostics into out[0..count): [0] time, [1] steps, [2] window shifts,
  * [3] live particles, [4] total charge, [5] kinetic energy sum w (gamma-1),
- * [6..6+M] field energy per mode, then the overflow flag. */
+ * [6..6+M] field energy per mode (1/2 sum V (|E|^2 + |B|^2), modes m >= 1 counted
+ * twice by the Sec. III.B convention F_0 + 2 Re F_m e^{i m phi}), then the
+ * fixed-point overflow flag.  Sums are FP64-grade (per-thread double-float
+ * partial sums, FP64 block and grid sums in a fixed order). */
 qpic_status qpic_get_diag(qpic_ctx *ctx, double *out, int32_t count);
 
 /* Gauss's law residual per mode in the dual form of Eq. 10: out[2m] = L2 norm
@@ -231,24 +234,26 @@ qpic_status qpic_get_diag(qpic_ctx *ctx, double *out, int32_t count);
  * are left out.  QPIC_ESTATE with a moving window (the background would move). */
 qpic_status qpic_gauss_residual(qpic_ctx *ctx, double *out, int32_t count);
 
-/* Energy spectrum of the electrons: weights[k] = sum of w over particles with
+/* Energy spectrum of the electrons (the spectra of Sec. IV): weights[k] = sum of w over particles with
  * kinetic energy (gamma - 1) 0.511 MeV in [edges_mev[k], edges_mev[k+1]),
  * k < nbins (edges strictly increasing, nbins <= 4096).  Weights are summed in
  * int64 fixed point, so the result does not depend on particle order. */
 qpic_status qpic_spectrum(qpic_ctx *ctx, const double *edges_mev, int32_t nbins, double *weights);
 
-/* Number of CUDA kernels this context has launched so far. */
+/* Number of CUDA kernels this context has launched so far (bookkeeping; the
+ * paper has no counterpart). */
 qpic_status qpic_launch_count(const qpic_ctx *ctx, int64_t *n);
 
 /* Per-kernel device time (ms, CUDA events on the context's stream) and launch
  * counts accumulated since the last reset, for n kernel classes; names gives
- * "name" strings (static).  Timing is on only when enabled. */
+ * "name" strings (static).  Timing is on only when enabled.  (Measurement
+ * support; the paper has no counterpart.) */
 qpic_status qpic_profile(qpic_ctx *ctx, int32_t enable, int32_t reset);
 qpic_status qpic_kernel_times(qpic_ctx *ctx, int32_t n, double *ms, int64_t *launches,
                               const char **names, int32_t *n_classes);
 
-/* Batches: many independent runs (for example a parameter scan) advanced by
- * one CUDA graph launch per cycle.  qpic_batch_create captures one cycle of
+/* Batches (a systems feature; the paper has no counterpart): many independent
+ * runs (for example a parameter scan) advanced by one CUDA graph launch per cycle.  qpic_batch_create captures one cycle of
  * 2 x `sort_period` full steps of every run (a sort swaps the particle
  * buffers, so a cycle holds two sorts and every replay starts from the
  * buffers the graph was recorded with) -- each run on its own stream, forked
