@@ -187,6 +187,14 @@ qpic_status qpic_get_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t m
 qpic_status qpic_set_field(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t mode,
                            const double *re, const double *im);
 
+/* The same with the caller's buffer length: count is the number of doubles
+ * each of re and im holds; QPIC_EINVAL (nothing copied) if count is below
+ * (nr+1)*nz.  im may be NULL (mode 0, or the imaginary part not wanted/0). */
+qpic_status qpic_get_fields(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t mode, double *re,
+                            double *im, int64_t count);
+qpic_status qpic_set_fields(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t mode,
+                            const double *re, const double *im, int64_t count);
+
 /* Charge density per mode like qpic_get_field(ctx, QPIC_FIELD_RHO, ...), but
  * without allocating any device memory.  The paper has no counterpart: this
  * entry point serves callers that cannot allocate -- hosts that hand the

@@ -90,6 +90,8 @@ def _declare(L):
     L.qpic_run_stages.argtypes = [_P, _I]
     L.qpic_get_field.argtypes = [_P, _I, _I, _I, _D, _D]
     L.qpic_set_field.argtypes = [_P, _I, _I, _I, _D, _D]
+    L.qpic_get_fields.argtypes = [_P, _I, _I, _I, _D, _D, ctypes.c_int64]
+    L.qpic_set_fields.argtypes = [_P, _I, _I, _I, _D, _D, ctypes.c_int64]
     L.qpic_num_particles.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
     L.qpic_get_particles.argtypes = [_P, _D, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.qpic_get_particles_raw.argtypes = [_P, _D, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
@@ -122,7 +124,8 @@ def _declare(L):
                                     ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I)]
     for name in ("qpic_default_config", "qpic_init", "qpic_get_solver", "qpic_cfl_limit",
                  "qpic_load_plasma", "qpic_load_particles", "qpic_add_laser", "qpic_step",
-                 "qpic_run_stages", "qpic_get_field", "qpic_set_field", "qpic_num_particles",
+                 "qpic_run_stages", "qpic_get_field", "qpic_set_field", "qpic_get_fields",
+                 "qpic_set_fields", "qpic_num_particles",
                  "qpic_get_particles", "qpic_get_diag", "qpic_profile", "qpic_kernel_times",
                  "qpic_get_particles_raw", "qpic_fit_coefficients", "qpic_filter_taps",
                  "qpic_stability_limit"):
@@ -322,16 +325,16 @@ class Sim:
     def get_field(self, which, comp, mode):
         re = np.zeros((self.nr + 1, self.nz))
         im = np.zeros((self.nr + 1, self.nz))
-        self._check(self.L.qpic_get_field(self.h, FIELD[which], COMP[comp], mode, _dp(re), _dp(im)),
-                    "get_field")
+        self._check(self.L.qpic_get_fields(self.h, FIELD[which], COMP[comp], mode, _dp(re), _dp(im),
+                                           re.size), "get_fields")
         return re + 1j * im
 
     def set_field(self, which, comp, mode, val):
         val = np.asarray(val, dtype=np.complex128).reshape(self.nr + 1, self.nz)
         re = np.ascontiguousarray(val.real)
         im = np.ascontiguousarray(val.imag)
-        self._check(self.L.qpic_set_field(self.h, FIELD[which], COMP[comp], mode, _dp(re), _dp(im)),
-                    "set_field")
+        self._check(self.L.qpic_set_fields(self.h, FIELD[which], COMP[comp], mode, _dp(re), _dp(im),
+                                           re.size), "set_fields")
 
     def fields(self, which):
         return np.array([[self.get_field(which, c, m) for m in range(self.nm)]

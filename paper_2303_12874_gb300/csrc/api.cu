@@ -738,6 +738,24 @@ qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
     return cuda_check(c, "set_field");
 }
 
+qpic_status qpic_get_fields(qpic_ctx *c, int32_t which, int32_t comp, int32_t mode, double *re,
+                            double *im, int64_t count)
+{
+    if (!c) return QPIC_EINVAL;
+    if (count < (int64_t)(c->g.nr + 1) * c->g.nz)
+        return fail(c, QPIC_EINVAL, "get_fields: buffer shorter than (nr+1)*nz");
+    return qpic_get_field(c, which, comp, mode, re, im);
+}
+
+qpic_status qpic_set_fields(qpic_ctx *c, int32_t which, int32_t comp, int32_t mode, const double *re,
+                            const double *im, int64_t count)
+{
+    if (!c) return QPIC_EINVAL;
+    if (count < (int64_t)(c->g.nr + 1) * c->g.nz)
+        return fail(c, QPIC_EINVAL, "set_fields: buffer shorter than (nr+1)*nz");
+    return qpic_set_field(c, which, comp, mode, re, im);
+}
+
 qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
 {
     if (!c || !n) return QPIC_EINVAL;

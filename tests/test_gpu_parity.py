@@ -193,3 +193,21 @@ def test_particle_stage_tiled(n_modes, tile):
     pr = o.particles()
     ke_o = float(np.sum(pr["w"] * (np.sqrt(1 + pr["ux"] ** 2 + pr["uy"] ** 2 + pr["uz"] ** 2) - 1)))
     assert abs(ke_g / ke_o - 1) < 1e-5
+
+
+def test_field_copies_check_the_buffer_length():
+    """qpic_get_fields / qpic_set_fields refuse buffers shorter than (nr+1)*nz
+    and copy nothing; the full length works"""
+    import ctypes
+    sim, _o = make_pair(40, 9, DZ, DR, 0.13)
+    D = ctypes.POINTER(ctypes.c_double)
+    n = (sim.nr + 1) * sim.nz
+    re = np.full(n, 7.0)
+    im = np.zeros(n)
+    assert sim.L.qpic_get_fields(sim.h, 0, 2, 0, re.ctypes.data_as(D), im.ctypes.data_as(D), n - 1) == -1
+    assert np.all(re == 7.0)
+    assert sim.L.qpic_set_fields(sim.h, 0, 2, 0, re.ctypes.data_as(D), im.ctypes.data_as(D), n - 1) == -1
+    assert sim.L.qpic_set_fields(sim.h, 0, 2, 0, re.ctypes.data_as(D), im.ctypes.data_as(D), n) == 0
+    back = np.zeros(n)
+    assert sim.L.qpic_get_fields(sim.h, 0, 2, 0, back.ctypes.data_as(D), None, n) == 0
+    assert np.array_equal(back, re)
