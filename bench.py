@@ -221,6 +221,21 @@ def oracle_sample(w, dt, nz_sample, steps):
     return n * steps / t, n, t
 
 
+def _host_cpu():
+    """CPU model and core count of this host (for the CPU baseline's record)"""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "Model Name", "CPU part") and v.strip():
+                model = v.strip()
+                break
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "cpus": os.cpu_count()}
+
+
 def _config(args, w, ws):
     """the workload keys both arms report"""
     return {"workload": args.workload, "nz": w["nz"], "nr": w["nr"], "modes": w["n_modes"],
@@ -390,6 +405,7 @@ def run_ours(args, w):
         sfa.profile(False, False)
         gfa = kfa["gather_push_deposit"]
         fatomic = {"value": nfa * args.fatomic_steps / (msfa / 1e3), "unit": "particle-steps/s",
+                   "cell_updates_per_s": w["nz"] * w["nr"] * args.fatomic_steps / (msfa / 1e3),
                    "ms_per_step": msfa / args.fatomic_steps, "steps": args.fatomic_steps,
                    "gpd_ms": gfa[0] / max(gfa[1], 1), "dtype": "f32",
                    "note": "same kernels, current summed by FP32 float atomics in global memory"}
@@ -412,6 +428,7 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1)
         fp64 = {"value": n64 * args.fp64_steps / (ms64 / 1e3), "unit": "particle-steps/s",
+                "cell_updates_per_s": w["nz"] * w["nr"] * args.fp64_steps / (ms64 / 1e3),
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                 "dtype": "f64", "note": "one thread per particle, FP64 atomics, no tiles or sort"}
         s64.close()
@@ -427,7 +444,8 @@ def run_ours(args, w):
         rate, n, t = oracle_sample(w, dt_used, args.ref_nz, args.cpu_steps)
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                "sample": "%d steps of a %d x %d periodic z-slab of the workload (%d particles), "
-                         "single-threaded FP64 C, %.1f s" % (args.cpu_steps, args.ref_nz, w["nr"], n, t)}
+                         "single-threaded FP64 C, %.1f s" % (args.cpu_steps, args.ref_nz, w["nr"], n, t),
+               "host": _host_cpu()}
 
     if rank == 0:
         line = {
