@@ -221,6 +221,11 @@ def oracle_sample(w, dt, nz_sample, steps):
     return n * steps / t, n, t
 
 
+# Arm (implementer 0x41) part numbers that /proc/cpuinfo gives in place of a model name
+_ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+              "0xd49": "Arm Neoverse N2", "0xd84": "Arm Neoverse V3"}
+
+
 def _host_cpu():
     """CPU model and core count of this host (for the CPU baseline's record)"""
     model = None
@@ -229,6 +234,8 @@ def _host_cpu():
             k, _, v = line.partition(":")
             if k.strip() in ("model name", "Model Name", "CPU part") and v.strip():
                 model = v.strip()
+                if k.strip() == "CPU part":
+                    model = _ARM_PARTS.get(model.lower(), "Arm part " + model)
                 break
     except OSError:
         pass
