@@ -16,7 +16,6 @@
 namespace qpic {
 
 static const int FTILE = 128;     // z columns per solver block
-static const int JTILE = 256;     // z columns per filter block
 
 // Coefficients live in a per-context device array [cE (MAX_L) | cB (MAX_L) |
 // taps (MAX_TAPS)] (FP32 copies of the FP64 host values); blocks stage what
@@ -83,24 +82,54 @@ __device__ __forceinline__ bool in_gap(int col, const GridArgs &a)
 __host__ __device__ __forceinline__ int part_mode(int p) { return (p + 1) >> 1; }
 __host__ __device__ __forceinline__ constexpr int imin_f(int x, int y) { return x < y ? x : y; }
 
+// The two staged components of a solver row are interleaved per column, so one
+// stencil tap reads both with one shared load; zstep adds c (hi - lo) to both
+// sums (for FP32 as paired operations, same rounding as two scalar FMAs).
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using t = float2; };
+template <> struct Pair2<double> { using t = double2; };
+
+__device__ __forceinline__ void zstep(float2 &acc, float c, float2 hi, float2 lo)
+{
+    acc = __ffma2_rn(make_float2(c, c), __fadd2_rn(hi, make_float2(-lo.x, -lo.y)), acc);
+}
+__device__ __forceinline__ void zstep(double2 &acc, double c, double2 hi, double2 lo)
+{
+    acc.x = fma(c, hi.x - lo.x, acc.x);
+    acc.y = fma(c, hi.y - lo.y, acc.y);
+}
+
+// sum_{l=1..L} C_l (f[l] - f[1 - l]) for both components of the pairs at f;
+// LT > 0 fixes L at compile time (the stencil unrolls), LT = 0 reads it from L
+template <int LT, typename T, typename V>
+__device__ __forceinline__ V zdiff(const V *f, const T *C, int L)
+{
+    V acc;
+    acc.x = 0; acc.y = 0;
+    const int n = LT > 0 ? LT : L;
+#pragma unroll
+    for (int l = 1; l <= n; l++) zstep(acc, C[l - 1], f[l], f[1 - l]);
+    return acc;
+}
+
 // ---------------------------------------------------------------- Faraday
 // dB/dt = -curl E:  B_r: -(i m/r) E_z + D^E_z E_phi;  B_phi: -D^E_z E_r + d_r E_z;
 // B_z: -(1/r) d_r(r E_phi) + (i m/r) E_r.  Writes B^{n+1/2} and Bbar^n.  One
 // block per row segment; E_phi and E_r of the row are staged with the stencil
 // halo.  Each thread loads its other operands (B, E_z, row j+1) before the
 // staging barrier, so both loads overlap.  P: parts (2M+1), compile time.
-template <typename T, int P>
-__global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *__restrict__ B,
+template <typename T, int P, int LT>
+__global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_faraday(const T *__restrict__ E, T *__restrict__ B,
                                                   T *__restrict__ Bb, GridArgs a)
 {
+    using V = typename Pair2<T>::t;
     extern __shared__ __align__(16) unsigned char shraw[];
     T *sh = reinterpret_cast<T *>(shraw);
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * FTILE;
     const int W = FTILE + 2 * a.L;
-    T *sC = sh;                      // [L] C^E
-    T *sEphi = sh + MAX_L;           // [P][W]
-    T *sEr = sEphi + P * W;          // [P][W]
+    T *sC = sh;                                    // [L] C^E
+    V *sE2 = reinterpret_cast<V *>(sh + MAX_L);    // [P][W] (E_phi, E_r)
     const int i = i0 + threadIdx.x;
     const bool live = i < a.nzp;
     const bool up = j < a.nr;        // row j + 1 exists
@@ -122,8 +151,10 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *_
         const int col = wide ? wrap1(i0 - a.L + k, a.nzp) : wrapz(i0 - a.L + k, a.nzp);
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            sEphi[p * W + k] = E[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
-            sEr[p * W + k] = E[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            V v;
+            v.x = E[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            v.y = E[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            sE2[p * W + k] = v;
         }
     }
     __syncthreads();
@@ -137,14 +168,9 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *_
         const int m = part_mode(p);
         const bool isim = (p > 0) && !(p & 1);
         const int pr = isim ? p - 1 : p, pim = isim ? p : imin_f(p + 1, P - 1);   // re / im partner
-        // D^E_z of E_phi and E_r at i + 1/2
-        T dEphi = 0, dEr = 0;
-        for (int l = 1; l <= a.L; l++) {
-            const T cl = sC[l - 1];
-            dEphi += cl * (sEphi[p * W + s + l] - sEphi[p * W + s + 1 - l]);
-            dEr += cl * (sEr[p * W + s + l] - sEr[p * W + s + 1 - l]);
-        }
-        dEphi /= dz; dEr /= dz;
+        // D^E_z of E_phi and E_r at i + 1/2: sum_l C_l (f_{i+l} - f_{i+1-l})
+        const V dE = zdiff<LT>(sE2 + p * W + s, sC, a.L);
+        const T dEphi = dE.x / dz, dEr = dE.y / dz;
         // B_r at (i+1/2, j)
         T d;
         if (j == 0) {
@@ -166,8 +192,8 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *_
             T bn = gap ? (T)0 : bp[p] + dt * d;
             B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bp[p] + bn);
             // B_z at (i, j+1/2); E_phi(j) and E_r(j) from the staged row
-            const T imr = m > 0 ? (isim ? sEr[pr * W + s] : -sEr[pim * W + s]) * (T)m / rh : (T)0;
-            d = -(rj1 * ep1[p] - rj * sEphi[p * W + s]) / (rh * dr) + imr;
+            const T imr = m > 0 ? (isim ? sE2[pr * W + s].y : -sE2[pim * W + s].y) * (T)m / rh : (T)0;
+            d = -(rj1 * ep1[p] - rj * sE2[p * W + s].x) / (rh * dr) + imr;
             q = (size_t)(2 * P + p) * a.plane + base;
             bn = gap ? (T)0 : bz[p] + dt * d;
             B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bz[p] + bn);
@@ -179,10 +205,18 @@ __global__ void __launch_bounds__(FTILE) k_faraday(const T *__restrict__ E, T *_
     }
 }
 
+// the dual solver's 16 coefficients get an unrolled FP32 stencil; other L
+// (and the plain FP64 path) the generic loop
 template <typename T, int P>
 static void faraday_launch(const GridArgs &a, dim3 grid, size_t sm, cudaStream_t st, const T *E, T *B, T *Bb)
 {
-    k_faraday<T, P><<<grid, FTILE, sm, st>>>(E, B, Bb, a);
+    if constexpr (sizeof(T) == 4) {
+        if (a.L == 16) {
+            k_faraday<T, P, 16><<<grid, FTILE, sm, st>>>(E, B, Bb, a);
+            return;
+        }
+    }
+    k_faraday<T, P, 0><<<grid, FTILE, sm, st>>>(E, B, Bb, a);
 }
 
 template <typename T>
@@ -214,54 +248,78 @@ void launch_faraday(qpic_ctx *c)
 // ---------------------------------------------------------------- J_z filter
 // J_z <- K * J_z along z (symbol [k]_Yee/[k]_B): keeps Gauss's law in the dual
 // form when the deposit satisfies the two-point continuity equation.
-// Each thread filters JR consecutive columns, keeping the two sides of the
-// symmetric stencil in sliding register windows: two shared loads per tap for
-// all JR outputs.  A block covers JTILE * JR columns of one row and part.
-static const int JR4 = 4;
+// Each thread filters JF_R = 8 consecutive columns.  The taps beyond the centre
+// are taken 8 at a time: the 16 columns on each side that 8 outputs x 8 taps
+// touch are read into registers with aligned vector loads and the products are
+// added in tap order, right + left side first (the symmetric stencil).  The
+// halo is rounded up to whole blocks of 8 taps, with 0 for the taps past the
+// last.  A block covers JF_T * JF_R columns of one row and part.
+static const int JF_T = 128;     // threads per filter block
+static const int JF_R = 8;       // columns per thread, taps per block
+
+__device__ __forceinline__ void ld8(const float *p, float x[8])
+{
+    const float4 *v = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const float4 t = v[k];
+        x[4 * k] = t.x; x[4 * k + 1] = t.y; x[4 * k + 2] = t.z; x[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void ld8(const double *p, double x[8])
+{
+    const double2 *v = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double2 t = v[k];
+        x[2 * k] = t.x; x[2 * k + 1] = t.y;
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(JTILE) k_jfilter(const T *__restrict__ Jf, T *__restrict__ Jzf,
-                                                  GridArgs a, int nk)
+__global__ void __launch_bounds__(JF_T) k_jfilter(const T *__restrict__ Jf, T *__restrict__ Jzf,
+                                                 GridArgs a, int nk)
 {
     extern __shared__ __align__(16) unsigned char shraw2[];
     T *sh2 = reinterpret_cast<T *>(shraw2);
     const int j = blockIdx.y, p = blockIdx.z;
-    const int i0 = blockIdx.x * (JTILE * JR4);
-    const int H = nk - 1, W = JTILE * JR4 + 2 * H;
-    T *sT = sh2, *sh = sh2 + MAX_TAPS;
-    for (int k = threadIdx.x; k < nk; k += JTILE)
-        sT[k] = sizeof(T) == 8 ? (T)a.coef64[2 * MAX_L + k] : (T)a.coef[2 * MAX_L + k];
+    const int i0 = blockIdx.x * (JF_T * JF_R);
+    const int nb = (nk - 1 + JF_R - 1) / JF_R;          // blocks of 8 taps beyond the centre
+    const int H = nb * JF_R, W = JF_T * JF_R + 2 * H;
+    T *sT = sh2, *sh = sh2 + MAX_TAPS;                  // sT[k]: tap k + 1, 0 past the last
+    for (int k = threadIdx.x; k < H; k += JF_T)
+        sT[k] = k + 1 < nk ? (sizeof(T) == 8 ? (T)a.coef64[2 * MAX_L + k + 1] : (T)a.coef[2 * MAX_L + k + 1])
+                           : (T)0;
+    const T c0 = sizeof(T) == 8 ? (T)a.coef64[2 * MAX_L] : (T)a.coef[2 * MAX_L];
     const T *src = Jf + (size_t)(2 * a.nparts + p) * a.plane + (size_t)j * a.nzp;
     const bool wide = a.nzp >= W;
-    for (int k = threadIdx.x; k < W; k += JTILE)
+    for (int k = threadIdx.x; k < W; k += JF_T)
         sh[k] = src[wide ? wrap1(i0 - H + k, a.nzp) : wrapz(i0 - H + k, a.nzp)];
     __syncthreads();
-    const int ib = i0 + threadIdx.x * JR4;
+    const int ib = i0 + threadIdx.x * JF_R;
     if (ib >= a.nzp) return;
-    const int s = threadIdx.x * JR4 + H;              // smem index of column ib
-    T acc[JR4], R[JR4], L[JR4];
-    const T c0 = sT[0];
+    const int s = threadIdx.x * JF_R + H;               // smem index of column ib, a multiple of 8
+    T acc[JF_R];
+    {
+        T x[8];
+        ld8(sh + s, x);
 #pragma unroll
-    for (int r = 0; r < JR4; r++) {
-        acc[r] = c0 * sh[s + r];
-        R[r] = nk > 1 ? sh[s + r + 1] : (T)0;          // sh[s + r + q] at q = 1
-        L[r] = nk > 1 ? sh[s + r - 1] : (T)0;          // sh[s + r - q] at q = 1
+        for (int r = 0; r < JF_R; r++) acc[r] = c0 * x[r];
     }
-    for (int q = 1; q < nk; q++) {
-        const T cq = sT[q];
+    for (int b = 0; b < nb; b++) {
+        const int q0 = b * JF_R;                         // taps q0 + 1 .. q0 + 8
+        T X[16], Y[16], c[8];
+        ld8(sh + s + q0, X); ld8(sh + s + q0 + 8, X + 8);    // X[k]: column ib + q0 + k
+        ld8(sh + s - q0 - 8, Y); ld8(sh + s - q0, Y + 8);    // Y[k]: column ib - q0 - 8 + k
+        ld8(sT + q0, c);
 #pragma unroll
-        for (int r = 0; r < JR4; r++) acc[r] += cq * (R[r] + L[r]);
-        if (q + 1 == nk) break;                        // the windows' next values lie in the halo
-        const T rn = sh[s + JR4 + q], ln = sh[s - q - 1];
+        for (int t = 0; t < JF_R; t++)                   // tap q = q0 + 1 + t
 #pragma unroll
-        for (int r = 0; r < JR4 - 1; r++) R[r] = R[r + 1];
-        R[JR4 - 1] = rn;
-#pragma unroll
-        for (int r = JR4 - 1; r > 0; r--) L[r] = L[r - 1];
-        L[0] = ln;
+            for (int r = 0; r < JF_R; r++) acc[r] += c[t] * (X[r + t + 1] + Y[r - t + 7]);
     }
     T *dst = Jzf + (size_t)p * a.plane + (size_t)j * a.nzp;
 #pragma unroll
-    for (int r = 0; r < JR4; r++) {
+    for (int r = 0; r < JF_R; r++) {
         const int i = ib + r;
         if (i < a.nzp) dst[i] = in_gap(i, a) ? (T)0 : acc[r];
     }
@@ -271,15 +329,15 @@ void launch_jfilter(qpic_ctx *c)
 {
     GridArgs a = grid_args(c);
     int nk = (int)c->taps.size();
-    dim3 grid((a.nzp + JTILE * JR4 - 1) / (JTILE * JR4), a.nr + 1, a.nparts);
+    const int H = (nk - 1 + JF_R - 1) / JF_R * JF_R;
+    dim3 grid((a.nzp + JF_T * JF_R - 1) / (JF_T * JF_R), a.nr + 1, a.nparts);
     prof_begin(c);
     if (c->fp64) {
-        size_t sm = (size_t)(MAX_TAPS + JTILE * JR4 + 2 * (nk - 1)) * sizeof(double);
-        cudaFuncSetAttribute(k_jfilter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_jfilter<double><<<grid, JTILE, sm, c->stream>>>(c->J64, c->Jz64, a, nk);
+        size_t sm = (size_t)(MAX_TAPS + JF_T * JF_R + 2 * H) * sizeof(double);
+        k_jfilter<double><<<grid, JF_T, sm, c->stream>>>(c->J64, c->Jz64, a, nk);
     } else {
-        size_t sm = (size_t)(MAX_TAPS + JTILE * JR4 + 2 * (nk - 1)) * sizeof(float);
-        k_jfilter<float><<<grid, JTILE, sm, c->stream>>>(c->Jf, c->Jzf, a, nk);
+        size_t sm = (size_t)(MAX_TAPS + JF_T * JF_R + 2 * H) * sizeof(float);
+        k_jfilter<float><<<grid, JF_T, sm, c->stream>>>(c->Jf, c->Jzf, a, nk);
     }
     prof_end(c, KC_JFILTER);
 }
@@ -291,18 +349,19 @@ void launch_jfilter(qpic_ctx *c)
 // d_r B_z(0) = 2 B_z(dr/2)/dr; m >= 2: 0.  Wall: E_phi = E_z = 0.
 // B_phi and B_r of the row are staged with the stencil halo; each thread loads
 // its other operands (E, J, B_z, row j - 1) before the staging barrier.
-template <typename T, int P>
-__global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__restrict__ B,
+template <typename T, int P, int LT>
+__global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_ampere(T *__restrict__ E, const T *__restrict__ B,
                                                  const T *__restrict__ Jf,
                                                  const T *__restrict__ Jz, GridArgs a)
 {
+    using V = typename Pair2<T>::t;
     extern __shared__ __align__(16) unsigned char shraw[];
     T *sh = reinterpret_cast<T *>(shraw);
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * FTILE;
     const int W = FTILE + 2 * a.L;
-    T *sC = sh;                          // [L] C^B
-    T *sBphi = sh + MAX_L, *sBr = sBphi + P * W;
+    T *sC = sh;                                    // [L] C^B
+    V *sB2 = reinterpret_cast<V *>(sh + MAX_L);    // [P][W] (B_phi, B_r)
     const int i = i0 + threadIdx.x;
     const bool live = i < a.nzp;
     const bool down = j > 0;             // row j - 1 exists
@@ -327,8 +386,10 @@ __global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__
         const int col = wide ? wrap1(i0 - a.L + k, a.nzp) : wrapz(i0 - a.L + k, a.nzp);
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            sBphi[p * W + k] = B[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
-            sBr[p * W + k] = B[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            V v;
+            v.x = B[(size_t)(1 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            v.y = B[(size_t)(0 * P + p) * a.plane + (size_t)j * a.nzp + col];
+            sB2[p * W + k] = v;
         }
     }
     __syncthreads();
@@ -343,13 +404,8 @@ __global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__
         const bool isim = (p > 0) && !(p & 1);
         const int pr = isim ? p - 1 : p, pim = isim ? p : imin_f(p + 1, P - 1);
         // D^B_z of B_phi and B_r at integer i: sum_l C_l (f_{i+l-1/2} - f_{i-l+1/2})
-        T dBphi = 0, dBr = 0;
-        for (int l = 1; l <= a.L; l++) {
-            const T cl = sC[l - 1];
-            dBphi += cl * (sBphi[p * W + s + l - 1] - sBphi[p * W + s - l]);
-            dBr += cl * (sBr[p * W + s + l - 1] - sBr[p * W + s - l]);
-        }
-        dBphi /= dz; dBr /= dz;
+        const V dB = zdiff<LT>(sB2 + p * W + s - 1, sC, a.L);
+        const T dBphi = dB.x / dz, dBr = dB.y / dz;
         // E_r at (i, j+1/2)
         if (j < a.nr) {
             const T imr = m > 0 ? (isim ? bz[pr] : -bz[pim]) * (T)m / rh : (T)0;
@@ -366,14 +422,14 @@ __global__ void __launch_bounds__(FTILE) k_ampere(T *__restrict__ E, const T *__
         }
         // E_z at (i+1/2, j); B_phi(j) and B_r(j) from the staged row
         {
-            const T bp0 = sBphi[p * W + s];
+            const T bp0 = sB2[p * W + s].x;
             T v;
             if (j == a.nr || (j == 0 && m != 0)) {
                 v = 0;
             } else if (j == 0) {
                 v = ez[p] + dt * ((T)4 * bp0 / dr - jz[p]);
             } else {
-                const T imr = m > 0 ? (isim ? sBr[pr * W + s] : -sBr[pim * W + s]) * (T)m / rj : (T)0;
+                const T imr = m > 0 ? (isim ? sB2[pr * W + s].y : -sB2[pim * W + s].y) * (T)m / rj : (T)0;
                 const T d = (rh * bp0 - rl * bpm[p]) / (rj * dr) - imr - jz[p];
                 v = ez[p] + dt * d;
             }
@@ -386,7 +442,13 @@ template <typename T, int P>
 static void ampere_launch(const GridArgs &a, dim3 grid, size_t sm, cudaStream_t st, T *E, const T *B,
                           const T *J, const T *Jz)
 {
-    k_ampere<T, P><<<grid, FTILE, sm, st>>>(E, B, J, Jz, a);
+    if constexpr (sizeof(T) == 4) {
+        if (a.L == 16) {
+            k_ampere<T, P, 16><<<grid, FTILE, sm, st>>>(E, B, J, Jz, a);
+            return;
+        }
+    }
+    k_ampere<T, P, 0><<<grid, FTILE, sm, st>>>(E, B, J, Jz, a);
 }
 
 template <typename T>
