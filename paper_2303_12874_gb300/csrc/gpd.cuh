@@ -966,26 +966,34 @@ __global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(c
     const int i = tz0 + c;
     const int epoch = *d_epoch;
     const bool dirty = jdirty[t] == epoch;
-    // candidate blocks: geometry first; their words are loaded together with
-    // the stamps that say whether they were written this step (no wait between)
+    // candidate blocks: geometry first, per z neighbour and per r neighbour
+    // (3 + 3), then combined; their words are loaded together with the stamps
+    // that say whether they were written this step (no wait between)
+    long long zpart[3], rpart[3];
+    int ztile[3], ljb[3];
+    bool zok[3], rok[3];
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        int kz = tzi + e - 1;
+        kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
+        const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
+        ztile[e] = kz * a.ntr;
+        zpart[e] = (long long)ztile[e] * tile_words + li;
+        zok[e] = tiles_ok && li < JW;
+        const int kr = tri + e - 1;
+        ljb[e] = tr0 - (kr * TR - H - 1);
+        rpart[e] = (long long)kr * tile_words + (long long)(comp * NP) * (JR * JW);
+        rok[e] = kr >= 0 && kr < a.ntr;
+    }
     long long kbase[9];
-    int ljb[9], kt[9];
-    bool geo[9];
+    bool geo[9], ok[9];
 #pragma unroll
     for (int d = 0; d < 9; d++) {
-        const int dz = d / 3 - 1, dr = d % 3 - 1;
-        int kz = tzi + dz;
-        kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
-        const int kr = tri + dr;
-        const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
-        kt[d] = kz * a.ntr + kr;
-        ljb[d] = tr0 - (kr * TR - H - 1);
-        kbase[d] = (long long)kt[d] * tile_words + (long long)(comp * NP) * (JR * JW) + li;
-        geo[d] = tiles_ok && kr >= 0 && kr < a.ntr && li < JW;
+        const int ez = d / 3, er = d % 3;
+        kbase[d] = zpart[ez] + rpart[er];
+        geo[d] = zok[ez] && rok[er];
+        ok[d] = geo[d] && tstamp[ztile[ez] + tri + er - 1] == epoch;
     }
-    bool ok[9];
-#pragma unroll
-    for (int d = 0; d < 9; d++) ok[d] = geo[d] && tstamp[kt[d]] == epoch;
     int l = i - (int)a.zoff;
     l = l < 0 ? l + a.nzp : l;
     const bool gap = l >= a.nz;
@@ -1005,7 +1013,7 @@ __global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(c
         }
 #pragma unroll
         for (int d = 0; d < 9; d++) {
-            const int lj = ljb[d] + r;
+            const int lj = ljb[d % 3] + r;
             if (geo[d] && lj >= 0 && lj < JR) {
                 const unsigned long long *src = Jtile + kbase[d] + lj * JW;
                 unsigned long long w[NP];
