@@ -38,8 +38,8 @@ struct GridArgs {
     int nz, nr, nzp, nparts, L;
     long long zoff;
     size_t plane;
-    float dz, dr, dt;
-    double dz64, dr64, dt64;
+    float dz, dr, dt, idz, idr;
+    double dz64, dr64, dt64, idz64, idr64;
     const float *coef;     // [cE | cB | taps] FP32
     const double *coef64;  // the same in FP64 (plain FP64 path)
 };
@@ -51,6 +51,8 @@ static GridArgs grid_args(const qpic_ctx *c)
     a.zoff = c->g.zoff % c->g.nzp; a.plane = c->g.plane;
     a.dz = (float)c->dz; a.dr = (float)c->dr; a.dt = (float)c->dt;
     a.dz64 = c->dz; a.dr64 = c->dr; a.dt64 = c->dt;
+    a.idz64 = 1.0 / c->dz; a.idr64 = 1.0 / c->dr;
+    a.idz = (float)a.idz64; a.idr = (float)a.idr64;
     a.coef = c->coef;
     a.coef64 = c->coef64;
     return a;
@@ -67,6 +69,15 @@ __device__ __forceinline__ int wrapz(int i, int nzp)
 __device__ __forceinline__ int wrap1(int i, int nzp)
 {
     return i < 0 ? i + nzp : (i >= nzp ? i - nzp : i);
+}
+
+// a grid parameter in the kernel's precision (the FP32 kernels take the FP32
+// copies: no conversions from FP64 on the device)
+template <typename T>
+__device__ __forceinline__ T gparam(float f, double d)
+{
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
 }
 
 // true when the physical column lies in the gap of an open box
@@ -160,8 +171,11 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
     __syncthreads();
     if (!live) return;
     const bool gap = in_gap(i, a);
-    const T dr = (T)a.dr64, dz = (T)a.dz64, dt = (T)a.dt64;
+    const T dr = gparam<T>(a.dr, a.dr64), dt = gparam<T>(a.dt, a.dt64);
+    const T idz = gparam<T>(a.idz, a.idz64), idr = gparam<T>(a.idr, a.idr64);
     const T rj = j * dr, rh = (j + (T)0.5) * dr, rj1 = (j + 1) * dr;
+    // the row's reciprocals, once per thread (divisions are long sequences)
+    const T irh = (T)1 / rh, irj = j > 0 ? (T)1 / rj : (T)0, irhdr = irh * idr;
     const int s = threadIdx.x + a.L;   // smem index of column i
 #pragma unroll
     for (int p = 0; p < P; p++) {
@@ -170,14 +184,14 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
         const int pr = isim ? p - 1 : p, pim = isim ? p : imin_f(p + 1, P - 1);   // re / im partner
         // D^E_z of E_phi and E_r at i + 1/2: sum_l C_l (f_{i+l} - f_{i+1-l})
         const V dE = zdiff<LT>(sE2 + p * W + s, sC, a.L);
-        const T dEphi = dE.x / dz, dEr = dE.y / dz;
+        const T dEphi = dE.x * idz, dEr = dE.y * idz;
         // B_r at (i+1/2, j)
         T d;
         if (j == 0) {
             // m = 1: -(i/r) E_z -> -i E_z^1(dr)/dr on the axis; m != 1: 0
-            d = m == 1 ? (isim ? -ez1[pr] : ez1[pim]) / dr + dEphi : (T)0;
+            d = m == 1 ? (isim ? -ez1[pr] : ez1[pim]) * idr + dEphi : (T)0;
         } else {
-            const T imr = m > 0 ? (isim ? ez[pr] : -ez[pim]) * (T)m / rj : (T)0;   // (i m / r) E_z
+            const T imr = m > 0 ? (isim ? ez[pr] : -ez[pim]) * ((T)m * irj) : (T)0;   // (i m / r) E_z
             d = -imr + dEphi;
         }
         {
@@ -187,13 +201,13 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
         }
         if (up) {
             // B_phi at (i+1/2, j+1/2)
-            d = -dEr + (ez1[p] - ez[p]) / dr;
+            d = -dEr + (ez1[p] - ez[p]) * idr;
             size_t q = (size_t)(1 * P + p) * a.plane + base;
             T bn = gap ? (T)0 : bp[p] + dt * d;
             B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bp[p] + bn);
             // B_z at (i, j+1/2); E_phi(j) and E_r(j) from the staged row
-            const T imr = m > 0 ? (isim ? sE2[pr * W + s].y : -sE2[pim * W + s].y) * (T)m / rh : (T)0;
-            d = -(rj1 * ep1[p] - rj * sE2[p * W + s].x) / (rh * dr) + imr;
+            const T imr = m > 0 ? (isim ? sE2[pr * W + s].y : -sE2[pim * W + s].y) * ((T)m * irh) : (T)0;
+            d = -(rj1 * ep1[p] - rj * sE2[p * W + s].x) * irhdr + imr;
             q = (size_t)(2 * P + p) * a.plane + base;
             bn = gap ? (T)0 : bz[p] + dt * d;
             B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bz[p] + bn);
@@ -395,8 +409,10 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
     __syncthreads();
     if (!live) return;
     const bool gap = in_gap(i, a);
-    const T dr = (T)a.dr64, dz = (T)a.dz64, dt = (T)a.dt64;
+    const T dr = gparam<T>(a.dr, a.dr64), dt = gparam<T>(a.dt, a.dt64);
+    const T idz = gparam<T>(a.idz, a.idz64), idr = gparam<T>(a.idr, a.idr64);
     const T rj = j * dr, rh = (j + (T)0.5) * dr, rl = (j - (T)0.5) * dr;
+    const T irh = (T)1 / rh, irj = j > 0 ? (T)1 / rj : (T)0, irjdr = irj * idr;
     const int s = threadIdx.x + a.L;
 #pragma unroll
     for (int p = 0; p < P; p++) {
@@ -405,10 +421,10 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
         const int pr = isim ? p - 1 : p, pim = isim ? p : imin_f(p + 1, P - 1);
         // D^B_z of B_phi and B_r at integer i: sum_l C_l (f_{i+l-1/2} - f_{i-l+1/2})
         const V dB = zdiff<LT>(sB2 + p * W + s - 1, sC, a.L);
-        const T dBphi = dB.x / dz, dBr = dB.y / dz;
+        const T dBphi = dB.x * idz, dBr = dB.y * idz;
         // E_r at (i, j+1/2)
         if (j < a.nr) {
-            const T imr = m > 0 ? (isim ? bz[pr] : -bz[pim]) * (T)m / rh : (T)0;
+            const T imr = m > 0 ? (isim ? bz[pr] : -bz[pim]) * ((T)m * irh) : (T)0;
             const T d = imr - dBphi - jr[p];
             E[(size_t)(0 * P + p) * a.plane + base] = gap ? (T)0 : er[p] + dt * d;
         }
@@ -416,8 +432,8 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
         {
             T v;
             if (j == a.nr || (j == 0 && m != 1)) v = 0;
-            else if (j == 0) v = ep[p] + dt * (dBr - (T)2 * bz[p] / dr - jp[p]);
-            else v = ep[p] + dt * (dBr - (bz[p] - bzm[p]) / dr - jp[p]);
+            else if (j == 0) v = ep[p] + dt * (dBr - (T)2 * bz[p] * idr - jp[p]);
+            else v = ep[p] + dt * (dBr - (bz[p] - bzm[p]) * idr - jp[p]);
             E[(size_t)(1 * P + p) * a.plane + base] = gap ? (T)0 : v;
         }
         // E_z at (i+1/2, j); B_phi(j) and B_r(j) from the staged row
@@ -427,10 +443,10 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
             if (j == a.nr || (j == 0 && m != 0)) {
                 v = 0;
             } else if (j == 0) {
-                v = ez[p] + dt * ((T)4 * bp0 / dr - jz[p]);
+                v = ez[p] + dt * ((T)4 * bp0 * idr - jz[p]);
             } else {
-                const T imr = m > 0 ? (isim ? sB2[pr * W + s].y : -sB2[pim * W + s].y) * (T)m / rj : (T)0;
-                const T d = (rh * bp0 - rl * bpm[p]) / (rj * dr) - imr - jz[p];
+                const T imr = m > 0 ? (isim ? sB2[pr * W + s].y : -sB2[pim * W + s].y) * ((T)m * irj) : (T)0;
+                const T d = (rh * bp0 - rl * bpm[p]) * irjdr - imr - jz[p];
                 v = ez[p] + dt * d;
             }
             E[(size_t)(2 * P + p) * a.plane + base] = gap ? (T)0 : v;
