@@ -330,9 +330,17 @@ class Sim:
         return re + 1j * im
 
     def set_field(self, which, comp, mode, val):
-        val = np.asarray(val, dtype=np.complex128).reshape(self.nr + 1, self.nz)
-        re = np.ascontiguousarray(val.real)
-        im = np.ascontiguousarray(val.imag)
+        """val: a complex (nr+1, nz) array, or a (re, im) pair of float64 arrays
+        of that size (passed as they are when C-contiguous: pinned host
+        buffers are then copied without staging)."""
+        if isinstance(val, tuple):
+            re, im = (np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in val)
+        else:
+            val = np.asarray(val, dtype=np.complex128).reshape(self.nr + 1, self.nz)
+            re = np.ascontiguousarray(val.real)
+            im = np.ascontiguousarray(val.imag)
+        if re.size != (self.nr + 1) * self.nz or im.size != re.size:
+            raise ValueError("set_field: %d values, the grid has %d" % (re.size, (self.nr + 1) * self.nz))
         self._check(self.L.qpic_set_fields(self.h, FIELD[which], COMP[comp], mode, _dp(re), _dp(im),
                                            re.size), "set_fields")
 

@@ -321,6 +321,7 @@ void qpic_destroy(qpic_ctx *ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->h_diag) cudaFreeHost(ctx->h_diag);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     std::vector<void *> all = ctx->allocs;
     for (void *p : all) dfree(ctx, p);
@@ -824,16 +825,24 @@ qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)
     v[0] = c->nstep * c->dt;
     v[1] = (double)c->nstep;
     v[2] = (double)c->shifts;
-    double s3[3];
-    if (c->fp64) fp64_particle_sums(c, s3);
-    else launch_particle_sums(c, s3);
-    v[3] = s3[0]; v[4] = s3[1]; v[5] = s3[2];
-    std::vector<double> fe(nm);
-    launch_field_energy(c, fe.data());
-    for (int m = 0; m < nm; m++) v[6 + m] = fe[m];
-    int e = 0;
-    cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    v[6 + nm] = (e & 1) ? 1.0 : 0.0;
+    // all reductions and the error word are copied into pinned host words and
+    // read after one synchronisation (pageable words when pinning failed)
+    if (!c->h_diag && cudaMallocHost(&c->h_diag, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_diag = nullptr;
+    }
+    double hv[64];
+    double *hb = c->h_diag ? c->h_diag : hv;
+    int *he = reinterpret_cast<int *>(hb + 32);
+    for (int m = 0; m < nm; m++) hb[3 + m] = 0.0;       // (no copy when the reduction buffer is short)
+    if (c->fp64) fp64_particle_sums(c, hb);
+    else launch_particle_sums(c, hb);
+    launch_field_energy(c, hb + 3);
+    cudaMemcpyAsync(he, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    v[3] = hb[0]; v[4] = hb[1]; v[5] = hb[2];
+    for (int m = 0; m < nm; m++) v[6 + m] = hb[3 + m];
+    v[6 + nm] = (*he & 1) ? 1.0 : 0.0;
     for (int k = 0; k < count && k < (int)v.size(); k++) out[k] = v[k];
     return cuda_check(c, "get_diag");
 }
@@ -878,6 +887,7 @@ qpic_status qpic_spectrum(qpic_ctx *c, const double *edges_mev, int32_t nbins, d
     if (c->fp64 || !(wref > 0)) {
         double s3[3];
         if (c->fp64) fp64_particle_sums(c, s3); else launch_particle_sums(c, s3);
+        cudaStreamSynchronize(c->stream);
         wref = s3[0] > 0 ? std::fabs(s3[1]) / s3[0] * 64.0 : 1.0;    // mean weight x 64
     }
     const double wscale = 4294967296.0 / wref;

@@ -709,9 +709,10 @@ void launch_field_energy(qpic_ctx *c, double *out_modes)
     else k_energy_partial<float><<<grid, 256, 0, c->stream>>>(c->E, c->B, a, c->d_red);
     k_sum_ordered<<<nm, 256, 0, c->stream>>>(c->d_red, nbx * (a.nr + 1), nm, c->d_red + need - nm);
     prof_end(c, KC_DIAG, 2);
+    // out_modes holds the energies once the stream has passed the copy (the
+    // caller synchronises)
     cudaMemcpyAsync(out_modes, c->d_red + need - nm, nm * sizeof(double), cudaMemcpyDeviceToHost,
                     c->stream);
-    cudaStreamSynchronize(c->stream);
 }
 
 }  // namespace qpic

@@ -667,8 +667,8 @@ void launch_particle_sums(qpic_ctx *c, double *out3)
     k_psums_partial<<<nb, 256, 0, c->stream>>>(c->p, dcount, part);
     k_psums_final<<<3, 256, 0, c->stream>>>(part, nb, part + 3 * nb);
     prof_end(c, KC_DIAG, 2);
+    // out3 holds the sums once the stream has passed the copy (the caller synchronises)
     cudaMemcpyAsync(out3, part + 3 * nb, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
 }
 
 }  // namespace qpic

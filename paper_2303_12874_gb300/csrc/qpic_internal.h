@@ -142,6 +142,7 @@ struct qpic_ctx {
 
     // device scratch
     int *d_err = nullptr;         // error word: bit 0 overflow, bit 1 capacity
+    double *h_diag = nullptr;     // pinned host words: diagnostics read back with one synchronisation
     double *rho_ion = nullptr;    // fixed ion background -rho_e at plasma load, [nm][2][nr+1][nz]
     double *d_red = nullptr;      // reduction scratch
     int red_cap = 0;

@@ -211,3 +211,19 @@ def test_field_copies_check_the_buffer_length():
     back = np.zeros(n)
     assert sim.L.qpic_get_fields(sim.h, 0, 2, 0, back.ctypes.data_as(D), None, n) == 0
     assert np.array_equal(back, re)
+
+
+def test_set_field_takes_re_im_pairs():
+    """set_field with a (re, im) pair of float64 arrays stores what the complex
+    form stores; a pair of the wrong size is refused"""
+    sim, _o = make_pair(40, 9, DZ, DR, 0.13)
+    rng = np.random.default_rng(3)
+    shape = (sim.nr + 1, sim.nz)
+    re, im = rng.standard_normal(shape), rng.standard_normal(shape)
+    sim.set_field("B", "phi", 1, (re, im))
+    got = sim.get_field("B", "phi", 1)
+    sim.set_field("B", "phi", 1, re + 1j * im)
+    assert np.array_equal(got, sim.get_field("B", "phi", 1))
+    assert np.array_equal(got.real, re.astype(np.float32).astype(np.float64))
+    with pytest.raises(ValueError):
+        sim.set_field("B", "phi", 1, (re[:-1], im[:-1]))
