@@ -231,7 +231,10 @@ qpic_status qpic_get_particles_raw(qpic_ctx *ctx, double *out, int64_t capacity,
  * [6..6+M] field energy per mode (1/2 sum V (|E|^2 + |B|^2), modes m >= 1 counted
  * twice by the Sec. III.B convention F_0 + 2 Re F_m e^{i m phi}), then the
  * fixed-point overflow flag.  Sums are FP64-grade (per-thread double-float
- * partial sums, FP64 block and grid sums in a fixed order). */
+ * partial sums, FP64 block and grid sums in a fixed order).  Synchronises the
+ * context's stream once; the first call allocates 512 bytes of pinned host
+ * memory for the read-back (freed by qpic_destroy; pageable words are used if
+ * pinning fails). */
 qpic_status qpic_get_diag(qpic_ctx *ctx, double *out, int32_t count);
 
 /* Gauss's law residual per mode in the dual form of Eq. 10: out[2m] = L2 norm
