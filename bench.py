@@ -428,6 +428,33 @@ def run_ours(args, w):
                    "note": "same kernels, current summed by FP32 float atomics in global memory"}
         sfa.close()
 
+    # ---- per-particle work in the directional split (Eq. 17) on the same workload
+    work = None
+    if not args.no_work:
+        sim.close()
+        swk = _make_sim(q, w, stream, track_work=2)
+        _init_state(swk, w)
+        swk.step(args.warmup)
+        nwk = swk.diag()["particles"]
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        swk.step(args.work_steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        mswk = g0.elapsed_time(g1)
+        swk.profile(True, True)
+        swk.step(2)
+        kwk = swk.kernel_times()
+        swk.profile(False, False)
+        gwk = kwk["gather_push_deposit"]
+        work = {"value": nwk * args.work_steps / (mswk / 1e3), "unit": "particle-steps/s",
+                "ms_per_step": mswk / args.work_steps, "steps": args.work_steps,
+                "gpd_ms": gwk[0] / max(gwk[1], 1), "dtype": "f32",
+                "note": "track_work = 2: W_z and W_perp per particle (Eq. 17), 8 B more read "
+                        "and written per particle-step"}
+        swk.close()
+
     # ---- the plain FP64 GPU path on the same workload and GPU
     fp64 = None
     if not args.no_fp64:
@@ -482,7 +509,7 @@ def run_ours(args, w):
                          "peak_source": peak_src + " (hbm_gbs, burst)",
                          "algorithmic_bytes_per_launch": gpd_bytes, "traffic": traffic},
             "fp64_gpu_path": fp64,
-            "fp32_float_atomic_path": fatomic,
+            "fp32_float_atomic_path": fatomic, "work_tracking_path": work,
             "batch_scan": batch,
             "fp32_over_fp64": (value / ws / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
@@ -505,6 +532,8 @@ def main():
                     help="steps of the end-to-end leg (0: the same as --steps)")
     ap.add_argument("--ref-nz", type=int, default=100)
     ap.add_argument("--no-fatomic", action="store_true")
+    ap.add_argument("--no-work", action="store_true")
+    ap.add_argument("--work-steps", type=int, default=20)
     ap.add_argument("--fatomic-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=24,
                     help="oracle steps timed for cpu_baseline (about 10 s on one core)")

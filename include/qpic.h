@@ -87,7 +87,9 @@ typedef struct {
     int32_t tile_z, tile_r;   /* particle tile in cells: 16x8 (default), 32x8, 8x8, 16x16, 32x4 */
     int32_t sort_period;      /* steps between particle sorts (0: default 2; a particle moves
                                  < 1 cell per step, so 2 keeps every one inside its tile halo) */
-    int32_t track_work;       /* 1: accumulate modal work W0, W1 per particle (Eq. 16) */
+    int32_t track_work;       /* per-particle work in W0, W1: 0 off; 1 modal (Eq. 16:
+                                 W0 from m = 0, W1 from m >= 1); 2 directional (Eq. 17:
+                                 W0 = W_z, W1 = W_perp, all modes) */
     uint64_t seed;            /* plasma azimuthal jitter seed */
     int64_t max_particles;    /* capacity (0: sized at the first load, +25%) */
     void *cuda_stream;        /* cudaStream_t to run on, NULL: the legacy default stream */
@@ -138,6 +140,20 @@ qpic_status qpic_filter_taps(const double *cB, int32_t L, double tol, double *ta
 qpic_status qpic_stability_limit(int32_t solver, double dz, double dr, int32_t nr,
                                  int32_t n_modes, int32_t n_coef, double fit_band,
                                  double *dt_max);
+
+/* Host-only, usable without a GPU: the LWFA / DLA split estimated from the
+ * directional work of Eq. 17 (a run with track_work = 2), Sec. III.B Eqs. 19-20.
+ * For each of n particles (momenta u = p/(m c), work W_z, W_perp in m c^2):
+ *   f = -2 sqrt(2 gamma) / (omega0 omega_p w0^2)   (Eq. 19, c = 1, gamma from u),
+ *   lwfa[k] = W_z - f W_perp,  dla[k] = (1 + f) W_perp   (Eq. 20).
+ * omega_p and omega0 in the units of 1/t (omega0 = 1 in the normalized units),
+ * w0 the laser spot size in units of length: the paper takes average values
+ * near the electron bunch.  All arrays are caller-owned host arrays of n
+ * doubles; lwfa and dla may not alias the inputs.  QPIC_EINVAL for n < 0, a
+ * missing array or a non-positive omega_p, omega0 or w0. */
+qpic_status qpic_work_f_estimate(int64_t n, const double *ux, const double *uy, const double *uz,
+                                 const double *Wz, const double *Wperp, double omega_p, double w0,
+                                 double omega0, double *lwfa, double *dla);
 
 /* Stability limit of the configured solver on this grid (leapfrog bound
  * (dt^2/4) lambda_max(curl curl) <= 1, coefficients refitted per trial dt). */

@@ -82,7 +82,9 @@ COMPS = {"r": 0, "phi": 1, "z": 2}
 
 
 class Oracle:
-    """One oracle simulation box.  Fields are per mode, complex, [nr+1][nz]."""
+    """One oracle simulation box.  Fields are per mode, complex, [nr+1][nz].
+    track_work: 0 off; 1 the modal work of Eq. 16 (W0 from m = 0, W1 from
+    m >= 1); 2 the directional work of Eq. 17 (W0 = W_z, W1 = W_perp)."""
 
     def __init__(self, nz, nr, n_modes, dz, dr, dt, cE, cB, ktaps=None,
                  periodic=True, track_work=False):

@@ -116,3 +116,21 @@ def spectrum(p, edges_mev):
     g = np.sqrt(1.0 + p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2)
     h, _ = np.histogram((g - 1.0) * MEC2_MEV, bins=edges_mev, weights=p["w"])
     return h
+
+
+def work_f_ratio(gamma, omega_p, w0, omega0=1.0):
+    """Eq. 19: ratio f of the cycle-averaged work of the laser's longitudinal
+    field to that of its transverse field, for an electron of Lorentz factor
+    gamma in betatron resonance near focus (c = 1): f = -2 sqrt(2 gamma) /
+    (omega0 omega_p w0^2)."""
+    return -2.0 * np.sqrt(2.0 * np.asarray(gamma, dtype=np.float64)) / (omega0 * omega_p * w0 * w0)
+
+
+def work_f_estimate(gamma, Wz, Wperp, omega_p, w0, omega0=1.0):
+    """Eq. 20: the LWFA / DLA split estimated from the directional work of
+    Eq. 17, W*_LWFA = W_z - f W_perp and W*_DLA = (1 + f) W_perp, with f of
+    Eq. 19 at each particle's gamma."""
+    f = work_f_ratio(gamma, omega_p, w0, omega0)
+    Wz = np.asarray(Wz, dtype=np.float64)
+    Wperp = np.asarray(Wperp, dtype=np.float64)
+    return Wz - f * Wperp, (1.0 + f) * Wperp

@@ -538,12 +538,19 @@ void or_push_deposit(ostate *s)
         double g = sqrt(1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
         double vx = up[0] / g, vy = up[1] / g, vz = up[2] / g;
         if (s->track_work) {
-            /* Eq. 16: W_m += q dt E^m . v, with v at time n the mean of u/gamma at n -+ 1/2 */
+            /* v at time n: the mean of u/gamma at n -+ 1/2 */
             double vn[3] = { 0.5 * (u[0] / g_old + vx), 0.5 * (u[1] / g_old + vy), 0.5 * (u[2] / g_old + vz) };
-            double w0 = e[3] * vn[0] + e[4] * vn[1] + e[5] * vn[2];
-            double wt = e[0] * vn[0] + e[1] * vn[1] + e[2] * vn[2];
-            s->W0[p] += q * dt * w0;
-            s->W1[p] += q * dt * (wt - w0);
+            if (s->track_work == 2) {
+                /* Eq. 17: W_z += q dt E_z v_z, W_perp += q dt E_perp . v_perp (all modes) */
+                s->W0[p] += q * dt * (e[2] * vn[2]);
+                s->W1[p] += q * dt * (e[0] * vn[0] + e[1] * vn[1]);
+            } else {
+                /* Eq. 16: W_m += q dt E^m . v; W0 holds m = 0, W1 the modes m >= 1 */
+                double w0 = e[3] * vn[0] + e[4] * vn[1] + e[5] * vn[2];
+                double wt = e[0] * vn[0] + e[1] * vn[1] + e[2] * vn[2];
+                s->W0[p] += q * dt * w0;
+                s->W1[p] += q * dt * (wt - w0);
+            }
         }
         double x1 = x0 + dt * vx, y1 = y0 + dt * vy, z1 = z0 + dt * vz;
         double r1 = hypot(x1, y1);

@@ -18,7 +18,7 @@ _lib = None
 
 # revision tag of the gather+push+deposit kernel; measured DRAM traffic stored
 # under profiles/ is only reported while it matches
-KERNEL_REV = "gpd-v9"
+KERNEL_REV = "gpd-v10"
 
 QPIC_YEE, QPIC_DUAL = 0, 1
 QPIC_FP64, QPIC_FP32_FIXED, QPIC_FP32_FATOMIC = 0, 1, 2
@@ -120,6 +120,8 @@ def _declare(L):
     L.qpic_spectrum.restype = ctypes.c_int
     L.qpic_charge_density_noalloc.restype = ctypes.c_int
     L.qpic_launch_count.restype = ctypes.c_int
+    L.qpic_work_f_estimate.argtypes = [ctypes.c_int64] + [_D] * 5 + [ctypes.c_double] * 3 + [_D, _D]
+    L.qpic_work_f_estimate.restype = ctypes.c_int
     L.qpic_kernel_times.argtypes = [_P, _I, _D, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I)]
     for name in ("qpic_default_config", "qpic_init", "qpic_get_solver", "qpic_cfl_limit",
@@ -168,6 +170,22 @@ def stability_limit(solver, dz, dr, nr, n_modes, n_coef=16, fit_band=0.8):
     if st != 0:
         raise QpicError("qpic_stability_limit: %s" % STATUS.get(st, st))
     return v.value
+
+
+def work_f_estimate(ux, uy, uz, Wz, Wperp, omega_p, w0, omega0=1.0):
+    """LWFA / DLA work estimated from the directional work of a run with
+    track_work=2 (W0 = W_z, W1 = W_perp), by the library's host function
+    qpic_work_f_estimate (Eqs. 19-20; no GPU needed).  Returns (lwfa, dla)."""
+    L = load()
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (ux, uy, uz, Wz, Wperp)]
+    n = len(a[0])
+    if any(len(x) != n for x in a):
+        raise ValueError("work_f_estimate: arrays of different lengths")
+    lwfa, dla = np.zeros(n), np.zeros(n)
+    st = L.qpic_work_f_estimate(n, *[_dp(x) for x in a], omega_p, w0, omega0, _dp(lwfa), _dp(dla))
+    if st != 0:
+        raise QpicError("qpic_work_f_estimate: %s" % STATUS.get(st, st))
+    return lwfa, dla
 
 
 class Batch:
@@ -245,6 +263,7 @@ class Sim:
         cfg.jz_filter, cfg.filter_tol = int(jz_filter), filter_tol
         cfg.periodic_z, cfg.moving_window, cfg.window_v = int(periodic), int(moving_window), window_v
         cfg.tile_z, cfg.tile_r, cfg.sort_period = tile_z, tile_r, sort_period
+        # track_work: False/0 off, True/1 modal work (Eq. 16), 2 directional work (Eq. 17)
         cfg.track_work, cfg.seed, cfg.max_particles = int(track_work), seed, max_particles
         if stream is not None:
             cfg.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream

@@ -344,6 +344,8 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     if (cfg->nz < 4 || cfg->nr < 2 || cfg->n_modes < 1 || cfg->n_modes > MAX_MODES)
         return bad(QPIC_EINVAL, "grid: need nz >= 4, nr >= 2, 1 <= n_modes <= 4");
     if (!(cfg->dz > 0) || !(cfg->dr > 0)) return bad(QPIC_EINVAL, "dz, dr must be positive");
+    if (cfg->track_work < 0 || cfg->track_work > 2)
+        return bad(QPIC_EINVAL, "track_work: 0, 1 (modal work, Eq. 16) or 2 (directional work, Eq. 17)");
     if (cfg->solver != QPIC_YEE && cfg->solver != QPIC_DUAL) return bad(QPIC_EINVAL, "solver");
     if (cfg->precision != QPIC_FP32_FIXED && cfg->precision != QPIC_FP64 &&
         cfg->precision != QPIC_FP32_FATOMIC)
@@ -815,6 +817,22 @@ qpic_status qpic_get_particles_raw(qpic_ctx *c, double *out, int64_t capacity, i
         dfree(c, d);
     }
     return cuda_check(c, "get_particles_raw");
+}
+
+qpic_status qpic_work_f_estimate(int64_t n, const double *ux, const double *uy, const double *uz,
+                                 const double *Wz, const double *Wperp, double omega_p, double w0,
+                                 double omega0, double *lwfa, double *dla)
+{
+    if (n < 0 || !(omega_p > 0) || !(w0 > 0) || !(omega0 > 0)) return QPIC_EINVAL;
+    if (n > 0 && (!ux || !uy || !uz || !Wz || !Wperp || !lwfa || !dla)) return QPIC_EINVAL;
+    const double k = -2.0 / (omega0 * omega_p * w0 * w0);
+    for (int64_t p = 0; p < n; p++) {
+        const double gamma = std::sqrt(1.0 + ux[p] * ux[p] + uy[p] * uy[p] + uz[p] * uz[p]);
+        const double f = k * std::sqrt(2.0 * gamma);          // Eq. 19
+        lwfa[p] = Wz[p] - f * Wperp[p];                        // Eq. 20
+        dla[p] = (1.0 + f) * Wperp[p];
+    }
+    return QPIC_OK;
 }
 
 qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)

@@ -369,14 +369,21 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
     const float ig = rsqrtf(1.f + unx * unx + uny * uny + unz * unz);
     const float vx = unx * ig, vy = uny * ig, vz = unz * ig;
     if (a.track_work) {
-        // Eq. 16: W_m += q dt E^m . v, v at time n the mean of u/gamma at n -+ 1/2
+        // v at time n: the mean of u/gamma at n -+ 1/2
         const float igo = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
         float wx = 0.5f * (ux * igo + vx), wy = 0.5f * (uy * igo + vy), wz = 0.5f * (uz * igo + vz);
-        float E0x = F[0][0][0] * cph - F[0][1][0] * sph, E0y = F[0][0][0] * sph + F[0][1][0] * cph;
-        float p0 = E0x * wx + E0y * wy + F[0][2][0] * wz;
-        float pt = Ex * wx + Ey * wy + Ez * wz;
-        s.W0 -= a.dt * p0;
-        s.W1 -= a.dt * (pt - p0);
+        if (a.track_work == 2) {
+            // Eq. 17: W_z += q dt E_z v_z, W_perp += q dt E_perp . v_perp (all modes)
+            s.W0 -= a.dt * (Ez * wz);
+            s.W1 -= a.dt * (Ex * wx + Ey * wy);
+        } else {
+            // Eq. 16: W_m += q dt E^m . v; W0 holds m = 0, W1 the modes m >= 1
+            float E0x = F[0][0][0] * cph - F[0][1][0] * sph, E0y = F[0][0][0] * sph + F[0][1][0] * cph;
+            float p0 = E0x * wx + E0y * wy + F[0][2][0] * wz;
+            float pt = Ex * wx + Ey * wy + Ez * wz;
+            s.W0 -= a.dt * p0;
+            s.W1 -= a.dt * (pt - p0);
+        }
     }
     // ---- move in Cartesian x, y; r and angle with cancellation-free differences
     const float ddz = a.dt * vz;

@@ -152,7 +152,14 @@ __global__ void k_push64(Particles64 P, long long np, const double *E, const dou
                         um[2] + upr[0] * sv[1] - upr[1] * sv[0] + h * e[2]};
         const double g = sqrt(1.0 + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
         const double vx = un[0] / g, vy = un[1] / g, vz = un[2] / g;
-        if (a.track_work) {
+        if (a.track_work == 2) {
+            // Eq. 17: W_z and W_perp, v at time n the mean of u/gamma at n -+ 1/2
+            const double wx = 0.5 * (u0x / gold + vx), wy = 0.5 * (u0y / gold + vy),
+                         wz = 0.5 * (u0z / gold + vz);
+            P.W0[i] -= a.dt * (e[2] * wz);
+            P.W1[i] -= a.dt * (e[0] * wx + e[1] * wy);
+        } else if (a.track_work) {
+            // Eq. 16: W0 from the m = 0 field, W1 from the modes m >= 1
             const double wx = 0.5 * (u0x / gold + vx), wy = 0.5 * (u0y / gold + vy),
                          wz = 0.5 * (u0z / gold + vz);
             const double e0x = F0[0] * c0 - F0[1] * s0, e0y = F0[0] * s0 + F0[1] * c0;

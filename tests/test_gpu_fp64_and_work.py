@@ -1,6 +1,7 @@
 """The plain FP64 GPU path against the oracle (same readings, double
-precision: agreement to ~1e-12 per step), and the modal work of Eq. 16
-(W_LWFA from the m = 0 field, W_DLA from m = 1) on both GPU paths."""
+precision: agreement to ~1e-12 per step), and the per-particle work on both
+GPU paths: the modal split of Eq. 16 (W_LWFA from the m = 0 field, W_DLA
+from m = 1) and the directional split of Eq. 17 (W_z, W_perp)."""
 import numpy as np
 import pytest
 
@@ -55,12 +56,15 @@ def test_fp64_path_particles_match_oracle():
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_modal_work_eq16(precision):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_work_eq16_eq17(precision, mode):
     """the oracle evolves a wake for 6 steps (laser a0 = 2); that state goes to
     the GPU (whose work counters start at 0) and both take one step: the GPU's
-    W0, W1 equal the oracle's increments.  The FP64 path keeps the particle
-    order and is compared particle by particle; the FP32 path sorts at load, so
-    it is compared through the sums and the z-moments of the increments."""
+    W0, W1 equal the oracle's increments, for the modal split of Eq. 16
+    (mode 1) and the directional split of Eq. 17 (mode 2).  The FP64 path
+    keeps the particle order and is compared particle by particle; the FP32
+    path sorts at load, so it is compared through the sums and the z-moments
+    of the increments."""
     import oracle
     w = synth.workload("cfg1_small")
     w = dict(w, laser=dict(w["laser"], a0=2.0))
@@ -68,11 +72,11 @@ def test_modal_work_eq16(precision):
     prec = q.QPIC_FP64 if precision == "fp64" else q.QPIC_FP32_FIXED
     cE, cB = C.dual_coefficients(dt, dz)
     o = oracle.Oracle(nz, nr, 2, dz, dr, dt, cE, cB, C.filter_taps(cB), periodic=True,
-                      track_work=True)
+                      track_work=mode)
     oracle_config1_state(o, w, dt)
     o.step(6)                            # let the plasma respond: an m = 0 wake field appears
     r0 = o.particles()
-    sim = q.Sim(nz, nr, dz, dr, dt=dt, precision=prec, track_work=True)
+    sim = q.Sim(nz, nr, dz, dr, dt=dt, precision=prec, track_work=mode)
     oracle_state_to_gpu(o, sim)
     sim.run_stages(1 | 2 | 4)            # one step without sort: buffer order kept
     o.step(1)
