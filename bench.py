@@ -135,6 +135,40 @@ def _init_state(sim, w):
     sim.add_laser(la["a0"], la["w0"], la["fwhm"], la["z_centroid"], la["z_focus"])
 
 
+def reduced_leg(q, torch, stream, args):
+    """The reduced model of Eq. 8 (FP64 Dormand-Prince, one thread per electron) on
+    a synthetic bunch; the oracle timed on a small sample unless --no-cpu."""
+    from oracle import reduced as R                 # the oracle: its CPU baseline only
+    nr_e, st_e = args.reduced_electrons, args.reduced_steps
+    rng = np.random.default_rng(8)
+    y0 = [rng.uniform(-3.0, 3.0, nr_e), rng.uniform(-40.0, -5.0, nr_e), rng.normal(0.0, 1.0, nr_e),
+          rng.uniform(0.0, 60.0, nr_e)]
+    par = (2.0, 1 / 12.0, 0.04, 1.0008)             # a0, omega_p, k_perp, v_phi (omega0 = 1)
+    dev = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in y0]
+    ptrs = [d.data_ptr() for d in dev]
+    sh = stream.cuda_stream
+    q.reduced_integrate_device(ptrs, nr_e, *par, 0.0, 0.05, 5, stream=sh)     # warm-up
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    q.reduced_integrate_device(ptrs, nr_e, *par, 0.25, 0.05, st_e, stream=sh)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    msr = g0.elapsed_time(g1)
+    ocpu = None
+    if not args.no_cpu:
+        ns = 1000
+        t0c = time.perf_counter()
+        R.integrate(*[v[:ns] for v in y0], *par, 0.0, 0.05, 50)
+        tc = time.perf_counter() - t0c
+        ocpu = {"value": ns * 50 / tc, "unit": "electron-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "1000 electrons x 50 steps, numpy FP64"}
+    return {"value": nr_e * st_e / (msr / 1e3), "unit": "electron-steps/s", "electrons": nr_e,
+            "steps": st_e, "ms": msr, "dtype": "f64", "cpu_baseline": ocpu,
+            "note": "Eq. 8 in a spherical bubble and a channel laser (a0 2, omega_p 1/12, "
+                    "k_perp 0.04, v_phi 1.0008), fifth-order Dormand-Prince at dt 0.05"}
+
+
 def batch_scan(q, torch, stream, nruns, steps, seed=5):
     """Parameter scan of independent periodic runs (grids 256-1024 x 32-128,
     n 0.003-0.02, a0 1-4, ppc 8/16/32; run k draws from a generator seeded
@@ -455,6 +489,14 @@ def run_ours(args, w):
                         "and written per particle-step"}
         swk.close()
 
+    # ---- the reduced model of Eq. 8 (FP64 Dormand-Prince, one thread per electron)
+    reduced = None
+    if not args.no_reduced:
+        try:
+            reduced = reduced_leg(q, torch, stream, args)
+        except Exception as e:                          # an auxiliary leg never voids the main line
+            reduced = {"error": "%s: %s" % (type(e).__name__, e)}
+
     # ---- the plain FP64 GPU path on the same workload and GPU
     fp64 = None
     if not args.no_fp64:
@@ -509,7 +551,7 @@ def run_ours(args, w):
                          "peak_source": peak_src + " (hbm_gbs, burst)",
                          "algorithmic_bytes_per_launch": gpd_bytes, "traffic": traffic},
             "fp64_gpu_path": fp64,
-            "fp32_float_atomic_path": fatomic, "work_tracking_path": work,
+            "fp32_float_atomic_path": fatomic, "work_tracking_path": work, "reduced_model_path": reduced,
             "batch_scan": batch,
             "fp32_over_fp64": (value / ws / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
@@ -533,6 +575,9 @@ def main():
     ap.add_argument("--ref-nz", type=int, default=100)
     ap.add_argument("--no-fatomic", action="store_true")
     ap.add_argument("--no-work", action="store_true")
+    ap.add_argument("--no-reduced", action="store_true")
+    ap.add_argument("--reduced-electrons", type=int, default=1 << 20)
+    ap.add_argument("--reduced-steps", type=int, default=200)
     ap.add_argument("--work-steps", type=int, default=20)
     ap.add_argument("--fatomic-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=24,

@@ -155,6 +155,32 @@ qpic_status qpic_work_f_estimate(int64_t n, const double *ux, const double *uy, 
                                  const double *Wz, const double *Wperp, double omega_p, double w0,
                                  double omega0, double *lwfa, double *dla);
 
+/* Reduced model of Sec. II (Eqs. 1-8), independent of any context: n electrons
+ * in a spherical bubble wake (Eq. 6) and a channel-guided laser (Eqs. 3-4),
+ * moving in the x-z plane, advanced by nsteps fixed steps of dt from time t0
+ * with the fifth-order Dormand-Prince Runge-Kutta method, in FP64 on the GPU
+ * (one thread per electron).  State per electron: x, zeta = z - t, u_x, u_z
+ * (u = gamma v), in/out.  Units c = 1, laser frequency omega0 = 1; omega_p
+ * the plasma frequency (the bubble's w_beta^2 = omega_p^2/(2 gamma), Eq. 1),
+ * k_perp the laser's transverse wavenumber (Eq. 3; the paper's choice is
+ * 2.4/(r_b + c/omega_p)), v_phi its phase velocity (k_z = omega0/v_phi), a0 its
+ * normalized amplitude.
+ *   qpic_reduced_integrate: caller-owned host arrays of n doubles; the call
+ *     copies them to the device and back and returns when done.
+ *   qpic_reduced_integrate_device: device arrays, launched on `stream`
+ *     (a cudaStream_t, NULL for the default stream); asynchronous.
+ * QPIC_EINVAL for n < 0, nsteps < 0, a missing array, dt <= 0, v_phi <= 0,
+ * k_perp < 0 or a non-finite parameter; QPIC_ENOMEM / QPIC_ECUDA when device
+ * memory or a CUDA call fails.  The paper has no such interface: it integrates
+ * Eq. 8 for single electrons. */
+qpic_status qpic_reduced_integrate(int64_t n, double *x, double *zeta, double *ux, double *uz,
+                                   double a0, double omega_p, double k_perp, double v_phi,
+                                   double t0, double dt, int32_t nsteps);
+qpic_status qpic_reduced_integrate_device(int64_t n, double *x, double *zeta, double *ux,
+                                          double *uz, double a0, double omega_p, double k_perp,
+                                          double v_phi, double t0, double dt, int32_t nsteps,
+                                          void *stream);
+
 /* Stability limit of the configured solver on this grid (leapfrog bound
  * (dt^2/4) lambda_max(curl curl) <= 1, coefficients refitted per trial dt). */
 qpic_status qpic_cfl_limit(const qpic_ctx *ctx, double *dt_max);

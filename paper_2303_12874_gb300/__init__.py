@@ -120,6 +120,11 @@ def _declare(L):
     L.qpic_spectrum.restype = ctypes.c_int
     L.qpic_charge_density_noalloc.restype = ctypes.c_int
     L.qpic_launch_count.restype = ctypes.c_int
+    L.qpic_reduced_integrate.argtypes = [ctypes.c_int64] + [_D] * 4 + [ctypes.c_double] * 6 + [_I]
+    L.qpic_reduced_integrate.restype = ctypes.c_int
+    L.qpic_reduced_integrate_device.argtypes = ([ctypes.c_int64] + [ctypes.c_void_p] * 4 +
+                                                [ctypes.c_double] * 6 + [_I, ctypes.c_void_p])
+    L.qpic_reduced_integrate_device.restype = ctypes.c_int
     L.qpic_work_f_estimate.argtypes = [ctypes.c_int64] + [_D] * 5 + [ctypes.c_double] * 3 + [_D, _D]
     L.qpic_work_f_estimate.restype = ctypes.c_int
     L.qpic_kernel_times.argtypes = [_P, _I, _D, ctypes.POINTER(ctypes.c_int64),
@@ -186,6 +191,30 @@ def work_f_estimate(ux, uy, uz, Wz, Wperp, omega_p, w0, omega0=1.0):
     if st != 0:
         raise QpicError("qpic_work_f_estimate: %s" % STATUS.get(st, st))
     return lwfa, dla
+
+
+def reduced_integrate(x, zeta, ux, uz, a0, omega_p, k_perp, v_phi, t0, dt, nsteps):
+    """The reduced model of Eq. 8 on the GPU (qpic_reduced_integrate): host
+    arrays in, new host arrays (x, zeta, u_x, u_z) out after nsteps steps."""
+    L = load()
+    a = [np.array(v, dtype=np.float64, copy=True).reshape(-1) for v in (x, zeta, ux, uz)]
+    n = len(a[0])
+    if any(len(v) != n for v in a):
+        raise ValueError("reduced_integrate: arrays of different lengths")
+    st = L.qpic_reduced_integrate(n, *[_dp(v) for v in a], a0, omega_p, k_perp, v_phi, t0, dt, int(nsteps))
+    if st != 0:
+        raise QpicError("qpic_reduced_integrate: %s" % STATUS.get(st, st))
+    return tuple(a)
+
+
+def reduced_integrate_device(ptrs, n, a0, omega_p, k_perp, v_phi, t0, dt, nsteps, stream=None):
+    """Device variant: ptrs = four device addresses of n doubles (x, zeta, u_x,
+    u_z), advanced in place on `stream` (an integer cudaStream_t or None)."""
+    L = load()
+    st = L.qpic_reduced_integrate_device(n, *[ctypes.c_void_p(int(p)) for p in ptrs], a0, omega_p, k_perp,
+                                         v_phi, t0, dt, int(nsteps), ctypes.c_void_p(stream or 0))
+    if st != 0:
+        raise QpicError("qpic_reduced_integrate_device: %s" % STATUS.get(st, st))
 
 
 class Batch:

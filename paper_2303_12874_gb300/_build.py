@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqpic.so")
-SOURCES = ["api.cu", "k_fields.cu", "k_particles.cu", "host_numerics.cpp", "noalloc.cu", "k_fp64.cu"]
+SOURCES = ["api.cu", "k_fields.cu", "k_particles.cu", "host_numerics.cpp", "noalloc.cu", "k_fp64.cu",
+           "k_reduced.cu"]
 # the particle kernel, one object per (mode parts, float-atomic deposit) so that
 # the instantiations compile in parallel: (object name, defines)
 GPD_OBJECTS = [("gpd_np%d_fa%d" % (np_, fa), ["-DGPD_NP=%d" % np_, "-DGPD_FA=%d" % fa])
