@@ -138,7 +138,6 @@ def _init_state(sim, w):
 def reduced_leg(q, torch, stream, args):
     """The reduced model of Eq. 8 (FP64 Dormand-Prince, one thread per electron) on
     a synthetic bunch; the oracle timed on a small sample unless --no-cpu."""
-    from oracle import reduced as R                 # the oracle: its CPU baseline only
     nr_e, st_e = args.reduced_electrons, args.reduced_steps
     rng = np.random.default_rng(8)
     y0 = [rng.uniform(-3.0, 3.0, nr_e), rng.uniform(-40.0, -5.0, nr_e), rng.normal(0.0, 1.0, nr_e),
@@ -157,6 +156,7 @@ def reduced_leg(q, torch, stream, args):
     msr = g0.elapsed_time(g1)
     ocpu = None
     if not args.no_cpu:
+        from oracle import reduced as R             # the oracle, for this leg's CPU baseline only
         ns = 1000
         t0c = time.perf_counter()
         R.integrate(*[v[:ns] for v in y0], *par, 0.0, 0.05, 50)
