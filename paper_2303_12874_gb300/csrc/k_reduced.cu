@@ -95,10 +95,12 @@ __global__ void __launch_bounds__(128) k_reduced_dp5(double *__restrict__ X, dou
     X[i] = y[0]; Z[i] = y[1]; UX[i] = y[2]; UZ[i] = y[3];
 }
 
-bool red_args_ok(long long n, double dt, int nsteps, double vphi, double kperp, double wp, double a0)
+bool red_args_ok(long long n, double dt, int nsteps, double vphi, double kperp, double wp, double a0,
+                 double t0)
 {
     return n >= 0 && nsteps >= 0 && std::isfinite(dt) && dt > 0 && vphi > 0 && std::isfinite(vphi) &&
-           kperp >= 0 && std::isfinite(kperp) && std::isfinite(wp) && std::isfinite(a0);
+           kperp >= 0 && std::isfinite(kperp) && std::isfinite(wp) && std::isfinite(a0) &&
+           std::isfinite(t0);
 }
 
 qpic_status red_launch(long long n, double *x, double *zeta, double *ux, double *uz, double a0,
@@ -119,7 +121,7 @@ extern "C" qpic_status qpic_reduced_integrate_device(int64_t n, double *x, doubl
                                                      double k_perp, double v_phi, double t0,
                                                      double dt, int32_t nsteps, void *stream)
 {
-    if (!red_args_ok(n, dt, nsteps, v_phi, k_perp, omega_p, a0)) return QPIC_EINVAL;
+    if (!red_args_ok(n, dt, nsteps, v_phi, k_perp, omega_p, a0, t0)) return QPIC_EINVAL;
     if (n > 0 && (!x || !zeta || !ux || !uz)) return QPIC_EINVAL;
     if (n > (long long)(1u << 31) * 127) return QPIC_EINVAL;
     return red_launch(n, x, zeta, ux, uz, a0, omega_p, k_perp, v_phi, t0, dt, nsteps,
@@ -130,7 +132,7 @@ extern "C" qpic_status qpic_reduced_integrate(int64_t n, double *x, double *zeta
                                               double a0, double omega_p, double k_perp, double v_phi,
                                               double t0, double dt, int32_t nsteps)
 {
-    if (!red_args_ok(n, dt, nsteps, v_phi, k_perp, omega_p, a0)) return QPIC_EINVAL;
+    if (!red_args_ok(n, dt, nsteps, v_phi, k_perp, omega_p, a0, t0)) return QPIC_EINVAL;
     if (n > 0 && (!x || !zeta || !ux || !uz)) return QPIC_EINVAL;
     if (n == 0) return QPIC_OK;
     double *d = nullptr;
