@@ -66,3 +66,24 @@ def test_context_needs_a_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(q.QpicError):
         q.Sim(64, 8, 0.2, 0.5)
+
+
+def test_reduced_model_argument_checks_without_a_gpu():
+    """qpic_reduced_integrate refuses bad arguments before touching the GPU,
+    accepts an empty set, and reports a CUDA error (no CPU fallback) otherwise
+    when no GPU is present"""
+    import math
+    L = q.load()
+    ok = (1.0, 0.1, 0.04, 1.0, 0.0, 0.1, 1)                 # a0, w_p, k_perp, v_phi, t0, dt, nsteps
+    assert L.qpic_reduced_integrate(0, None, None, None, None, *ok) == 0
+    assert L.qpic_reduced_integrate(-1, None, None, None, None, *ok) == -1
+    for k, bad in ((3, -1.0), (3, 0.0), (4, math.nan), (5, 0.0), (5, math.inf), (2, -0.1), (6, -1)):
+        args = list(ok)
+        args[k] = bad
+        assert L.qpic_reduced_integrate(0, None, None, None, None, *args) == -1, (k, bad)
+    x = np.zeros(3)
+    assert L.qpic_reduced_integrate(3, q._dp(x), None, q._dp(x), q._dp(x), *ok) == -1
+    import torch
+    if not torch.cuda.is_available():
+        y = [np.zeros(2) for _ in range(4)]
+        assert L.qpic_reduced_integrate(2, *[q._dp(v) for v in y], *ok) != 0
