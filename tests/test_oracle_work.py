@@ -125,3 +125,12 @@ def test_library_f_estimate_matches_the_oracle():
         q.work_f_estimate(u[0], u[1], u[2], Wz, Wp, 0.0, 30.36)
     L = q.load()
     assert L.qpic_work_f_estimate(-1, None, None, None, None, None, 0.1, 1.0, 1.0, None, None) == -1
+
+
+def test_f_at_the_papers_bunch_values():
+    """Sec. IV.C evaluates Eq. 19 with omega0 = 12 omega_p and w0 = 2.53 c/omega_p:
+    in units of omega0, omega_p = 1/12 and w0 = 30.36, so f = -0.0260 sqrt(2 gamma)
+    and f(gamma = 200) = -0.52"""
+    f = diag.work_f_ratio(200.0, 1 / 12.0, 2.53 * 12.0)
+    assert f == pytest.approx(-0.5208, abs=5e-4)
+    assert diag.work_f_ratio(50.0, 1 / 12.0, 2.53 * 12.0) / np.sqrt(100.0) == pytest.approx(-0.02604, abs=5e-5)
