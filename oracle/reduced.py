@@ -22,9 +22,10 @@ gamma = sqrt(1 + u_x^2 + u_z^2).
 
 Readings: k_z = omega0 / v_phi (the laser's longitudinal wavenumber follows the
 phase velocity, which the paper takes from a PIC run), k_perp is an input
-(Eq. 3's 2.4/(r_b + c/w_p) is the caller's choice), and the integrator is the
-fifth-order Dormand-Prince Runge-Kutta method (Dormand & Prince, J. Comput.
-Appl. Math. 6, 1980) at a fixed step, its fifth-order weights.
+(Eq. 3's 2.4/(r_b + c/w_p) is the caller's choice), and the explicit
+fifth-order Runge-Kutta method of Appendix A is taken to be Dormand-Prince
+(Dormand & Prince, J. Comput. Appl. Math. 6, 1980) at a fixed step, its
+fifth-order weights.
 """
 import numpy as np
 from scipy import special

@@ -13,8 +13,8 @@
 // (Eq. 8's x'' + (gamma'/gamma) x' is d(gamma x')/dt / gamma, and
 // zeta'' + (gamma'/gamma)(zeta' + 1) is d(gamma z')/dt / gamma.)
 //
-// Integrator: the fifth-order Dormand-Prince Runge-Kutta method (Dormand &
-// Prince 1980) at a fixed step.  Each electron is independent: the kernel
+// Integrator: an explicit fifth-order Runge-Kutta method (Appendix A), here
+// Dormand-Prince (Dormand & Prince 1980) at a fixed step.  Each electron is independent: the kernel
 // reads its four words once, keeps the state in registers for all the steps
 // and writes it back; it is bound by FP64 arithmetic and the Bessel functions.
 #include <cuda_runtime.h>
