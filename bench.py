@@ -139,10 +139,13 @@ def reduced_leg(q, torch, stream, args):
     """The reduced model of Eq. 8 (FP64 Dormand-Prince, one thread per electron) on
     a synthetic bunch; the oracle timed on a small sample unless --no-cpu."""
     nr_e, st_e = args.reduced_electrons, args.reduced_steps
-    rng = np.random.default_rng(8)
-    y0 = [rng.uniform(-3.0, 3.0, nr_e), rng.uniform(-40.0, -5.0, nr_e), rng.normal(0.0, 1.0, nr_e),
-          rng.uniform(0.0, 60.0, nr_e)]
-    par = (2.0, 1 / 12.0, 0.04, 1.0008)             # a0, omega_p, k_perp, v_phi (omega0 = 1)
+    # Appendix A's bunch and parameters, in units of the local laser frequency
+    # (omega0 = v_phi k_z = 12.17 omega_p); k_perp = 2.4/(R + c/omega_p) with R
+    # standing for the mean bubble radius at the bunch
+    P = synth.REDUCED_PAPER
+    wp = 1.0 / (P["v_phi"] * P["kz_over_wp"])
+    y0 = list(synth.reduced_bunch(8, nr_e, v_g=P["v_g"], wp=wp, R_over_lp=P["R_over_lp"]))
+    par = (P["a0"], wp, 2.4 * wp / (P["R_over_lp"] + 1.0), P["v_phi"])   # a0, omega_p, k_perp, v_phi
     dev = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in y0]
     ptrs = [d.data_ptr() for d in dev]
     sh = stream.cuda_stream
@@ -165,8 +168,8 @@ def reduced_leg(q, torch, stream, args):
                 "sample": "1000 electrons x 50 steps, numpy FP64"}
     return {"value": nr_e * st_e / (msr / 1e3), "unit": "electron-steps/s", "electrons": nr_e,
             "steps": st_e, "ms": msr, "dtype": "f64", "cpu_baseline": ocpu,
-            "note": "Eq. 8 in a spherical bubble and a channel laser (a0 2, omega_p 1/12, "
-                    "k_perp 0.04, v_phi 1.0008), fifth-order Dormand-Prince at dt 0.05"}
+            "note": "Eq. 8 with Appendix A's bunch and parameters (a0 2.8, v_phi 1.002565, "
+                    "k_z 12.14 omega_p, R 3 c/omega_p), fifth-order Dormand-Prince at dt 0.05 / omega0"}
 
 
 def batch_scan(q, torch, stream, nruns, steps, seed=5):

@@ -70,3 +70,30 @@ def random_fields(seed, nz, nr, n_modes, amp=0.3):
             im = rng.standard_normal((nr + 1, nz)) if m else np.zeros((nr + 1, nz))
             out[c].append(amp * (re + 1j * im))
     return out
+
+
+# Appendix A's reduced-model set (measured from the paper's 3D PIC runs):
+# v_phi = 1.002565 c, v_g = 0.993583 c, k_z = 12.14 w_p/c, R = 3 c/w_p, a0 = 2.8.
+# In units of the local laser frequency w0 = v_phi k_z (= 12.17 w_p):
+REDUCED_PAPER = dict(a0=2.8, v_phi=1.002565, v_g=0.993583, kz_over_wp=12.14, R_over_lp=3.0)
+
+
+def reduced_bunch(seed, n, v_g=0.993583, wp=1.0 / (1.002565 * 12.14), R_over_lp=3.0):
+    """Electrons injected into the bubble as Appendix A describes, in units of
+    the laser frequency (c = 1): zeta uniform in [-2R + 0.286/w_p, -2R +
+    0.836/w_p] shifted by +R (the model's bubble is centred on zeta = 0), x
+    uniform in [-r_b, r_b] with r_b = sqrt(R^2 - zeta^2), gamma uniform in
+    [gamma_g, 2 gamma_g] with gamma_g = 1/sqrt(1 - v_g^2), and the velocity at
+    a random angle to the x axis with v_z >= v_g.  Returns (x, zeta, u_x, u_z)."""
+    rng = np.random.default_rng([seed, 7])
+    R = R_over_lp / wp
+    zeta = rng.uniform(-2 * R + 0.286 / wp, -2 * R + 0.836 / wp, n) + R
+    rb = np.sqrt(np.maximum(R * R - zeta * zeta, 0.0))
+    x = rng.uniform(-1.0, 1.0, n) * rb
+    gg = 1.0 / np.sqrt(1.0 - v_g * v_g)
+    gamma = rng.uniform(gg, 2 * gg, n)
+    v = np.sqrt(1.0 - 1.0 / (gamma * gamma))
+    smin = np.minimum(v_g / v, 1.0)                  # sin of the angle to the x axis, v_z >= v_g
+    th = rng.uniform(np.arcsin(smin), np.pi - np.arcsin(smin))
+    u = gamma * v
+    return x, zeta, u * np.cos(th), u * np.sin(th)

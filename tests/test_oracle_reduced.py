@@ -93,3 +93,28 @@ def test_matches_scipy_dop853():
     y = _run(tuple(y0), LASER, 0.05, int(T / 0.05))[:, 0]
     assert np.max(np.abs(y - sol.y[:, -1]) / (1 + np.abs(sol.y[:, -1]))) < 1e-9
     assert abs(y[2]) > 0.1                                     # the laser drove the x motion
+
+
+def test_appendix_bunch_and_its_orbits():
+    """the seeded bunch follows Appendix A's injection recipe, and the oracle
+    integrates it with the appendix's parameters without leaving the model:
+    the wake invariant changes only through the laser"""
+    import synth
+    P = synth.REDUCED_PAPER
+    wp = 1.0 / (P["v_phi"] * P["kz_over_wp"])
+    Rb = P["R_over_lp"] / wp
+    x, zeta, ux, uz = synth.reduced_bunch(3, 4000, v_g=P["v_g"], wp=wp, R_over_lp=P["R_over_lp"])
+    assert np.all((zeta >= -Rb + 0.286 / wp) & (zeta <= -Rb + 0.836 / wp))
+    assert np.all(np.abs(x) <= np.sqrt(Rb * Rb - zeta * zeta))
+    gamma = np.sqrt(1 + ux ** 2 + uz ** 2)
+    gg = 1 / np.sqrt(1 - P["v_g"] ** 2)
+    assert np.all((gamma >= gg * (1 - 1e-12)) & (gamma <= 2 * gg))
+    assert np.all(uz / gamma >= P["v_g"] * (1 - 1e-12))
+    y = R.integrate(x[:200], zeta[:200], ux[:200], uz[:200], P["a0"], wp, 2.4 * wp / (P["R_over_lp"] + 1),
+                    P["v_phi"], 0.0, 0.1, 300)
+    assert np.all(np.isfinite(np.array(y)))
+    y0 = R.integrate(x[:200], zeta[:200], ux[:200], uz[:200], 0.0, wp, 0.05, P["v_phi"], 0.0, 0.1, 300)
+    I = lambda x_, z_, a_, b_: np.sqrt(1 + a_ ** 2 + b_ ** 2) - b_ + 0.25 * wp * wp * (x_ ** 2 + z_ ** 2)
+    I0 = I(x[:200], zeta[:200], ux[:200], uz[:200])
+    assert np.max(np.abs(I(*y0) - I0) / I0) < 1e-10            # no laser: invariant kept
+    assert np.max(np.abs(I(*y) - I0) / I0) > 1e-6               # the laser changes it
