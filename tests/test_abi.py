@@ -87,3 +87,13 @@ def test_reduced_model_argument_checks_without_a_gpu():
     if not torch.cuda.is_available():
         y = [np.zeros(2) for _ in range(4)]
         assert L.qpic_reduced_integrate(2, *[q._dp(v) for v in y], *ok) != 0
+
+
+def test_configuration_checks_come_before_the_gpu():
+    """qpic_init validates its configuration before it touches the device: an
+    unknown work-tracking mode or precision is named in the error (with or
+    without a GPU)"""
+    with pytest.raises(q.QpicError, match="track_work"):
+        q.Sim(64, 8, 0.2, 0.5, track_work=3)
+    with pytest.raises(q.QpicError, match="precision"):
+        q.Sim(64, 8, 0.2, 0.5, precision=7)
