@@ -109,7 +109,10 @@ qpic_status qpic_default_config(qpic_config *cfg);
  * long-wavelength limit), find dt by bisection of the leapfrog stability
  * bound when cfg->dt <= 0, build the J_z filter taps, allocate zeroed device
  * fields.  *out receives the context; on failure it may still receive one so
- * that qpic_last_error can explain -- destroy it with qpic_destroy. */
+ * that qpic_last_error can explain -- destroy it with qpic_destroy.
+ * The device current at this call owns every buffer of the context: every
+ * later call on the context that touches the device must be made with that
+ * device current, else it returns QPIC_ESTATE and launches nothing. */
 qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out);
 
 /* Free everything the context owns.  NULL is allowed. */
@@ -164,7 +167,14 @@ qpic_status qpic_work_f_estimate(int64_t n, const double *ux, const double *uy, 
  * the plasma frequency (the bubble's w_beta^2 = omega_p^2/(2 gamma), Eq. 1),
  * k_perp the laser's transverse wavenumber (Eq. 3; the paper's choice is
  * 2.4/(r_b + c/omega_p)), v_phi its phase velocity (k_z = omega0/v_phi), a0 its
- * normalized amplitude.
+ * normalized amplitude.  bfac multiplies the laser's magnetic terms (those
+ * proportional to v sin(k_z xi)): cos(omega0 dt/2) models the time-staggering
+ * error of a PIC solver with time step dt (Sec. IV.A; about 0.994 for the
+ * paper's Yee runs), 1 gives Eq. 8 as printed.  start_step: NULL, or n int32
+ * step indices (host for qpic_reduced_integrate, device for the _device
+ * variant): electron i stays at its initial state until step start_step[i]
+ * of the grid t0 + k dt and is integrated from there (Appendix A injects the
+ * electrons over a time interval); a start at or beyond nsteps leaves it.
  *   qpic_reduced_integrate: caller-owned host arrays of n doubles; the call
  *     copies them to the device and back and returns when done.
  *   qpic_reduced_integrate_device: device arrays, launched on `stream`
@@ -175,10 +185,12 @@ qpic_status qpic_work_f_estimate(int64_t n, const double *ux, const double *uy, 
  * Eq. 8 for single electrons. */
 qpic_status qpic_reduced_integrate(int64_t n, double *x, double *zeta, double *ux, double *uz,
                                    double a0, double omega_p, double k_perp, double v_phi,
-                                   double t0, double dt, int32_t nsteps);
+                                   double bfac, double t0, double dt, int32_t nsteps,
+                                   const int32_t *start_step);
 qpic_status qpic_reduced_integrate_device(int64_t n, double *x, double *zeta, double *ux,
                                           double *uz, double a0, double omega_p, double k_perp,
-                                          double v_phi, double t0, double dt, int32_t nsteps,
+                                          double v_phi, double bfac, double t0, double dt,
+                                          int32_t nsteps, const int32_t *start_step,
                                           void *stream);
 
 /* Stability limit of the configured solver on this grid (leapfrog bound
@@ -251,7 +263,8 @@ qpic_status qpic_set_fields(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t 
  * the array (each clears what it uses first); calls that overlap on the GPU,
  * from any context or thread, race.  re/im: caller-owned host arrays of
  * (nr+1)*nz doubles in the field-plane layout; im may be NULL.  Synchronises
- * the context's stream. */
+ * the context's stream.  The context's device (current at qpic_init) must be
+ * current; otherwise QPIC_ESTATE and nothing is launched. */
 qpic_status qpic_charge_density_noalloc(qpic_ctx *ctx, int32_t mode, double *re, double *im);
 
 /* Number of live particles. */
@@ -276,7 +289,9 @@ qpic_status qpic_get_particles_raw(qpic_ctx *ctx, double *out, int64_t capacity,
  * partial sums, FP64 block and grid sums in a fixed order).  Synchronises the
  * context's stream once; the first call allocates 512 bytes of pinned host
  * memory for the read-back (freed by qpic_destroy; pageable words are used if
- * pinning fails). */
+ * pinning fails).  QPIC_ENONFINITE (out still filled) when the charge, the
+ * kinetic energy or a field energy is NaN or infinite: a NaN or infinity in
+ * any particle or field value reaches these sums. */
 qpic_status qpic_get_diag(qpic_ctx *ctx, double *out, int32_t count);
 
 /* Gauss's law residual per mode in the dual form of Eq. 10: out[2m] = L2 norm

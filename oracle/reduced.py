@@ -20,12 +20,22 @@ the state (x, zeta, u_x, u_z) is explicit:
     du_z/dt = gamma F_z - (w_p^2/2)(zeta - x x'/2),
 gamma = sqrt(1 + u_x^2 + u_z^2).
 
+Time-staggering factor (Sec. IV.A): to model a solver whose E and B are
+staggered in time, the laser's magnetic terms -- those proportional to
+v sin(k_z xi): k_z z' J0 and (k_perp^2/k_z) z' J1' in F_x, k_z x' [J0 +
+(k_perp/k_z)^2 J1'] in F_z -- are multiplied by b = cos(omega0 dt_PIC / 2)
+(about 0.994 for the paper's Yee runs); b = 1 is the unstaggered model.
+
+Injection (Appendix A): electrons enter the bubble over a time interval.
+Electron i is held at its initial state until step start[i] of the fixed step
+grid t0 + k dt and integrated from there (start = None: all from step 0).
+
 Readings: k_z = omega0 / v_phi (the laser's longitudinal wavenumber follows the
 phase velocity, which the paper takes from a PIC run), k_perp is an input
-(Eq. 3's 2.4/(r_b + c/w_p) is the caller's choice), and the explicit
-fifth-order Runge-Kutta method of Appendix A is taken to be Dormand-Prince
-(Dormand & Prince, J. Comput. Appl. Math. 6, 1980) at a fixed step, its
-fifth-order weights.
+(Eq. 3's 2.4/(r_b + c/w_p) is the caller's choice), the injection time is
+rounded up to the step grid, and the explicit fifth-order Runge-Kutta method
+of Appendix A is taken to be Dormand-Prince (Dormand & Prince, J. Comput.
+Appl. Math. 6, 1980) at a fixed step, its fifth-order weights.
 """
 import numpy as np
 from scipy import special
@@ -52,8 +62,9 @@ def j1_prime(s):
     return out
 
 
-def rhs(t, y, a0, wp, kperp, vphi):
-    """time derivative of y = (x, zeta, u_x, u_z) (arrays of n particles)"""
+def rhs(t, y, a0, wp, kperp, vphi, bfac=1.0):
+    """time derivative of y = (x, zeta, u_x, u_z) (arrays of n particles);
+    bfac multiplies the laser's magnetic (v sin(k_z xi)) terms"""
     x, zeta, ux, uz = y
     gamma = np.sqrt(1.0 + ux * ux + uz * uz)
     vx, vz = ux / gamma, uz / gamma
@@ -62,8 +73,8 @@ def rhs(t, y, a0, wp, kperp, vphi):
     s = kperp * x
     J0, J1, J1p = special.j0(s), special.j1(s), j1_prime(s)
     sn, cs = np.sin(kz * xi), np.cos(kz * xi)
-    Fx = (a0 / gamma) * ((1.0 - kz * vz) * J0 - (kperp * kperp / kz) * vz * J1p) * sn
-    Fz = -(a0 / gamma) * ((kperp / kz) * J1 * cs - kz * vx * (J0 + (kperp * kperp) / (kz * kz) * J1p) * sn)
+    Fx = (a0 / gamma) * ((1.0 - bfac * kz * vz) * J0 - bfac * (kperp * kperp / kz) * vz * J1p) * sn
+    Fz = -(a0 / gamma) * ((kperp / kz) * J1 * cs - bfac * kz * vx * (J0 + (kperp * kperp) / (kz * kz) * J1p) * sn)
     dux = gamma * Fx - 0.25 * wp * wp * (1.0 + vz) * x
     duz = gamma * Fz - 0.5 * wp * wp * (zeta - 0.5 * x * vx)
     return np.array([vx, vz - 1.0, dux, duz])
@@ -78,11 +89,18 @@ def dp5_step(t, y, dt, *par):
     return y + dt * sum(b * kj for b, kj in zip(DP_B, k))
 
 
-def integrate(x, zeta, ux, uz, a0, wp, kperp, vphi, t0, dt, nsteps):
-    """nsteps fixed steps from t0; returns the final (x, zeta, u_x, u_z)"""
+def integrate(x, zeta, ux, uz, a0, wp, kperp, vphi, t0, dt, nsteps, bfac=1.0, start=None):
+    """nsteps fixed steps from t0; electron i moves from step start[i] on (all
+    from step 0 when start is None); returns the final (x, zeta, u_x, u_z)"""
     y = np.array([np.asarray(v, dtype=np.float64) for v in (x, zeta, ux, uz)])
+    st = None if start is None else np.asarray(start)
     t = t0
     for k in range(nsteps):
-        y = dp5_step(t, y, dt, a0, wp, kperp, vphi)
+        if st is None:
+            y = dp5_step(t, y, dt, a0, wp, kperp, vphi, bfac)
+        else:
+            on = st <= k
+            if on.any():
+                y[:, on] = dp5_step(t, y[:, on], dt, a0, wp, kperp, vphi, bfac)
         t = t0 + (k + 1) * dt
     return y[0], y[1], y[2], y[3]

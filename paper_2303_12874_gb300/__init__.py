@@ -120,10 +120,12 @@ def _declare(L):
     L.qpic_spectrum.restype = ctypes.c_int
     L.qpic_charge_density_noalloc.restype = ctypes.c_int
     L.qpic_launch_count.restype = ctypes.c_int
-    L.qpic_reduced_integrate.argtypes = [ctypes.c_int64] + [_D] * 4 + [ctypes.c_double] * 6 + [_I]
+    L.qpic_reduced_integrate.argtypes = ([ctypes.c_int64] + [_D] * 4 + [ctypes.c_double] * 7 +
+                                         [_I, ctypes.POINTER(_I)])
     L.qpic_reduced_integrate.restype = ctypes.c_int
     L.qpic_reduced_integrate_device.argtypes = ([ctypes.c_int64] + [ctypes.c_void_p] * 4 +
-                                                [ctypes.c_double] * 6 + [_I, ctypes.c_void_p])
+                                                [ctypes.c_double] * 7 + [_I, ctypes.c_void_p,
+                                                                         ctypes.c_void_p])
     L.qpic_reduced_integrate_device.restype = ctypes.c_int
     L.qpic_work_f_estimate.argtypes = [ctypes.c_int64] + [_D] * 5 + [ctypes.c_double] * 3 + [_D, _D]
     L.qpic_work_f_estimate.restype = ctypes.c_int
@@ -193,26 +195,39 @@ def work_f_estimate(ux, uy, uz, Wz, Wperp, omega_p, w0, omega0=1.0):
     return lwfa, dla
 
 
-def reduced_integrate(x, zeta, ux, uz, a0, omega_p, k_perp, v_phi, t0, dt, nsteps):
+def reduced_integrate(x, zeta, ux, uz, a0, omega_p, k_perp, v_phi, t0, dt, nsteps, bfac=1.0,
+                      start=None):
     """The reduced model of Eq. 8 on the GPU (qpic_reduced_integrate): host
-    arrays in, new host arrays (x, zeta, u_x, u_z) out after nsteps steps."""
+    arrays in, new host arrays (x, zeta, u_x, u_z) out after nsteps steps.
+    bfac: factor on the laser's magnetic terms (cos(omega0 dt/2) models a
+    time-staggered solver); start: optional per-electron first step."""
     L = load()
     a = [np.array(v, dtype=np.float64, copy=True).reshape(-1) for v in (x, zeta, ux, uz)]
     n = len(a[0])
     if any(len(v) != n for v in a):
         raise ValueError("reduced_integrate: arrays of different lengths")
-    st = L.qpic_reduced_integrate(n, *[_dp(v) for v in a], a0, omega_p, k_perp, v_phi, t0, dt, int(nsteps))
+    sp = None
+    if start is not None:
+        sa = np.ascontiguousarray(start, dtype=np.int32).reshape(-1)
+        if len(sa) != n:
+            raise ValueError("reduced_integrate: start has %d entries, need %d" % (len(sa), n))
+        sp = sa.ctypes.data_as(ctypes.POINTER(_I))
+    st = L.qpic_reduced_integrate(n, *[_dp(v) for v in a], a0, omega_p, k_perp, v_phi, bfac, t0, dt,
+                                  int(nsteps), sp)
     if st != 0:
         raise QpicError("qpic_reduced_integrate: %s" % STATUS.get(st, st))
     return tuple(a)
 
 
-def reduced_integrate_device(ptrs, n, a0, omega_p, k_perp, v_phi, t0, dt, nsteps, stream=None):
+def reduced_integrate_device(ptrs, n, a0, omega_p, k_perp, v_phi, t0, dt, nsteps, stream=None, bfac=1.0,
+                             start_ptr=None):
     """Device variant: ptrs = four device addresses of n doubles (x, zeta, u_x,
-    u_z), advanced in place on `stream` (an integer cudaStream_t or None)."""
+    u_z), advanced in place on `stream` (an integer cudaStream_t or None);
+    start_ptr: optional device address of n int32 first steps."""
     L = load()
     st = L.qpic_reduced_integrate_device(n, *[ctypes.c_void_p(int(p)) for p in ptrs], a0, omega_p, k_perp,
-                                         v_phi, t0, dt, int(nsteps), ctypes.c_void_p(stream or 0))
+                                         v_phi, bfac, t0, dt, int(nsteps), ctypes.c_void_p(start_ptr or 0),
+                                         ctypes.c_void_p(stream or 0))
     if st != 0:
         raise QpicError("qpic_reduced_integrate_device: %s" % STATUS.get(st, st))
 

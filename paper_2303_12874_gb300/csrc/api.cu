@@ -250,6 +250,17 @@ void record_ions(qpic_ctx *c)
 
 namespace qpic {
 
+qpic_status check_device(qpic_ctx *c)
+{
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(c, QPIC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev != c->device)
+        return fail(c, QPIC_ESTATE, "the context was created on device " + std::to_string(c->device) +
+                                        " but device " + std::to_string(dev) + " is current");
+    return QPIC_OK;
+}
+
 void prof_begin(qpic_ctx *c)
 {
     if (!c->profile) return;
@@ -353,6 +364,10 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->fp64 = cfg->precision == QPIC_FP64;
     c->fatomic = cfg->precision == QPIC_FP32_FATOMIC;
     if (cfg->moving_window && cfg->periodic_z) return bad(QPIC_EINVAL, "moving window needs periodic_z = 0");
+    {
+        const cudaError_t e = cudaGetDevice(&c->device);
+        if (e != cudaSuccess) return bad(QPIC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
     c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     c->dz = cfg->dz;
     c->dr = cfg->dr;
@@ -534,6 +549,7 @@ qpic_status qpic_load_plasma(qpic_ctx *c, double n0, double z_start, double ramp
 {
     if (!c) return QPIC_EINVAL;
     if (ppc_z < 1 || ppc_r < 1 || ppc_phi < 1 || !(n0 >= 0)) return fail(c, QPIC_EINVAL, "plasma parameters");
+    QPIC_REQUIRE_DEVICE(c);
     c->have_plasma = true;
     c->n0 = n0; c->z_start = z_start; c->ramp_len = ramp_len;
     c->ppc_z = ppc_z; c->ppc_r = ppc_r; c->ppc_phi = ppc_phi; c->jitter = phi_jitter ? 1 : 0;
@@ -564,6 +580,7 @@ qpic_status qpic_load_particles(qpic_ctx *c, int64_t n, const double *z, const d
 {
     if (!c || n < 0 || (n > 0 && (!z || !r || !phi || !ux || !uy || !uz || !w)))
         return fail(c, QPIC_EINVAL, "load_particles arguments");
+    QPIC_REQUIRE_DEVICE(c);
     qpic_status s = ensure_capacity(c, n);
     if (s != QPIC_OK) return s;
     double *tmp = nullptr;
@@ -600,6 +617,7 @@ qpic_status qpic_add_laser(qpic_ctx *c, double a0, double w0, double fwhm, doubl
     if (!c) return QPIC_EINVAL;
     if (c->g.nm < 2) return fail(c, QPIC_EINVAL, "a laser needs n_modes >= 2");
     if (!(w0 > 0) || !(fwhm > 0)) return fail(c, QPIC_EINVAL, "laser parameters");
+    QPIC_REQUIRE_DEVICE(c);
     launch_laser(c, a0, w0, fwhm, z_centroid, z_focus, pol_angle);
     return cuda_check(c, "add_laser");
 }
@@ -607,6 +625,7 @@ qpic_status qpic_add_laser(qpic_ctx *c, double a0, double w0, double fwhm, doubl
 qpic_status qpic_run_stages(qpic_ctx *c, int32_t stages)
 {
     if (!c) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     run_one_step(c, stages);
     qpic_status s = cuda_check(c, "run_stages");
@@ -617,6 +636,7 @@ qpic_status qpic_run_stages(qpic_ctx *c, int32_t stages)
 qpic_status qpic_step(qpic_ctx *c, int32_t nsteps)
 {
     if (!c || nsteps < 0) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     const int all = QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE |
                     QPIC_STAGE_WINDOW | QPIC_STAGE_SORT;
@@ -631,6 +651,7 @@ qpic_status qpic_get_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
 {
     if (!c || !re || comp < 0 || comp > 2 || mode < 0 || mode >= c->g.nm || which < 0 || which > 4)
         return fail(c, QPIC_EINVAL, "get_field arguments");
+    QPIC_REQUIRE_DEVICE(c);
     const FieldGeom &g = c->g;
     const size_t nout = (size_t)(g.nr + 1) * g.nz;
     const ColMap cm = col_map(c);
@@ -697,6 +718,7 @@ qpic_status qpic_set_field(qpic_ctx *c, int32_t which, int32_t comp, int32_t mod
     if (!c || !re || comp < 0 || comp > 2 || mode < 0 || mode >= c->g.nm ||
         (which != QPIC_FIELD_E && which != QPIC_FIELD_B && which != QPIC_FIELD_BBAR))
         return fail(c, QPIC_EINVAL, "set_field arguments");
+    QPIC_REQUIRE_DEVICE(c);
     const FieldGeom &g = c->g;
     const ColMap cm = col_map(c);
     if (c->fp64) {
@@ -762,6 +784,7 @@ qpic_status qpic_set_fields(qpic_ctx *c, int32_t which, int32_t comp, int32_t mo
 qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
 {
     if (!c || !n) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     if (c->fp64) {
         fp64_compact(c);
         *n = c->np;
@@ -775,6 +798,7 @@ qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
 qpic_status qpic_get_particles(qpic_ctx *c, double *out, int64_t capacity, int64_t *n_out)
 {
     if (!c || !out || !n_out) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     long long n;
     if (c->fp64) {
         fp64_compact(c);
@@ -802,6 +826,7 @@ qpic_status qpic_get_particles(qpic_ctx *c, double *out, int64_t capacity, int64
 qpic_status qpic_get_particles_raw(qpic_ctx *c, double *out, int64_t capacity, int64_t *n_out)
 {
     if (!c || !out || !n_out) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     long long n = c->fp64 ? c->np : live_count(c);   // buffer slots in use
     *n_out = n;
     if (n > capacity) return fail(c, QPIC_ECAPACITY, "get_particles_raw: capacity too small");
@@ -838,6 +863,7 @@ qpic_status qpic_work_f_estimate(int64_t n, const double *ux, const double *uy, 
 qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)
 {
     if (!c || !out) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     const int nm = c->g.nm;
     std::vector<double> v(7 + nm, 0.0);
     v[0] = c->nstep * c->dt;
@@ -862,12 +888,20 @@ qpic_status qpic_get_diag(qpic_ctx *c, double *out, int32_t count)
     for (int m = 0; m < nm; m++) v[6 + m] = hb[3 + m];
     v[6 + nm] = (*he & 1) ? 1.0 : 0.0;
     for (int k = 0; k < count && k < (int)v.size(); k++) out[k] = v[k];
-    return cuda_check(c, "get_diag");
+    qpic_status st = cuda_check(c, "get_diag");
+    if (st != QPIC_OK) return st;
+    // a NaN or infinity anywhere in the fields or the particles reaches these sums
+    for (int k = 4; k < 6 + nm; k++)
+        if (!std::isfinite(v[k]))
+            return fail(c, QPIC_ENONFINITE, "get_diag: non-finite charge, kinetic or field energy "
+                                            "(NaN or infinity in the particles or fields)");
+    return QPIC_OK;
 }
 
 qpic_status qpic_gauss_residual(qpic_ctx *c, double *out, int32_t count)
 {
     if (!c || !out) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
     if (c->cfg.moving_window) return fail(c, QPIC_ESTATE, "gauss_residual: ion background moves with the window");
     if (!c->rho_ion) return fail(c, QPIC_ESTATE, "gauss_residual: no particles loaded");
     const int nm = c->g.nm;
@@ -892,6 +926,7 @@ qpic_status qpic_spectrum(qpic_ctx *c, const double *edges_mev, int32_t nbins, d
     if (!c || !edges_mev || !weights || nbins < 1 || nbins > 4096) return fail(c, QPIC_EINVAL, "spectrum arguments");
     for (int k = 0; k < nbins; k++)
         if (!(edges_mev[k + 1] > edges_mev[k])) return fail(c, QPIC_EINVAL, "spectrum: edges must increase");
+    QPIC_REQUIRE_DEVICE(c);
     const double wmax = c->fp64 ? 0.0 : c->qref;
     double *de = nullptr;
     unsigned long long *dh = nullptr;
@@ -1034,6 +1069,7 @@ qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_strea
             return QPIC_EINVAL;
         }
         if (c->sort_period != runs[0]->sort_period) { b->err = "batch runs need one sort period"; return QPIC_EINVAL; }
+        if (check_device(c) != QPIC_OK) { b->err = "batch runs: " + c->err; return QPIC_ESTATE; }
         b->runs.push_back(c);
     }
     // bring every run to a cycle boundary, then drain all work

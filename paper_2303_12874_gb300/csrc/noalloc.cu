@@ -12,7 +12,8 @@
 // 16 MiB until the process exits.  In host code the array's name is only a
 // host-side stand-in, so the device address is looked up once per device with
 // cudaGetSymbolAddress (on the first call on that device, with it current)
-// and passed to the deposit kernel.
+// and passed to the deposit kernel.  A call must be made with the context's
+// device current (the device of qpic_init); otherwise it returns QPIC_ESTATE.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,20 +31,19 @@ static __device__ __align__(256) double g_rho_scratch[kScratchDoubles];
 std::mutex g_mu;
 double *g_ptr[kMaxDevices] = {nullptr};
 
-// device address of the scratch array on the current device (set-up on the
-// first call per device); nullptr on failure with *err set
-double *scratch_address(std::string *err)
+// device address of the scratch array on device dev, which must be current
+// (set-up on the first call per device); nullptr on failure with *err set
+double *scratch_address(int dev, std::string *err)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        *err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    if (dev < 0 || dev >= kMaxDevices) {
+        *err = "device index " + std::to_string(dev) + " is beyond the " + std::to_string(kMaxDevices) +
+               " devices the scratch table holds";
         return nullptr;
     }
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_ptr[dev]) {
         double *p = nullptr;
-        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_rho_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_rho_scratch);
         if (e != cudaSuccess || !p) {
             *err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
             return nullptr;
@@ -70,8 +70,11 @@ extern "C" qpic_status qpic_charge_density_noalloc(qpic_ctx *c, int32_t mode, do
                  std::to_string(kScratchDoubles);
         return QPIC_EINVAL;
     }
+    // the array and the context's stream belong to the context's device: refuse
+    // a call made while another device is current
+    QPIC_REQUIRE_DEVICE(c);
     std::string err;
-    double *d = scratch_address(&err);
+    double *d = scratch_address(c->device, &err);
     if (!d) {
         c->err = "charge_density_noalloc: " + err;
         return QPIC_ECUDA;

@@ -89,6 +89,7 @@ struct qpic_ctx {
     qpic_config cfg;
     std::string err;
     cudaStream_t stream = nullptr;
+    int device = -1;                      // the device current at qpic_init (owns every buffer)
     bool fp64 = false;
     bool fatomic = false;                 // FP32 path with float-atomic deposit (precision variant)
 
@@ -220,11 +221,22 @@ void fp64_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale, unsi
 void scale_buffer(qpic_ctx *c, double *buf, size_t n, double s);
 void fp64_field_energy(qpic_ctx *c, double *out_modes);
 
+// QPIC_OK when the context's device is the current one, else QPIC_ESTATE (or
+// QPIC_ECUDA) with the context's error text set (api.cu)
+qpic_status check_device(qpic_ctx *c);
+
 // profiling helpers (api.cu)
 void prof_begin(qpic_ctx *c);
 void prof_end(qpic_ctx *c, int kclass, int nkernels = 1);
 
 }  // namespace qpic
+
+// return early from an entry point whose context belongs to another device
+#define QPIC_REQUIRE_DEVICE(c)                                                         \
+    do {                                                                               \
+        qpic_status _s = qpic::check_device(c);                                        \
+        if (_s != QPIC_OK) return _s;                                                  \
+    } while (0)
 
 #define QPIC_CUDA_OK(c, call)                                                          \
     do {                                                                               \

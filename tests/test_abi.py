@@ -74,10 +74,11 @@ def test_reduced_model_argument_checks_without_a_gpu():
     when no GPU is present"""
     import math
     L = q.load()
-    ok = (1.0, 0.1, 0.04, 1.0, 0.0, 0.1, 1)                 # a0, w_p, k_perp, v_phi, t0, dt, nsteps
+    ok = (1.0, 0.1, 0.04, 1.0, 1.0, 0.0, 0.1, 1, None)     # a0, w_p, k_perp, v_phi, bfac, t0, dt, nsteps, start
     assert L.qpic_reduced_integrate(0, None, None, None, None, *ok) == 0
     assert L.qpic_reduced_integrate(-1, None, None, None, None, *ok) == -1
-    for k, bad in ((3, -1.0), (3, 0.0), (4, math.nan), (5, 0.0), (5, math.inf), (2, -0.1), (6, -1)):
+    for k, bad in ((3, -1.0), (3, 0.0), (5, math.nan), (6, 0.0), (6, math.inf), (2, -0.1), (7, -1),
+                   (4, math.inf)):
         args = list(ok)
         args[k] = bad
         assert L.qpic_reduced_integrate(0, None, None, None, None, *args) == -1, (k, bad)

@@ -2,10 +2,11 @@
 
 It exists for callers that cannot allocate device memory during the call, for
 example hosts with a fixed device-memory budget or code running inside a
-device allocator's callbacks.  Its result must
-equal the allocating path (qpic_get_field with QPIC_FIELD_RHO) -- on two calls
-in a row, so a second call does not add onto what the first left in the shared
-static array -- and grids too large for the static array are refused.
+device allocator's callbacks.  Its result must equal the allocating path
+(qpic_get_field with QPIC_FIELD_RHO) -- on two calls in a row, so a second call
+does not add onto what the first left in the shared static array -- on the
+FP32 fixed-point path and the plain FP64 path, and grids too large for the
+static array are refused.
 
 This file is named to be collected last: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -27,8 +28,9 @@ def _noalloc(sim, mode):
     return st, re + 1j * im
 
 
-def test_noalloc_matches_allocating_path_twice():
-    sim = q.Sim(96, 20, 0.2, 0.5, n_modes=2, dt=0.13)
+@pytest.mark.parametrize("precision", [q.QPIC_FP32_FIXED, q.QPIC_FP64])
+def test_noalloc_matches_allocating_path_twice(precision):
+    sim = q.Sim(96, 20, 0.2, 0.5, n_modes=2, dt=0.13, precision=precision)
     sim.load_plasma(0.01, 0.0, 0.0, (2, 2, 4))
     sim.add_laser(1.0, 4.0, 6.0, 9.6, 9.6)
     sim.step(3)
