@@ -25,14 +25,19 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the oracle's C core with plain gcc (strict IEEE FP64, no fast-math)."""
+    """Compile the oracle's C core with plain gcc (strict IEEE FP64, no
+    fast-math), with OpenMP when the compiler has it (the serial result is the
+    same either way; see or_set_partitions)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                           "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,6 +76,8 @@ def _declare(L):
     L.or_deposit_rho.argtypes = [_VP, _D, _D]
     L.or_shift_window.argtypes = [_VP]
     L.or_compact.argtypes = [_VP]
+    L.or_set_partitions.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+    L.or_has_openmp.restype = ctypes.c_int
 
 
 def _p(a):
@@ -87,7 +94,7 @@ class Oracle:
     m >= 1); 2 the directional work of Eq. 17 (W0 = W_z, W1 = W_perp)."""
 
     def __init__(self, nz, nr, n_modes, dz, dr, dt, cE, cB, ktaps=None,
-                 periodic=True, track_work=False):
+                 periodic=True, track_work=False, partitions=1, threads=0):
         cE = np.ascontiguousarray(cE, dtype=np.float64)
         cB = np.ascontiguousarray(cB, dtype=np.float64)
         kt = np.ascontiguousarray(ktaps if ktaps is not None else np.zeros(1), dtype=np.float64)
@@ -101,6 +108,19 @@ class Oracle:
                                   nk, _p(kt), int(periodic), int(track_work))
         if not self.h:
             raise ValueError("oracle: bad configuration")
+        if partitions > 1 or threads > 0:
+            self.set_partitions(partitions, threads)
+
+    def set_partitions(self, partitions, threads=0):
+        """Deposit the particles in `partitions` fixed ranges (in parallel when
+        the library has OpenMP; `threads` > 0 sets the thread count) and sum
+        the range currents node by node in range order: the result depends on
+        the number of ranges, not on the number of threads.  1 = serial."""
+        self.L.or_set_partitions(self.h, int(partitions), int(threads))
+
+    @staticmethod
+    def has_openmp():
+        return bool(lib().or_has_openmp())
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -27,6 +27,13 @@
  *   charge-conserving deposit of J^{n+1/2} per mode
  *   J_z <- K * J_z (dual solver only); E^n -> E^{n+1}        (Ampere)
  *
+ * Threads: with or_set_partitions(s, P > 1) the particles are split into P
+ * fixed contiguous ranges, each pushed and deposited into its own current
+ * buffer, and the buffers are summed node by node in range order.  The result
+ * then depends on P but not on how many OpenMP threads run the ranges (the
+ * current is a sum over particles; the ranges only fix its order).  Field
+ * updates are independent per node and match the serial ones bit for bit.
+ *
  * Parity pins for each function are in tests/test_oracle_*.py.
  */
 #define _USE_MATH_DEFINES
@@ -35,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -59,6 +69,8 @@ typedef struct {
     int track_work;
     double zmin;               /* lab z of logical cell 0 */
     cplx *E, *B, *Bb, *J;      /* [comp][mode][j=0..nr][i=0..nz-1] */
+    int nparts;                /* particle ranges deposited separately (1: serial) */
+    cplx *Jp;                  /* nparts current buffers when nparts > 1 */
     long np, cap;
     double *z, *x, *y, *ux, *uy, *uz, *w, *W0, *W1;
 } ostate;
@@ -83,13 +95,37 @@ ostate *or_create(int nz, int nr, int nm, double dz, double dr, double dt,
     size_t n = (size_t)3 * nm * (nr + 1) * nz;
     s->E = (cplx *)calloc(n, sizeof(cplx)); s->B = (cplx *)calloc(n, sizeof(cplx));
     s->Bb = (cplx *)calloc(n, sizeof(cplx)); s->J = (cplx *)calloc(n, sizeof(cplx));
+    s->nparts = 1;
     return s;
+}
+
+/* number of particle ranges deposited separately (1: serial, the default) and,
+ * when OpenMP is available, the number of threads (<= 0: leave it) */
+void or_set_partitions(ostate *s, int nparts, int nthreads)
+{
+    if (nparts < 1) nparts = 1;
+    if (nparts != s->nparts) { free(s->Jp); s->Jp = NULL; s->nparts = nparts; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* 1 when the library was built with OpenMP */
+int or_has_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 void or_destroy(ostate *s)
 {
     if (!s) return;
-    free(s->E); free(s->B); free(s->Bb); free(s->J);
+    free(s->E); free(s->B); free(s->Bb); free(s->J); free(s->Jp);
     free(s->z); free(s->x); free(s->y); free(s->ux); free(s->uy); free(s->uz);
     free(s->w); free(s->W0); free(s->W1);
     free(s);
@@ -202,6 +238,7 @@ void or_faraday(ostate *s)
     size_t n = (size_t)3 * s->nm * (nr + 1) * nz;
     cplx *Bn = (cplx *)malloc(n * sizeof(cplx));
     memcpy(Bn, s->B, n * sizeof(cplx));
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int m = 0; m < s->nm; m++) {
         for (int j = 0; j <= nr; j++) {
             double rj = j * dr, rh = (j + 0.5) * dr;
@@ -242,9 +279,10 @@ static void filter_jz(ostate *s)
 {
     if (s->nk <= 0) return;
     const int nz = s->nz;
-    cplx *tmp = (cplx *)malloc((size_t)nz * sizeof(cplx));
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int m = 0; m < s->nm; m++)
         for (int j = 0; j <= s->nr; j++) {
+            cplx *tmp = (cplx *)malloc((size_t)nz * sizeof(cplx));
             for (int i = 0; i < nz; i++) {
                 cplx acc = s->kt[0] * s->J[fidx(s, CZ, m, j, i)];
                 for (int q = 1; q < s->nk; q++)
@@ -252,8 +290,8 @@ static void filter_jz(ostate *s)
                 tmp[i] = acc;
             }
             for (int i = 0; i < nz; i++) s->J[fidx(s, CZ, m, j, i)] = tmp[i];
+            free(tmp);
         }
-    free(tmp);
 }
 
 /* dE/dt = curl B - J per mode:
@@ -268,6 +306,7 @@ void or_ampere(ostate *s)
     const int nz = s->nz, nr = s->nr;
     const double dt = s->dt, dr = s->dr;
     filter_jz(s);
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int m = 0; m < s->nm; m++) {
         for (int j = 0; j <= nr; j++) {
             double rj = j * dr, rh = (j + 0.5) * dr, rl = (j - 0.5) * dr;
@@ -397,11 +436,11 @@ static double cvol(const ostate *s, int j)
     return 2.0 * M_PI * j * dr * dr * dz;
 }
 
-static void addJ(ostate *s, int c, int m, int j, int i, cplx v)
+static void addJ(const ostate *s, cplx *J, int c, int m, int j, int i, cplx v)
 {
     int k = zwrap(s, i);
     if (k < 0 || j < 0 || j > s->nr) return;
-    s->J[fidx(s, c, m, j, k)] += v;
+    J[fidx(s, c, m, j, k)] += v;
 }
 
 /* Charge-conserving deposit of one particle move (z0,r0,phi0) -> (z1,r1,phi1),
@@ -410,8 +449,8 @@ static void addJ(ostate *s, int c, int m, int j, int i, cplx v)
  *   (S1 - S0) (e0+e1)/2   -> r and z fluxes by the 2D Esirkepov decomposition
  *   (S0 + S1)/2 (e1 - e0)  -> J_phi through (i m / r_j) J_phi V_j = -dQ/dt.
  * For m = 0, J_phi = Q v_phi Sbar / V with v_phi at the mid-point of the move. */
-static void deposit_one(ostate *s, double Q, double zc0, double rc0, double zc1, double rc1,
-                        double c0, double s0, double c1, double s1, double vphi)
+static void deposit_one(const ostate *s, cplx *J, double Q, double zc0, double rc0, double zc1,
+                        double rc1, double c0, double s0, double c1, double s1, double vphi)
 {
     const double dt = s->dt, dz = s->dz, dr = s->dr;
     int ilo = (int)floor(fmin(zc0, zc1)), jlo = (int)floor(fmin(rc0, rc1));
@@ -441,7 +480,7 @@ static void deposit_one(ostate *s, double Q, double zc0, double rc0, double zc1,
             for (int a = 0; a < nzs - 1; a++) {
                 acc += Wz[a][b];
                 cplx flux = -(Q / dt) * acc * ebar;               /* charge per time */
-                addJ(s, CZ, m, j, ilo + a, flux * dz / cvol(s, j));
+                addJ(s, J, CZ, m, j, ilo + a, flux * dz / cvol(s, j));
             }
         }
         /* r fluxes through faces (i, j+1/2): prefix sums of W^r along r */
@@ -452,7 +491,7 @@ static void deposit_one(ostate *s, double Q, double zc0, double rc0, double zc1,
                 acc += Wr[a][b];
                 if (j < 0 || j >= s->nr) continue;
                 cplx flux = -(Q / dt) * acc * ebar;
-                addJ(s, CR, m, j, ilo + a, flux / (2.0 * M_PI * (j + 0.5) * dr * dz));
+                addJ(s, J, CR, m, j, ilo + a, flux / (2.0 * M_PI * (j + 0.5) * dr * dz));
             }
         }
         /* azimuthal current at nodes (i, j) */
@@ -463,7 +502,7 @@ static void deposit_one(ostate *s, double Q, double zc0, double rc0, double zc1,
                 cplx v;
                 if (m == 0) v = Q * vphi * Sb[a][b] / cvol(s, j);
                 else v = I * (j * dr) * Q * Sb[a][b] * de / ((double)m * cvol(s, j) * dt);
-                addJ(s, CP, m, j, ilo + a, v);
+                addJ(s, J, CP, m, j, ilo + a, v);
             }
     }
 }
@@ -505,77 +544,100 @@ void or_deposit_rho(ostate *s, double *re, double *im)
  * Move in Cartesian x, y, then (r, phi) from the new position.  A particle
  * beyond the conducting wall is reflected specularly.  In an open box a
  * particle leaving [0, nz dz) is removed (weight set to 0 after its deposit). */
-void or_push_deposit(ostate *s)
+static void push_one(ostate *s, long p, cplx *J)
 {
     const double dt = s->dt, q = -1.0;
     const double R = s->nr * s->dr;
-    size_t n = (size_t)3 * s->nm * (s->nr + 1) * s->nz;
+    if (s->w[p] == 0.0) return;
+    double z0 = s->z[p], x0 = s->x[p], y0 = s->y[p];
+    double r0 = hypot(x0, y0);
+    double c0 = r0 > 0 ? x0 / r0 : 1.0, s0 = r0 > 0 ? y0 / r0 : 0.0;
+    double zc0 = (z0 - s->zmin) / s->dz, rc0 = r0 / s->dr;
+    double e[6], b[6];
+    gather_one(s, s->E, 0, zc0, rc0, c0, s0, e);
+    gather_one(s, s->Bb, 1, zc0, rc0, c0, s0, b);
+    double u[3] = { s->ux[p], s->uy[p], s->uz[p] };
+    double g_old = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double um[3], up[3], t[3], sv[3], uprime[3];
+    for (int k = 0; k < 3; k++) um[k] = u[k] + 0.5 * q * dt * e[k];
+    double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    for (int k = 0; k < 3; k++) t[k] = 0.5 * q * dt * b[k] / gm;
+    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int k = 0; k < 3; k++) sv[k] = 2.0 * t[k] / (1.0 + t2);
+    uprime[0] = um[0] + um[1] * t[2] - um[2] * t[1];
+    uprime[1] = um[1] + um[2] * t[0] - um[0] * t[2];
+    uprime[2] = um[2] + um[0] * t[1] - um[1] * t[0];
+    up[0] = um[0] + uprime[1] * sv[2] - uprime[2] * sv[1];
+    up[1] = um[1] + uprime[2] * sv[0] - uprime[0] * sv[2];
+    up[2] = um[2] + uprime[0] * sv[1] - uprime[1] * sv[0];
+    for (int k = 0; k < 3; k++) up[k] += 0.5 * q * dt * e[k];
+    double g = sqrt(1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+    double vx = up[0] / g, vy = up[1] / g, vz = up[2] / g;
+    if (s->track_work) {
+        /* v at time n: the mean of u/gamma at n -+ 1/2 */
+        double vn[3] = { 0.5 * (u[0] / g_old + vx), 0.5 * (u[1] / g_old + vy), 0.5 * (u[2] / g_old + vz) };
+        if (s->track_work == 2) {
+            /* Eq. 17: W_z += q dt E_z v_z, W_perp += q dt E_perp . v_perp (all modes) */
+            s->W0[p] += q * dt * (e[2] * vn[2]);
+            s->W1[p] += q * dt * (e[0] * vn[0] + e[1] * vn[1]);
+        } else {
+            /* Eq. 16: W_m += q dt E^m . v; W0 holds m = 0, W1 the modes m >= 1 */
+            double w0 = e[3] * vn[0] + e[4] * vn[1] + e[5] * vn[2];
+            double wt = e[0] * vn[0] + e[1] * vn[1] + e[2] * vn[2];
+            s->W0[p] += q * dt * w0;
+            s->W1[p] += q * dt * (wt - w0);
+        }
+    }
+    double x1 = x0 + dt * vx, y1 = y0 + dt * vy, z1 = z0 + dt * vz;
+    double r1 = hypot(x1, y1);
+    if (r1 > R) {                       /* specular reflection at the wall */
+        double cr = x1 / r1, sr = y1 / r1;
+        double urad = up[0] * cr + up[1] * sr;
+        up[0] -= 2.0 * urad * cr; up[1] -= 2.0 * urad * sr;
+        double rn = 2.0 * R - r1;
+        x1 = cr * rn; y1 = sr * rn; r1 = rn;
+    }
+    double c1 = r1 > 0 ? x1 / r1 : c0, s1 = r1 > 0 ? y1 / r1 : s0;
+    /* mid-point azimuthal velocity for the m = 0 J_phi */
+    double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1), rm = hypot(xm, ym);
+    double vphi = rm > 0 ? (xm * (y1 - y0) - ym * (x1 - x0)) / (rm * dt) : 0.0;
+    double zc1 = (z1 - s->zmin) / s->dz, rc1 = r1 / s->dr;
+    deposit_one(s, J, q * s->w[p], zc0, rc0, zc1, rc1, c0, s0, c1, s1, vphi);
+    s->z[p] = z1; s->x[p] = x1; s->y[p] = y1;
+    s->ux[p] = up[0]; s->uy[p] = up[1]; s->uz[p] = up[2];
+    if (s->periodic) {
+        double Lz = s->nz * s->dz;
+        double zrel = s->z[p] - s->zmin;
+        if (zrel < 0) s->z[p] += Lz; else if (zrel >= Lz) s->z[p] -= Lz;
+    } else if (zc1 < 0.0 || zc1 >= s->nz) {
+        s->w[p] = 0.0;                  /* left the open box */
+    }
+}
+
+void or_push_deposit(ostate *s)
+{
+    const size_t n = (size_t)3 * s->nm * (s->nr + 1) * s->nz;
     memset(s->J, 0, n * sizeof(cplx));
-    for (long p = 0; p < s->np; p++) {
-        if (s->w[p] == 0.0) continue;
-        double z0 = s->z[p], x0 = s->x[p], y0 = s->y[p];
-        double r0 = hypot(x0, y0);
-        double c0 = r0 > 0 ? x0 / r0 : 1.0, s0 = r0 > 0 ? y0 / r0 : 0.0;
-        double zc0 = (z0 - s->zmin) / s->dz, rc0 = r0 / s->dr;
-        double e[6], b[6];
-        gather_one(s, s->E, 0, zc0, rc0, c0, s0, e);
-        gather_one(s, s->Bb, 1, zc0, rc0, c0, s0, b);
-        double u[3] = { s->ux[p], s->uy[p], s->uz[p] };
-        double g_old = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        double um[3], up[3], t[3], sv[3], uprime[3];
-        for (int k = 0; k < 3; k++) um[k] = u[k] + 0.5 * q * dt * e[k];
-        double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-        for (int k = 0; k < 3; k++) t[k] = 0.5 * q * dt * b[k] / gm;
-        double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-        for (int k = 0; k < 3; k++) sv[k] = 2.0 * t[k] / (1.0 + t2);
-        uprime[0] = um[0] + um[1] * t[2] - um[2] * t[1];
-        uprime[1] = um[1] + um[2] * t[0] - um[0] * t[2];
-        uprime[2] = um[2] + um[0] * t[1] - um[1] * t[0];
-        up[0] = um[0] + uprime[1] * sv[2] - uprime[2] * sv[1];
-        up[1] = um[1] + uprime[2] * sv[0] - uprime[0] * sv[2];
-        up[2] = um[2] + uprime[0] * sv[1] - uprime[1] * sv[0];
-        for (int k = 0; k < 3; k++) up[k] += 0.5 * q * dt * e[k];
-        double g = sqrt(1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
-        double vx = up[0] / g, vy = up[1] / g, vz = up[2] / g;
-        if (s->track_work) {
-            /* v at time n: the mean of u/gamma at n -+ 1/2 */
-            double vn[3] = { 0.5 * (u[0] / g_old + vx), 0.5 * (u[1] / g_old + vy), 0.5 * (u[2] / g_old + vz) };
-            if (s->track_work == 2) {
-                /* Eq. 17: W_z += q dt E_z v_z, W_perp += q dt E_perp . v_perp (all modes) */
-                s->W0[p] += q * dt * (e[2] * vn[2]);
-                s->W1[p] += q * dt * (e[0] * vn[0] + e[1] * vn[1]);
-            } else {
-                /* Eq. 16: W_m += q dt E^m . v; W0 holds m = 0, W1 the modes m >= 1 */
-                double w0 = e[3] * vn[0] + e[4] * vn[1] + e[5] * vn[2];
-                double wt = e[0] * vn[0] + e[1] * vn[1] + e[2] * vn[2];
-                s->W0[p] += q * dt * w0;
-                s->W1[p] += q * dt * (wt - w0);
-            }
-        }
-        double x1 = x0 + dt * vx, y1 = y0 + dt * vy, z1 = z0 + dt * vz;
-        double r1 = hypot(x1, y1);
-        if (r1 > R) {                       /* specular reflection at the wall */
-            double cr = x1 / r1, sr = y1 / r1;
-            double urad = up[0] * cr + up[1] * sr;
-            up[0] -= 2.0 * urad * cr; up[1] -= 2.0 * urad * sr;
-            double rn = 2.0 * R - r1;
-            x1 = cr * rn; y1 = sr * rn; r1 = rn;
-        }
-        double c1 = r1 > 0 ? x1 / r1 : c0, s1 = r1 > 0 ? y1 / r1 : s0;
-        /* mid-point azimuthal velocity for the m = 0 J_phi */
-        double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1), rm = hypot(xm, ym);
-        double vphi = rm > 0 ? (xm * (y1 - y0) - ym * (x1 - x0)) / (rm * dt) : 0.0;
-        double zc1 = (z1 - s->zmin) / s->dz, rc1 = r1 / s->dr;
-        deposit_one(s, q * s->w[p], zc0, rc0, zc1, rc1, c0, s0, c1, s1, vphi);
-        s->z[p] = z1; s->x[p] = x1; s->y[p] = y1;
-        s->ux[p] = up[0]; s->uy[p] = up[1]; s->uz[p] = up[2];
-        if (s->periodic) {
-            double Lz = s->nz * s->dz;
-            double zrel = s->z[p] - s->zmin;
-            if (zrel < 0) s->z[p] += Lz; else if (zrel >= Lz) s->z[p] -= Lz;
-        } else if (zc1 < 0.0 || zc1 >= s->nz) {
-            s->w[p] = 0.0;                  /* left the open box */
-        }
+    if (s->nparts <= 1) {
+        for (long p = 0; p < s->np; p++) push_one(s, p, s->J);
+        return;
+    }
+    const int P = s->nparts;
+    if (!s->Jp) s->Jp = (cplx *)malloc((size_t)P * n * sizeof(cplx));
+    /* range k: particles [k np / P, (k+1) np / P) into buffer k */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < P; k++) {
+        cplx *Jk = s->Jp + (size_t)k * n;
+        memset(Jk, 0, n * sizeof(cplx));
+        const long p0 = (long)((long long)s->np * k / P), p1 = (long)((long long)s->np * (k + 1) / P);
+        for (long p = p0; p < p1; p++) push_one(s, p, Jk);
+    }
+    /* node by node, in range order */
+    #pragma omp parallel for schedule(static)
+    for (long long q = 0; q < (long long)n; q++) {
+        cplx acc = s->Jp[q];
+        for (int k = 1; k < P; k++) acc += s->Jp[(size_t)k * n + q];
+        s->J[q] = acc;
     }
 }
 
