@@ -40,6 +40,31 @@ GPD_BYTES_PER_PARTICLE = 68.0
 GPD_BYTES_PER_CELL = 72.0 + 144.0
 
 
+def kernel_bytes(name, w, particles, launches, nkeys, tile=(16, 8)):
+    """Algorithmic bytes one kernel class moves over `launches` launches (FP32
+    path, np = 2M+1 mode parts, cells = nz nr):
+    - faraday: read E, B; write B, Bbar: 4 x 12 np B per cell;
+    - ampere: read E, B, J; write E: 4 x 12 np B per cell;
+    - jz_filter: read and write J_z: 2 x 4 np B per cell;
+    - j_decode: read the int64 tile blocks that cover a cell (3 np words per node,
+      (TZ+5)(TR+5) nodes per TZ x TR tile) and write the FP32 current (12 np B);
+    - gather_push_deposit: 68 B per particle + 216 B per cell (as above);
+    - sort: per sort, 76 B per particle (cell read twice, record read and
+      written, cell written) and 24 B per key (counts and offsets passes)."""
+    np_ = 2 * w["n_modes"] - 1
+    cells = w["nz"] * w["nr"]
+    tz, tr = tile
+    per = {
+        "faraday": 48.0 * np_ * cells,
+        "ampere": 48.0 * np_ * cells,
+        "jz_filter": 8.0 * np_ * cells,
+        "j_decode": (24.0 * np_ * (tz + 5) * (tr + 5) / (tz * tr) + 12.0 * np_) * cells,
+        "gather_push_deposit": GPD_BYTES_PER_PARTICLE * particles + GPD_BYTES_PER_CELL * cells,
+        "sort": 76.0 * particles + 24.0 * nkeys,
+    }
+    return per[name] * launches if name in per else None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -234,17 +259,19 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
             "speedup": seq_ms / bat_ms, "unit": "particle-steps/s"}
 
 
-def oracle_sample(w, dt, nz_sample, steps):
+def oracle_sample(w, dt, nz_sample, steps, threads=1):
     """The FP64 oracle, as it stands, on a z-slab of the workload: the same
-    nr, dz, dr, dt, plasma and ppc over nz_sample columns (periodic).  Returns
-    (particle-steps/s, particles, seconds)."""
+    nr, dz, dr, dt, plasma and ppc over nz_sample columns (periodic).  With
+    threads > 1 its multi-threaded mode (4 particle ranges per thread).
+    Returns (particle-steps/s, particles, seconds)."""
     import oracle
     from oracle import coeffs as C
     from oracle import setup as S
     pl = w["plasma"]
     cE, cB = C.solver_coefficients(w["solver"], dt, w["dz"])
     o = oracle.Oracle(nz_sample, w["nr"], w["n_modes"], w["dz"], w["dr"], dt, cE, cB,
-                      C.filter_taps(cB), periodic=True)
+                      C.filter_taps(cB), periodic=True,
+                      partitions=4 * threads if threads > 1 else 1, threads=threads)
     # the slab sits on the plateau of the profile (z_start + ramp onwards)
     first = int(np.ceil((pl["z_start"] + pl["ramp_len"]) / w["dz"]))
     p = S.plasma_cells(np.arange(first, first + nz_sample), w["nr"], w["dz"], w["dr"],
@@ -295,8 +322,10 @@ def run_reference(args, w):
     from oracle import coeffs as C
     dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], w["nr"], w["n_modes"], w["solver"])
     nz_s = args.ref_nz
-    oracle_sample(w, dt, nz_s, max(1, args.warmup))      # warm-up (untimed)
-    rate, n, t = oracle_sample(w, dt, nz_s, args.steps)
+    import oracle
+    nth = (os.cpu_count() or 1) if oracle.Oracle.has_openmp() else 1
+    oracle_sample(w, dt, nz_s, max(1, args.warmup), threads=nth)      # warm-up (untimed)
+    rate, n, t = oracle_sample(w, dt, nz_s, args.steps, threads=nth)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "particle-steps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -305,9 +334,10 @@ def run_reference(args, w):
         "config": dict(_config(args, w, ws), dt=dt,
                        sample="each step: a periodic z-slab of %d of the %d columns (%d particles)"
                               % (nz_s, w["nz"], n)),
-        "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d steps of a %d x %d periodic slab (%d particles)"
-                                   % (args.steps, nz_s, w["nr"], n)},
+        "cpu_baseline": {"value": rate, "unit": "particle-steps/s", "cores": nth, "kind": "oracle",
+                         "sample": "%d steps of a %d x %d periodic slab (%d particles)%s"
+                                   % (args.steps, nz_s, w["nr"], n,
+                                      ", OpenMP over %d particle ranges" % (4 * nth) if nth > 1 else "")},
         "e2e": {"value": rate, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -373,16 +403,24 @@ def run_ours(args, w):
     cells = w["nz"] * w["nr"]
     cell_updates = ws * cells * args.steps / (ms_max / 1e3)
 
-    # ---- per-kernel times (a second, profiled run of the same steps)
+    # ---- per-kernel times: a second run of the same kind of steps with CUDA
+    # events around every kernel class.  Its launches are queued behind a GPU
+    # sleep, so no host delay falls between a pair of events; the per-class
+    # times then add up to no more than the pass itself.
     sim.profile(True, True)
+    torch.cuda._sleep(int(2e8))
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
     sim.step(args.prof_steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_total_ms = p0.elapsed_time(p1)
     kt = sim.kernel_times()
     sim.profile(False, True)
     dt_used = sim.dt
     gpd_ms, gpd_n = kt["gather_push_deposit"]
     gpd_avg = gpd_ms / max(gpd_n, 1)
     solver_ms = sum(kt[k][0] for k in ("faraday", "j_decode", "jz_filter", "ampere"))
-    step_prof_ms = sum(v[0] for v in kt.values())
     ppc = int(np.prod(w["plasma"]["ppc"]))
     gpd_bytes = n_avg * (GPD_BYTES_PER_PARTICLE + GPD_BYTES_PER_CELL / ppc)
     peaks = _peaks()
@@ -392,7 +430,18 @@ def run_ours(args, w):
         hbm, peak_src = 6800.0, "fallback"
     achieved = gpd_bytes / (gpd_avg / 1e3) / 1e9
     traffic = _measured_traffic(args.workload, q.KERNEL_REV)
-
+    nkeys = -(-w["nz"] // 16) * 16 * (-(-w["nr"] // 8) * 8)     # sort keys: cells rounded up to whole tiles
+    kernels = {}
+    for k, (kms, kn) in kt.items():
+        if not kn:
+            continue
+        b = kernel_bytes(k, w, n_avg, kn, nkeys)
+        ent = {"ms_per_step": kms / max(args.prof_steps, 1), "launches": int(kn)}
+        if b is not None and kms > 0:
+            gbs = b / (kms / 1e3) / 1e9
+            ent.update({"algorithmic_bytes_per_launch": b / kn, "achieved_gbs": gbs,
+                        "frac_of_measured_hbm": gbs / hbm})
+        kernels[k] = ent
     # ---- end to end through the C ABI with host buffers (rank-local)
     e2e = None
     if not args.no_e2e:
@@ -529,12 +578,22 @@ def run_ours(args, w):
 
     # ---- CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
     cpu = None
+    cpu_all = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         rate, n, t = oracle_sample(w, dt_used, args.ref_nz, args.cpu_steps)
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                "sample": "%d steps of a %d x %d periodic z-slab of the workload (%d particles), "
                          "single-threaded FP64 C, %.1f s" % (args.cpu_steps, args.ref_nz, w["nr"], n, t),
                "host": _host_cpu()}
+        nth = os.cpu_count() or 1
+        if nth > 1:
+            import oracle
+            if oracle.Oracle.has_openmp():
+                steps_all = max(args.cpu_steps, 4 * args.cpu_steps * min(nth, 16) // 16)
+                rate, n, t = oracle_sample(w, dt_used, args.ref_nz, steps_all, threads=nth)
+                cpu_all = {"value": rate, "unit": "particle-steps/s", "cores": nth, "kind": "oracle",
+                           "sample": "%d steps of the same slab (%d particles), FP64 C with OpenMP over "
+                                     "%d particle ranges, %.1f s" % (steps_all, n, 4 * nth, t)}
 
     if rank == 0:
         line = {
@@ -548,7 +607,11 @@ def run_ours(args, w):
             "cell_updates_per_s": cell_updates,
             "solver_cell_updates_per_s": cells * args.prof_steps / (solver_ms / 1e3) if solver_ms else None,
             "gpd_particle_steps_per_s": n_avg / (gpd_avg / 1e3),
-            "kernel_ms_per_step": {k: v[0] / max(args.prof_steps, 1) for k, v in kt.items() if v[1]},
+            "kernels": kernels,
+            "kernel_pass": {"steps": args.prof_steps, "ms_per_step": prof_total_ms / max(args.prof_steps, 1),
+                            "kernels_ms_per_step_sum": sum(v["ms_per_step"] for v in kernels.values()),
+                            "note": "per-kernel times from CUDA events in a second pass of the same steps, "
+                                    "its launches queued behind a GPU sleep"},
             "roofline": {"kernel": "gather_push_deposit", "bound": "hbm", "achieved": achieved,
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "peak_source": peak_src + " (hbm_gbs, burst)",
@@ -557,7 +620,8 @@ def run_ours(args, w):
             "fp32_float_atomic_path": fatomic, "work_tracking_path": work, "reduced_model_path": reduced,
             "batch_scan": batch,
             "fp32_over_fp64": (value / ws / fp64["value"]) if fp64 else None,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches,
         }
         print(json.dumps(line))
     if ws > 1:

@@ -157,9 +157,9 @@ float *field_base(qpic_ctx *c, int which)
 void set_qscale(qpic_ctx *c, double qmax)
 {
     c->qref = qmax > 0 ? qmax : 1.0;
-    // per-particle contributions stay below ~2 qref, i.e. 2^41 units: the
-    // exact FP32 split of the deposit handles up to 2^42, and int64 keeps
-    // 2^21 particles' worth of headroom per accumulator
+    // per-particle contributions stay below 2 qref, i.e. 2^41 units: the exact
+    // FP32 hi 2^21 + lo split of the deposit handles them, and int64 keeps
+    // 2^21 contributions of the largest size per accumulator
     c->qscale = (float)(1099511627776.0 / c->qref);        // 2^40 / qref
 }
 
@@ -960,6 +960,13 @@ qpic_status qpic_profile(qpic_ctx *c, int32_t enable, int32_t reset)
     if (!c) return QPIC_EINVAL;
     resolve_events(c);
     c->profile = enable != 0;
+    // events are created up front: creating them between launches would hold
+    // the host back and leave gaps on the GPU inside the timed pairs
+    while (c->profile && c->ev_pool.size() < 4096) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); break; }
+        c->ev_pool.push_back(e);
+    }
     if (reset) {
         for (int k = 0; k < KC_COUNT; k++) { c->kms[k] = 0.0; c->klaunch[k] = 0; }
     }

@@ -11,14 +11,21 @@
 //      (Eq. 6 time-centred as in Eq. 12); Cartesian move and an update of
 //      (r, cos phi, sin phi) written with cancellation-free differences;
 //      optional modal work (Eq. 16).
-//   3. charge-conserving deposit per mode into int64 fixed-point shared
-//      accumulators.  The modal charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
+//   3. charge-conserving deposit per mode into fixed-point shared
+//      accumulators: each int64 contribution v is added as two int32 parts,
+//      hi = round(v 2^-21) and lo = v - hi 2^21, to two int32 planes (32-bit
+//      shared atomics are several times faster than 64-bit ones); after every
+//      chunk of at most 2047 particles the planes are drained into an int64
+//      plane, so their sums never leave the int32 range.  The modal charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
 //      splits into (S1 - S0)(e0 + e1)/2, carried by 2D Esirkepov r/z fluxes,
 //      and (S0 + S1)/2 (e1 - e0), carried by J_phi through (i m / r) J_phi.
-//      Moves inside a cell are summed in registers per thread (FastSum) and
-//      added once per run of moves; moves across cells are queued and
-//      deposited once per tile.
-//   4. the tile's accumulators are stored to its own block of global memory;
+//      Each thread takes runs of consecutive particles of the tile (sorted by
+//      cell), so its moves inside one cell are summed in registers (FastSum)
+//      and added once per cell; moves across cells are queued and deposited
+//      once per tile.  One thread asks L2 for the tile's particles (bulk
+//      prefetch) before the fields are staged.
+//   4. the tile's accumulators are stored to its own block of global memory
+//      as int64 (hi 2^21 + lo);
 //      k_jreduce sums the blocks that cover each node.  Integer addition makes
 //      the step independent of particle order (bit-reproducible).
 //   Particles beyond the staged halo (drift between sorts, or injected by the
@@ -111,6 +118,17 @@ __device__ __forceinline__ float gsample_at(const float *E, const float *Bb, con
     return sgn * F[(size_t)(c * a.nparts + p) * a.plane + (size_t)j * a.nzp + ic];
 }
 
+// Fixed point of the current: a contribution x becomes v = round(x qscale)
+// with qscale = 2^40 / (largest particle charge), so |v| < 2^41 (the largest
+// factor of a charge in the deposit is 2).  v is split as hi 2^21 + lo with
+// |hi|, |lo| <= 2^20: two int32 sums hold 2^11 contributions of the largest
+// size without wrapping: a particle contributes at most once to a node, so
+// the planes are drained into int64 after every chunk of at most 2047
+// particles (GPD_C) and after the queued moves (at most QCAP).
+constexpr int FX_SHIFT = 21;
+constexpr float FX_DOWN = 4.76837158203125e-07f;  // 2^-21
+constexpr float FX_UP = 2097152.0f;               // 2^21
+
 // ------------------------------------------------------------ accessors
 // Staged tile of E and Bbar: per (field, component, row, column) node the NP
 // mode parts are packed in V = ceil(NP/4) float4 words, so a gather corner is
@@ -122,23 +140,25 @@ struct TileGeom {
     static constexpr int FW = TZ + 2 * H + 2, FR = TR + 2 * H + 2;   // staged fields
     static constexpr int JW = FW + 1, JR = FR + 1;                   // accumulators
     static constexpr int V = (NP + 3) / 4;
-    static constexpr int JWORDS = 3 * NP * JW * JR;                   // int64 words
-    static constexpr int JPAD = (JWORDS + 1) & ~1;                    // keeps the float4 tile 16-B aligned
+    static constexpr int JWORDS = 3 * NP * JW * JR;                   // accumulated values (int64 each)
+    static constexpr int JPAD = (JWORDS + 3) & ~3;                    // per int32 plane; keeps the float4 tile 16-B aligned
     static constexpr int FVEC = 2 * 3 * FR * FW * V;                  // float4 words
     static constexpr int NM = (NP + 1) / 2;
     static constexpr int QW = 8 + 4 * (NM - 1);                       // words per queued move
     static constexpr int QCAP = 512;                                  // queued cell-crossing moves
     static constexpr int PB = 9 * 256;      // prefetched words per buffer: 256 cells, 2 x 256 float4
-    static constexpr size_t SMEM =
-        (size_t)JPAD * 8 + (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
+    static constexpr size_t SMEM = (size_t)JPAD * 8 /* hi, lo int32 planes */ + (size_t)JPAD * 8 /* int64 plane */ +
+                                   (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
     static_assert((JPAD * 8) % 16 == 0, "float4 tile alignment");
+    // particles one thread handles between flushes of its register sums: the
+
 };
 
 template <int NP, int TZ, int TR>
 struct SmemAcc {
     using G = TileGeom<NP, TZ, TR>;
     const float4 *sf;            // [2][3][FR][FW][V]
-    unsigned long long *sJ;      // [3][NP][JR][JW]
+    unsigned *sJh, *sJl;         // hi and lo planes, each [3][NP][JR][JW]
     __device__ __forceinline__ void node(int fb, int c, int lj, int li, float out[NP]) const
     {
         const float4 *q = sf + ((size_t)((fb * 3 + c) * G::FR + lj) * G::FW + li) * G::V;
@@ -152,9 +172,11 @@ struct SmemAcc {
         }
     }
     float qs;                    // fixed-point scale
-    __device__ __forceinline__ void jadd(int c, int p, int lj, int li, long long v) const
+    __device__ __forceinline__ void jadd2(int c, int p, int lj, int li, int hi, int lo) const
     {
-        if (v) atomicAdd(&sJ[((size_t)(c * NP + p) * G::JR + lj) * G::JW + li], (unsigned long long)v);
+        const int k = ((c * NP + p) * G::JR + lj) * G::JW + li;
+        if (hi) atomicAdd(&sJh[k], (unsigned)hi);
+        if (lo) atomicAdd(&sJl[k], (unsigned)lo);
     }
     __device__ __forceinline__ void put(int c, int p, int lj, int li, float x) const;
 };
@@ -197,18 +219,19 @@ struct FloatAcc {
     }
 };
 
-// Exact round-to-nearest of a scaled contribution |v| < 2^42 into hi*2^20 + lo
-// (|lo| <= 2^19) using only FP32 adds: t + 1.5*2^23 has unit spacing, so its
-// bit pattern minus that of 1.5*2^23 is round(t).  (A float->int64 conversion
-// would run on the FP64 pipe, which is narrow on this part.)
+
+// Exact round-to-nearest of a scaled contribution |v| < 2^42 into hi 2^21 + lo
+// using only FP32 adds: t + 1.5*2^23 has unit spacing, so its bit pattern minus
+// that of 1.5*2^23 is round(t).  (A float->int64 conversion would run on the
+// FP64 pipe, which is narrow on this part.)
 __device__ __forceinline__ void fx_split(float v, int &hi, int &lo)
 {
     const float M = 12582912.0f;                       // 1.5 * 2^23
-    const float t = __fmul_rn(v, 9.5367431640625e-07f); // v * 2^-20 (exact)
+    const float t = __fmul_rn(v, FX_DOWN);              // v 2^-18 (exact)
     const float tm = __fadd_rn(t, M);
     hi = __float_as_int(tm) - 0x4B400000;
     const float hf = __fsub_rn(tm, M);                  // round(t), exact
-    const float r = __fmaf_rn(-hf, 1048576.0f, v);      // v - hi * 2^20, exact
+    const float r = __fmaf_rn(-hf, FX_UP, v);           // v - hi 2^18, exact
     lo = __float_as_int(__fadd_rn(r, M)) - 0x4B400000;
 }
 
@@ -216,13 +239,15 @@ __device__ __forceinline__ long long fx(float x, float qs)
 {
     int hi, lo;
     fx_split(x * qs, hi, lo);
-    return ((long long)hi << 20) + lo;
+    return ((long long)hi << FX_SHIFT) + lo;
 }
 
 template <int NP, int TZ, int TR>
 __device__ __forceinline__ void SmemAcc<NP, TZ, TR>::put(int c, int p, int lj, int li, float x) const
 {
-    jadd(c, p, lj, li, fx(x, qs));
+    int hi, lo;
+    fx_split(x * qs, hi, lo);
+    jadd2(c, p, lj, li, hi, lo);
 }
 
 template <int NP>
@@ -535,7 +560,7 @@ __device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, 
 // of its tile (see tile_slot), so successive moves mostly stay in one cell and
 // go to the same 8*NP accumulator words (J_z at 2 faces, J_r at 2 faces, J_phi
 // at 4 nodes, each per part).  Each contribution is rounded to the int64 fixed
-// point exactly as fx() does, kept as hi*2^20 + lo, and the two halves are
+// point exactly as fx() does, kept as hi 2^21 + lo, and the two halves are
 // summed in 32-bit registers; the biased bit patterns of the rounding sums
 // (1.5*2^23 + hi) are added directly and the bias is removed once per flush.
 // Integer sums make the result independent of particle order.  A flush adds
@@ -568,7 +593,7 @@ struct FastSum {
              : e == 3 ? p * PL + 1
                       : (NP + p) * PL + ((e - 4) & 1) + ((e - 4) >> 1) * G::JW;
     }
-    // two contributions t = value * qscale * 2^-20 (|t| < 2^22) at once, on the
+    // two contributions t = value * qscale * 2^-21 (|t| < 2^21) at once, on the
     // paired FP32 units: the same roundings as fx() for each lane
     __device__ __forceinline__ void put2(int i, float2 t)
     {
@@ -579,7 +604,7 @@ struct FastSum {
         hs[i + 1] += __float_as_uint(tm.y);
         const float2 hf = __fadd2_rn(tm, nM2);                        // round(t), exact
         const float2 r = __ffma2_rn(hf, make_float2(-1.f, -1.f), t);  // t - round(t), exact
-        const float2 lm = __ffma2_rn(r, make_float2(1048576.0f, 1048576.0f), M2);
+        const float2 lm = __ffma2_rn(r, make_float2(FX_UP, FX_UP), M2);
         ls[i] += __float_as_uint(lm.x);
         ls[i + 1] += __float_as_uint(lm.y);
     }
@@ -611,15 +636,17 @@ struct FastSum {
         }
         n += 1u;
     }
-    __device__ __forceinline__ void flush(unsigned long long *sJ)
+    // the sums go to the hi and lo planes with 32-bit shared atomics (the
+    // planes hold the int32 sums exactly: see FX_SHIFT)
+    __device__ __forceinline__ void flush(unsigned *sJh, unsigned *sJl)
     {
         if (n == 0u) return;
-        unsigned long long *b = sJ + (key >> 12) * G::JW + (key & 0xFFF);
+        const int base = (key >> 12) * G::JW + (key & 0xFFF);
         const unsigned bias = 0x4B400000u * n;
 #pragma unroll
         for (int i = 0; i < NV; i++) {
-            const long long w = ((long long)(int)(hs[i] - bias) << 20) + (long long)(int)(ls[i] - bias);
-            atomicAdd(b + off(i), (unsigned long long)w);
+            atomicAdd(sJh + base + off(i), hs[i] - bias);
+            atomicAdd(sJl + base + off(i), ls[i] - bias);
             hs[i] = 0u; ls[i] = 0u;
         }
         n = 0u;
@@ -628,12 +655,13 @@ struct FastSum {
 
 // ------------------------------------------------------------ the GPD kernel
 // Particle order inside a tile.  The n particles of a tile (sorted by cell) are
-// taken in chunks: full chunks of GPD_C = GPD_T * GPD_K, then the rest (rc <
-// GPD_C).  In a chunk every thread takes kc consecutive particles (GPD_K in a
-// full chunk, kc = ceil(rc / GPD_T) in the last; nt = rc / kc threads take kc,
-// thread nt the rem = rc - nt kc left), so one thread's moves mostly share a
-// cell (FastSum).  Thread t's k-th particle of a chunk is q0 + t kc + k.
-constexpr int GPD_T = 256, GPD_K = 8, GPD_C = GPD_T * GPD_K;
+// taken in chunks of at most GPD_C = 2047 (the int32 accumulator planes are
+// drained into int64 after each, FX_SHIFT).  In a chunk of rc particles every
+// thread takes kc = ceil(rc / GPD_T) consecutive particles (nt = rc / kc
+// threads take kc, thread nt the rem = rc - nt kc left), so one thread's moves
+// mostly share a cell (FastSum).  Thread t's k-th particle of a chunk is
+// q0 + t kc + k.
+constexpr int GPD_T = 256, GPD_C = 2047;
 
 struct Chunk { int q0, rc, kc, nt, rem; };
 
@@ -641,22 +669,23 @@ __host__ __device__ __forceinline__ int tile_nchunks(int n) { return (n + GPD_C 
 
 __host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c)
 {
-    const int nfull = n / GPD_C;
     Chunk k;
-    if (c < nfull) {
-        k.q0 = c * GPD_C; k.rc = GPD_C; k.kc = GPD_K; k.nt = GPD_T; k.rem = 0;
-    } else {
-        k.q0 = nfull * GPD_C;
-        k.rc = n - k.q0;
-        k.kc = (k.rc + GPD_T - 1) / GPD_T;
-        k.nt = k.rc / k.kc;
-        k.rem = k.rc - k.nt * k.kc;
-    }
+    k.q0 = c * GPD_C;
+    k.rc = n - k.q0 < GPD_C ? n - k.q0 : GPD_C;
+    k.kc = (k.rc + GPD_T - 1) / GPD_T;
+    k.nt = k.rc / k.kc;
+    k.rem = k.rc - k.nt * k.kc;
     return k;
 }
 
 // Ampere-style asynchronous 4-byte global -> shared copies (one per thread and
 // word); a thread waits only for its own groups
+// ask L2 to fetch [p, p + bytes) from global memory (p and bytes multiples of 16)
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -715,6 +744,36 @@ __device__ __forceinline__ void queue_get(const float *q, int &li, int &lj, DepI
     }
 }
 
+// One particle through global memory: for particles appended since the last
+// sort, particles that drifted beyond the staged halo (sort period above 2) and
+// boxes too short for a staged tile.
+template <int NP, bool FA>
+__device__ __forceinline__ void gpd_global_one(const Particles &P, long long idx, int cell, const PArgs &a,
+                                               const GlobAcc<NP> &gacc, const FloatAcc &facc)
+{
+    constexpr int NM = (NP + 1) / 2;
+    const int zoff = (int)a.zoff;
+    const int iz = cell_iz(cell), jr = cell_jr(cell);
+    if (!a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) { P.cell[idx] = -1; return; }
+    PState s;
+    DepIn<NM> d;
+    float4 ra, rb;
+    ld_rec(P.rec + 2 * idx, ra, rb);
+    s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
+    s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
+    s.W0 = a.track_work ? P.W0[idx] : 0.f;
+    s.W1 = a.track_work ? P.W1[idx] : 0.f;
+    s.jr = jr;
+    push_move<NP>(gacc, a, iz, jr, s, d);
+    if constexpr (FA) deposit_general<NP>(facc, a, iz, jr, d);
+    else deposit_general<NP>(gacc, a, iz, jr, d);
+    const int niz = wrapn(iz + s.diz, a.nzp);
+    const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
+    P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
+    st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph), make_float4(s.ux, s.uy, s.uz, s.w));
+    if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+}
+
 // FA: the FP32 float-atomic variant (every deposit goes to the global FP32
 // current Jfa with float atomics; the fixed-point accumulators are unused)
 template <int NP, int TZ, int TR, bool FA>
@@ -748,72 +807,64 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
         end = min(begin + tail_chunk, np);
         if (begin >= end) return;
     }
-    GlobAcc<NP> gacc{E, Bb, J, jdirty, d_epoch, a};
+    const GlobAcc<NP> gacc{E, Bb, J, jdirty, d_epoch, a};
     const FloatAcc facc{Jfa, a};
-    const int zoff = (int)a.zoff;
     if (!tile_mode || a.nzp < 2 * G::JW) {
         // particles appended since the last sort, or a box too short for the
         // staged tile: every access goes to global memory
         for (long long idx = begin + threadIdx.x; idx < end; idx += blockDim.x) {
             const int cell = P.cell[idx];
-            if (cell < 0) continue;
-            const int iz = cell_iz(cell), jr = cell_jr(cell);
-            if (!a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) { P.cell[idx] = -1; continue; }
-            PState s;
-            DepIn<NM> d;
-            float4 ra, rb;
-            ld_rec(P.rec + 2 * idx, ra, rb);
-            s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
-            s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
-            s.W0 = a.track_work ? P.W0[idx] : 0.f;
-            s.W1 = a.track_work ? P.W1[idx] : 0.f;
-            s.jr = jr;
-            push_move<NP>(gacc, a, iz, jr, s, d);
-            if constexpr (FA) deposit_general<NP>(facc, a, iz, jr, d);
-            else deposit_general<NP>(gacc, a, iz, jr, d);
-            const int niz = wrapn(iz + s.diz, a.nzp);
-            const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
-            P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
-            st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph), make_float4(s.ux, s.uy, s.uz, s.w));
-            if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+            if (cell >= 0) gpd_global_one<NP, FA>(P, idx, cell, a, gacc, facc);
         }
         return;
     }
-    // ---- shared memory: accumulators, staged fields, crossing queue, particle buffers
-    unsigned long long *sJ = sraw;
-    float4 *sf = reinterpret_cast<float4 *>(sraw + G::JPAD);
+    const int zoff = (int)a.zoff;
+    // ---- shared memory: accumulator planes, staged fields, crossing queue, particle buffers
+    unsigned long long *sJ64 = sraw;                          // int64 sums of drained chunks
+    unsigned *sJh = reinterpret_cast<unsigned *>(sraw + G::JPAD);   // int32 hi, lo planes of the chunk
+    unsigned *sJl = sJh + G::JPAD;
+    float4 *sf = reinterpret_cast<float4 *>(sJh + 2 * G::JPAD);
     float *queue = reinterpret_cast<float *>(sf + G::FVEC);
     int *qcount = reinterpret_cast<int *>(queue + G::QCAP * G::QW);
-    // ---- each thread pushes kc consecutive particles of the tile; the next
-    // particle's words are copied to shared memory while one is pushed (the
-    // first copy overlaps the staging of the fields)
     float *pbuf = reinterpret_cast<float *>(qcount + 4);
     const int n = (int)(end - begin);
-    const int nch = tile_nchunks(n);
     const int tid = threadIdx.x;
-    auto slot_of = [&](int ch, int k) -> long long {
-        const Chunk C = tile_chunk(n, ch);
-        const int cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
-        return k < cnt ? begin + C.q0 + tid * C.kc + k : -1;
-    };
-    auto prefetch = [&](int b, long long idx) {
-        if (idx >= 0) {
+    int32_t *const cellp = P.cell + begin;          // the tile's particles, tile-relative index
+    float4 *const recp = P.rec + 2 * begin;
+    // ---- one thread asks L2 for the tile's records and cells (bulk prefetch)
+    // before the fields are staged; the threads' per-particle copies below then
+    // mostly hit L2 instead of waiting on DRAM
+    if (tid == 0) {
+        const unsigned long long rb = (unsigned long long)n * 32;
+        for (unsigned long long o = 0; o < rb; o += 32768)
+            l2_prefetch(reinterpret_cast<const char *>(recp) + o, (unsigned)min(rb - o, 32768ull));
+        const unsigned long long c0 = ((unsigned long long)begin * 4 + 15) & ~15ull;
+        const unsigned long long c1 = ((unsigned long long)end * 4) & ~15ull;
+        if (c1 > c0) l2_prefetch(reinterpret_cast<const char *>(P.cell) + c0, (unsigned)(c1 - c0));
+    }
+    // ---- each thread pushes a run of consecutive particles; the next
+    // particle's words are copied to shared memory while one is pushed (the
+    // first copy overlaps the staging of the fields)
+    auto prefetch = [&](int b, int qi) {
+        if (qi >= 0) {
             float *pb = pbuf + b * G::PB;
             float4 *pr = reinterpret_cast<float4 *>(pb + GPD_T);
-            cp_async4(pb + tid, P.cell + idx);
-            cp_async16(pr + tid, P.rec + 2 * idx);
-            cp_async16(pr + GPD_T + tid, P.rec + 2 * idx + 1);
+            cp_async4(pb + tid, cellp + qi);
+            cp_async16(pr + tid, recp + 2 * qi);
+            cp_async16(pr + GPD_T + tid, recp + 2 * qi + 1);
         }
         cp_async_commit();
     };
-    long long idx = slot_of(0, 0);
-    prefetch(0, idx);
+    const int nch = tile_nchunks(n);
+    Chunk C = tile_chunk(n, 0);
+    int cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
+    int q = C.q0 + tid * C.kc;
+    prefetch(0, cnt > 0 ? q : -1);
     // ---- stage E and Bbar of the tile and its halo; clear the accumulators
     const int col0 = tz0 - G::H - 1;
     const int row0 = tr0 - G::H - 1;
-    const SmemAcc<NP, TZ, TR> sacc{sf, sJ, a.qscale};
-    for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) sJ[k] = 0ull;
-    if (threadIdx.x == 0) *qcount = 0;
+    for (int k = tid; k < 2 * G::JPAD; k += blockDim.x) sJ64[k] = 0ull;    // int64 plane and both int32 planes
+    if (tid == 0) *qcount = 0;
     // one float4 word (up to 4 mode parts of one node) per thread and pass
     // (compile-time trip count: the loop unrolls and its global loads overlap)
 #pragma unroll
@@ -834,24 +885,35 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
         sf[k] = make_float4(w4[0], w4[1], w4[2], w4[3]);
     }
     __syncthreads();
-    const float q20 = a.qscale * 9.5367431640625e-07f;            // qscale * 2^-20
+    const SmemAcc<NP, TZ, TR> sacc{sf, sJh, sJl, a.qscale};
+    const float q20 = a.qscale * FX_DOWN;                         // qscale 2^-21
     FastSum<NP, TZ, TR> fs;
     fs.clear();
-    int buf = 0;
     for (int ch = 0; ch < nch; ch++) {
-        const int kc = tile_chunk(n, ch).kc;
-        for (int k = 0; k < kc; k++) {                             // block-uniform trip count
-            const long long nidx = k + 1 < kc ? slot_of(ch, k + 1) : (ch + 1 < nch ? slot_of(ch + 1, 0) : -1);
-            prefetch(buf ^ 1, nidx);
+        if (ch > 0) {                                              // chunks beyond the first
+            C = tile_chunk(n, ch);
+            cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
+            q = C.q0 + tid * C.kc;
+            prefetch(0, cnt > 0 ? q : -1);
+        }
+        int buf = 0;
+        for (int k = 0; k < C.kc; k++) {                           // block-uniform trip count
+            prefetch(buf ^ 1, k + 1 < cnt ? q + k + 1 : -1);
             cp_async_wait_prev();                                  // this particle's words have landed
-            if (idx >= 0) {
+            if (k < cnt) {
+                const int qi = q + k;
                 const float *pb = pbuf + buf * G::PB;
                 const float4 *pr = reinterpret_cast<const float4 *>(pb + GPD_T);
                 const int cell = __float_as_int(pb[tid]);
                 const int iz = cell_iz(cell), jr = cell_jr(cell);
                 bool act = cell >= 0;
                 if (act && !a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
-                    P.cell[idx] = -1;                  // behind the moving window
+                    cellp[qi] = -1;                    // behind the moving window
+                    act = false;
+                }
+                const int li = wrapn(iz - col0, a.nzp), lj = jr - row0;
+                if (act && !(li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2)) {
+                    gpd_global_one<NP, FA>(P, begin + qi, cell, a, gacc, facc);   // drifted beyond the halo
                     act = false;
                 }
                 if (act) {
@@ -860,62 +922,66 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
                     const float4 ra = pr[tid], rb = pr[GPD_T + tid];
                     s.oz = ra.x; s.orr = ra.y; s.cph = ra.z; s.sph = ra.w;
                     s.ux = rb.x; s.uy = rb.y; s.uz = rb.z; s.w = rb.w;
-                    s.W0 = a.track_work ? P.W0[idx] : 0.f;
-                    s.W1 = a.track_work ? P.W1[idx] : 0.f;
+                    s.W0 = a.track_work ? P.W0[begin + qi] : 0.f;
+                    s.W1 = a.track_work ? P.W1[begin + qi] : 0.f;
                     s.jr = jr;
-                    const int li = wrapn(iz - col0, a.nzp), lj = jr - row0;
-                    if (li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2) {
-                        push_move<NP>(sacc, a, li, lj, s, d);
-                        if constexpr (FA) {
-                            deposit_general<NP>(facc, a, iz, jr, d);
-                        } else if (same_cell(d)) {
-                            const int key = (lj << 12) | li;
-                            if (key != fs.key) { fs.flush(sJ); fs.key = key; }
-                            fs.add(d, d.Q * q20);
-                        } else {
-                            // a move across a cell boundary waits in the queue (deposited
-                            // directly when the queue is full)
-                            const int slot = atomicAdd(qcount, 1);
-                            if (slot < G::QCAP) queue_put<NM>(queue + G::QW * slot, li, lj, d);
-                            else deposit_general<NP>(sacc, a, li, lj, d);
-                        }
-                    } else {                           // drifted beyond the staged halo
-                        push_move<NP>(gacc, a, iz, jr, s, d);
-                        if constexpr (FA) deposit_general<NP>(facc, a, iz, jr, d);
-                        else deposit_general<NP>(gacc, a, iz, jr, d);
+                    push_move<NP>(sacc, a, li, lj, s, d);
+                    if constexpr (FA) {
+                        deposit_general<NP>(facc, a, iz, jr, d);
+                    } else if (same_cell(d)) {
+                        const int key = (lj << 12) | li;
+                        if (key != fs.key) { fs.flush(sJh, sJl); fs.key = key; }
+                        fs.add(d, d.Q * q20);
+                    } else {
+                        // a move across a cell boundary waits in the queue (deposited
+                        // directly when the queue is full)
+                        const int slot = atomicAdd(qcount, 1);
+                        if (slot < G::QCAP) queue_put<NM>(queue + G::QW * slot, li, lj, d);
+                        else deposit_general<NP>(sacc, a, li, lj, d);
                     }
                     const int niz = wrapn(iz + s.diz, a.nzp);
                     const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
-                    P.cell[idx] = dead ? -1 : make_cell(niz, jr + s.djr);
-                    st_rec(P.rec + 2 * idx, make_float4(s.oz, s.orr, s.cph, s.sph),
+                    const int ncell = dead ? -1 : make_cell(niz, jr + s.djr);
+                    if (ncell != cell) cellp[qi] = ncell;   // most particles keep their cell
+                    st_rec(recp + 2 * qi, make_float4(s.oz, s.orr, s.cph, s.sph),
                            make_float4(s.ux, s.uy, s.uz, s.w));
-                    if (a.track_work) { P.W0[idx] = s.W0; P.W1[idx] = s.W1; }
+                    if (a.track_work) { P.W0[begin + qi] = s.W0; P.W1[begin + qi] = s.W1; }
                 }
             }
-            idx = nidx;
             buf ^= 1;
         }
         if constexpr (!FA) {
-            fs.flush(sJ);
+            fs.flush(sJh, sJl);
             fs.key = -1;
+            // drain the chunk's int32 planes into the int64 plane (each thread its
+            // own words: no atomics), so the next chunk starts from zero
+            __syncthreads();
+            for (int w = tid; w < G::JWORDS; w += blockDim.x) {
+                sJ64[w] += (unsigned long long)(((long long)(int)sJh[w] << FX_SHIFT) + (long long)(int)sJl[w]);
+                sJh[w] = 0u;
+                sJl[w] = 0u;
+            }
+            __syncthreads();
         }
     }
     if constexpr (FA) return;
     // the queued cell-crossing moves, spread over all threads
     __syncthreads();
     const int nq = imin(*qcount, G::QCAP);
-    for (int q = tid; q < nq; q += blockDim.x) {
+    for (int qq = tid; qq < nq; qq += blockDim.x) {
         int qi, qj;
         DepIn<NM> dq;
-        queue_get<NM>(queue + G::QW * q, qi, qj, dq);
+        queue_get<NM>(queue + G::QW * qq, qi, qj, dq);
         deposit_general<NP>(sacc, a, qi, qj, dq);
     }
     __syncthreads();
-    // the tile's accumulators go to its own scratch block with plain stores;
-    // the reduction kernel sums the tiles that cover each node
+    // the tile's accumulators (the int64 plane plus the queued moves' int32
+    // parts) go to its own scratch block with plain stores; the reduction
+    // kernel sums the tiles that cover each node
     unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
-    for (int k = threadIdx.x; k < G::JWORDS; k += blockDim.x) dst[k] = sJ[k];
-    if (threadIdx.x == 0) tstamp[blockIdx.x] = *d_epoch;
+    for (int k = tid; k < G::JWORDS; k += blockDim.x)
+        dst[k] = sJ64[k] + (unsigned long long)(((long long)(int)sJh[k] << FX_SHIFT) + (long long)(int)sJl[k]);
+    if (tid == 0) tstamp[blockIdx.x] = *d_epoch;
 }
 
 template <int NP, int TZ, int TR, bool FA>
