@@ -267,6 +267,24 @@ qpic_status qpic_set_fields(qpic_ctx *ctx, int32_t which, int32_t comp, int32_t 
  * current; otherwise QPIC_ESTATE and nothing is launched. */
 qpic_status qpic_charge_density_noalloc(qpic_ctx *ctx, int32_t mode, double *re, double *im);
 
+/* Checkpoint and resume (the paper has no counterpart; a long run is saved
+ * and resumed without changing its result).  A snapshot holds the E, B and
+ * Bbar planes, the live particles (sorted, or compacted on the FP64 path),
+ * the modal-work counters when tracked, the ion background of the Gauss
+ * diagnostic, the step and window counters and the plasma-injection
+ * parameters, as raw words after a header.  qpic_state_size gives its size in
+ * bytes; qpic_save_state writes it into a caller-owned host buffer of
+ * `capacity` bytes (*written = the size; QPIC_ECAPACITY, nothing written, if
+ * the buffer is too small); qpic_load_state reads it into a context created
+ * with the same configuration (QPIC_EINVAL otherwise) and replaces its state.
+ * On the FP32 fixed-point path the current is an integer sum, so the steps
+ * after a load are bit-identical to the steps the saved context would have
+ * taken.  Saving sorts the particles (FP32) or compacts them (FP64); all three
+ * synchronise the context's stream. */
+qpic_status qpic_state_size(qpic_ctx *ctx, int64_t *bytes);
+qpic_status qpic_save_state(qpic_ctx *ctx, void *buf, int64_t capacity, int64_t *written);
+qpic_status qpic_load_state(qpic_ctx *ctx, const void *buf, int64_t size);
+
 /* Number of live particles. */
 qpic_status qpic_num_particles(qpic_ctx *ctx, int64_t *n);
 

@@ -129,6 +129,12 @@ def _declare(L):
     L.qpic_reduced_integrate_device.restype = ctypes.c_int
     L.qpic_work_f_estimate.argtypes = [ctypes.c_int64] + [_D] * 5 + [ctypes.c_double] * 3 + [_D, _D]
     L.qpic_work_f_estimate.restype = ctypes.c_int
+    L.qpic_state_size.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+    L.qpic_state_size.restype = ctypes.c_int
+    L.qpic_save_state.argtypes = [_P, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.qpic_save_state.restype = ctypes.c_int
+    L.qpic_load_state.argtypes = [_P, ctypes.c_void_p, ctypes.c_int64]
+    L.qpic_load_state.restype = ctypes.c_int
     L.qpic_kernel_times.argtypes = [_P, _I, _D, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_I)]
     for name in ("qpic_default_config", "qpic_init", "qpic_get_solver", "qpic_cfl_limit",
@@ -457,6 +463,20 @@ class Sim:
         out = out.reshape(9, cap)[:, :n.value]
         keys = ("z", "r", "phi", "ux", "uy", "uz", "w", "W0", "W1")
         return {k: out[i].copy() for i, k in enumerate(keys)}
+
+    def save_state(self):
+        """the whole simulation state as a bytes-like numpy uint8 array (qpic_save_state)"""
+        n = ctypes.c_int64()
+        self._check(self.L.qpic_state_size(self.h, ctypes.byref(n)), "state_size")
+        buf = np.empty(n.value, dtype=np.uint8)
+        w = ctypes.c_int64()
+        self._check(self.L.qpic_save_state(self.h, buf.ctypes.data, buf.size, ctypes.byref(w)), "save_state")
+        return buf[:w.value]
+
+    def load_state(self, buf):
+        """replace this context's state with a snapshot from save_state"""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.L.qpic_load_state(self.h, buf.ctypes.data, buf.size), "load_state")
 
     def diag(self):
         v = np.zeros(7 + self.nm)

@@ -781,6 +781,169 @@ qpic_status qpic_set_fields(qpic_ctx *c, int32_t which, int32_t comp, int32_t mo
     return qpic_set_field(c, which, comp, mode, re, im);
 }
 
+// ---------------------------------------------------------------- snapshots
+// A snapshot is a header followed by raw device words: the E, B and Bbar
+// planes in their physical (circular z) layout, the live particles (sorted,
+// dead ones dropped), the modal-work counters when tracked and the ion
+// background of the Gauss diagnostic.  Loading it into a context of the same
+// configuration resumes the run: the current is an integer sum over particles
+// (FP32 path), so the steps after a load are bit-identical to the steps the
+// saved context would have taken.
+namespace {
+
+const unsigned long long kSnapMagic = 0x50414e5343495051ull;   // "QPICSNAP"
+
+struct SnapHeader {
+    unsigned long long magic;
+    int32_t version, nz, nr, nm, precision, track_work, periodic, solver, L, nzp;
+    double dz, dr, dt, qref;
+    long long nstep, shifts, zoff, np;
+    int32_t have_plasma, ppc_z, ppc_r, ppc_phi, jitter, has_ions;
+    double n0, z_start, ramp_len;
+    unsigned long long seed;
+    long long field_bytes, particle_bytes, ion_bytes;
+};
+
+size_t snap_field_words(const qpic_ctx *c) { return (size_t)3 * c->g.nparts * c->g.plane; }
+size_t snap_ion_doubles(const qpic_ctx *c) { return (size_t)c->g.nm * 2 * (c->g.nr + 1) * c->g.nz; }
+
+// live particles in buffer order, sorted (FP32) or compacted (FP64); returns the count
+long long snap_prepare(qpic_ctx *c)
+{
+    if (c->fp64) {
+        fp64_compact(c);
+        cudaStreamSynchronize(c->stream);
+        return c->np;
+    }
+    launch_sort(c);
+    return live_count(c);
+}
+
+SnapHeader snap_header(const qpic_ctx *c, long long np)
+{
+    SnapHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kSnapMagic; h.version = 1;
+    h.nz = c->g.nz; h.nr = c->g.nr; h.nm = c->g.nm; h.precision = c->cfg.precision;
+    h.track_work = c->cfg.track_work; h.periodic = c->g.periodic; h.solver = c->cfg.solver; h.L = c->L;
+    h.nzp = c->g.nzp;
+    h.dz = c->dz; h.dr = c->dr; h.dt = c->dt; h.qref = c->qref;
+    h.nstep = c->nstep; h.shifts = c->shifts; h.zoff = c->g.zoff; h.np = np;
+    h.have_plasma = c->have_plasma; h.ppc_z = c->ppc_z; h.ppc_r = c->ppc_r; h.ppc_phi = c->ppc_phi;
+    h.jitter = c->jitter; h.has_ions = c->rho_ion != nullptr;
+    h.n0 = c->n0; h.z_start = c->z_start; h.ramp_len = c->ramp_len; h.seed = c->cfg.seed;
+    const size_t fw = c->fp64 ? sizeof(double) : sizeof(float);
+    h.field_bytes = (long long)(3 * snap_field_words(c) * fw);
+    const long long per = c->fp64 ? (7 + (c->cfg.track_work ? 2 : 0)) * 8
+                                  : 4 + 32 + (c->cfg.track_work ? 8 : 0);
+    h.particle_bytes = np * per;
+    h.ion_bytes = h.has_ions ? (long long)(snap_ion_doubles(c) * sizeof(double)) : 0;
+    return h;
+}
+
+long long snap_bytes(const SnapHeader &h)
+{
+    return (long long)sizeof(SnapHeader) + h.field_bytes + h.particle_bytes + h.ion_bytes;
+}
+
+// the device arrays of a snapshot, in order, with their byte sizes
+std::vector<std::pair<void *, size_t>> snap_arrays(qpic_ctx *c, long long np)
+{
+    std::vector<std::pair<void *, size_t>> v;
+    const size_t fwords = snap_field_words(c);
+    if (c->fp64) {
+        v.push_back({c->E64, fwords * 8}); v.push_back({c->B64, fwords * 8}); v.push_back({c->Bb64, fwords * 8});
+        double *a[7] = {c->p64.z, c->p64.x, c->p64.y, c->p64.ux, c->p64.uy, c->p64.uz, c->p64.w};
+        for (double *x : a) v.push_back({x, (size_t)np * 8});
+        if (c->cfg.track_work) { v.push_back({c->p64.W0, (size_t)np * 8}); v.push_back({c->p64.W1, (size_t)np * 8}); }
+    } else {
+        v.push_back({c->E, fwords * 4}); v.push_back({c->B, fwords * 4}); v.push_back({c->Bb, fwords * 4});
+        v.push_back({c->p.cell, (size_t)np * 4});
+        v.push_back({c->p.rec, (size_t)np * 32});
+        if (c->cfg.track_work) { v.push_back({c->p.W0, (size_t)np * 4}); v.push_back({c->p.W1, (size_t)np * 4}); }
+    }
+    if (c->rho_ion) v.push_back({c->rho_ion, snap_ion_doubles(c) * 8});
+    return v;
+}
+
+}  // namespace
+
+qpic_status qpic_state_size(qpic_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
+    const long long np = snap_prepare(c);
+    *bytes = snap_bytes(snap_header(c, np));
+    return cuda_check(c, "state_size");
+}
+
+qpic_status qpic_save_state(qpic_ctx *c, void *buf, int64_t capacity, int64_t *written)
+{
+    if (!c || !buf) return QPIC_EINVAL;
+    QPIC_REQUIRE_DEVICE(c);
+    const long long np = snap_prepare(c);
+    const SnapHeader h = snap_header(c, np);
+    const long long need = snap_bytes(h);
+    if (written) *written = need;
+    if (need > capacity) return fail(c, QPIC_ECAPACITY, "save_state: buffer holds " + std::to_string(capacity) +
+                                                            " bytes, the snapshot needs " + std::to_string(need));
+    char *out = static_cast<char *>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (const auto &a : snap_arrays(c, np)) {
+        if (a.second) cudaMemcpyAsync(out + off, a.first, a.second, cudaMemcpyDeviceToHost, c->stream);
+        off += a.second;
+    }
+    cudaStreamSynchronize(c->stream);
+    return cuda_check(c, "save_state");
+}
+
+qpic_status qpic_load_state(qpic_ctx *c, const void *buf, int64_t size)
+{
+    if (!c || !buf || size < (int64_t)sizeof(SnapHeader)) return fail(c, QPIC_EINVAL, "load_state arguments");
+    QPIC_REQUIRE_DEVICE(c);
+    SnapHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kSnapMagic || h.version != 1) return fail(c, QPIC_EINVAL, "load_state: not a snapshot");
+    if (h.nz != c->g.nz || h.nr != c->g.nr || h.nm != c->g.nm || h.precision != c->cfg.precision ||
+        h.track_work != c->cfg.track_work || h.periodic != c->g.periodic || h.solver != c->cfg.solver ||
+        h.L != c->L || h.nzp != c->g.nzp || h.dz != c->dz || h.dr != c->dr || h.dt != c->dt)
+        return fail(c, QPIC_EINVAL, "load_state: the snapshot was taken with another configuration");
+    if (snap_bytes(h) != size) return fail(c, QPIC_EINVAL, "load_state: size does not match the header");
+    qpic_status st = ensure_capacity(c, h.np);
+    if (st != QPIC_OK) return st;
+    if (h.has_ions && !c->rho_ion && !alloc_arr(c, &c->rho_ion, snap_ion_doubles(c)))
+        return fail(c, QPIC_ENOMEM, "load_state: ion background");
+    c->nstep = h.nstep; c->shifts = h.shifts; c->g.zoff = h.zoff;
+    c->have_plasma = h.have_plasma != 0; c->n0 = h.n0; c->z_start = h.z_start; c->ramp_len = h.ramp_len;
+    c->ppc_z = h.ppc_z; c->ppc_r = h.ppc_r; c->ppc_phi = h.ppc_phi; c->jitter = h.jitter;
+    c->cfg.seed = h.seed;
+    set_qscale(c, h.qref);
+    const char *in = static_cast<const char *>(buf);
+    size_t off = sizeof(h);
+    for (const auto &a : snap_arrays(c, h.np)) {
+        if (a.second) cudaMemcpyAsync(a.first, in + off, a.second, cudaMemcpyHostToDevice, c->stream);
+        off += a.second;
+    }
+    c->np = h.np;
+    c->n_tail = 0;
+    c->j_filtered = false;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (c->fp64) {
+        cudaStreamSynchronize(c->stream);
+        return cuda_check(c, "load_state");
+    }
+    // the saved particles are sorted: set the counts and rebuild the tile offsets
+    const long long counts[2] = {h.np, h.np};
+    cudaMemcpyAsync(c->d_count, counts, sizeof(counts), cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(c->tstamp, 0xff, (size_t)c->ntz * c->ntr * sizeof(int), c->stream);
+    cudaMemsetAsync(c->jdirty, 0, (size_t)c->ntz * c->ntr * sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_epoch, 0, 4 * sizeof(int), c->stream);
+    launch_sort(c);
+    cudaStreamSynchronize(c->stream);
+    return cuda_check(c, "load_state");
+}
+
 qpic_status qpic_num_particles(qpic_ctx *c, int64_t *n)
 {
     if (!c || !n) return QPIC_EINVAL;

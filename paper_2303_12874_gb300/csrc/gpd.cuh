@@ -343,17 +343,8 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
             acc.node(fb, c, j0 + 1, i0, v10);
             acc.node(fb, c, j0 + 1, i0 + 1, v11);
 #pragma unroll
-            for (int p = 0; p + 1 < NP; p += 2) {          // two mode parts per paired FP32 op
-                float2 f = __fmul2_rn(make_float2(w[0], w[0]), make_float2(v00[p], v00[p + 1]));
-                f = __ffma2_rn(make_float2(w[1], w[1]), make_float2(v01[p], v01[p + 1]), f);
-                f = __ffma2_rn(make_float2(w[2], w[2]), make_float2(v10[p], v10[p + 1]), f);
-                f = __ffma2_rn(make_float2(w[3], w[3]), make_float2(v11[p], v11[p + 1]), f);
-                F[fb][c][p] = f.x;
-                F[fb][c][p + 1] = f.y;
-            }
-            if (NP & 1)
-                F[fb][c][NP - 1] = w[0] * v00[NP - 1] + w[1] * v01[NP - 1] + w[2] * v10[NP - 1] +
-                                   w[3] * v11[NP - 1];
+            for (int p = 0; p < NP; p++)
+                F[fb][c][p] = w[0] * v00[p] + w[1] * v01[p] + w[2] * v10[p] + w[3] * v11[p];
         }
     // ---- modal sum, rotation to Cartesian
     float cm[NM], sm[NM];
@@ -383,7 +374,7 @@ __device__ __forceinline__ void push_move(const Acc &acc, const PArgs &a, int bi
     float igm = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
     float tx = h * Bx * igm, ty = h * By * igm, tz = h * Bz * igm;
     float t2 = tx * tx + ty * ty + tz * tz;
-    float f2 = 2.f / (1.f + t2);
+    float f2 = __fdividef(2.f, 1.f + t2);
     float sx = f2 * tx, sy = f2 * ty, sz = f2 * tz;
     float upx = umx + (umy * tz - umz * ty);
     float upy = umy + (umz * tx - umx * tz);
