@@ -22,8 +22,7 @@
 //      Each thread takes runs of consecutive particles of the tile (sorted by
 //      cell), so its moves inside one cell are summed in registers (FastSum)
 //      and added once per cell; moves across cells are queued and deposited
-//      once per tile.  One thread asks L2 for the tile's particles (bulk
-//      prefetch) before the fields are staged.
+//      once per tile.
 //   4. the tile's accumulators are stored to its own block of global memory
 //      as int64 (hi 2^21 + lo);
 //      k_jreduce sums the blocks that cover each node.  Integer addition makes
@@ -145,7 +144,7 @@ struct TileGeom {
     static constexpr int FVEC = 2 * 3 * FR * FW * V;                  // float4 words
     static constexpr int NM = (NP + 1) / 2;
     static constexpr int QW = 8 + 4 * (NM - 1);                       // words per queued move
-    static constexpr int QCAP = 512;                                  // queued cell-crossing moves
+    static constexpr int QCAP = 256;                                  // queued cell-crossing moves
     static constexpr int PB = 9 * 256;      // prefetched words per buffer: 256 cells, 2 x 256 float4
     static constexpr size_t SMEM = (size_t)JPAD * 8 /* hi, lo int32 planes */ + (size_t)JPAD * 8 /* int64 plane */ +
                                    (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
@@ -671,12 +670,6 @@ __host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c)
 
 // Ampere-style asynchronous 4-byte global -> shared copies (one per thread and
 // word); a thread waits only for its own groups
-// ask L2 to fetch [p, p + bytes) from global memory (p and bytes multiples of 16)
-__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -822,17 +815,6 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
     const int tid = threadIdx.x;
     int32_t *const cellp = P.cell + begin;          // the tile's particles, tile-relative index
     float4 *const recp = P.rec + 2 * begin;
-    // ---- one thread asks L2 for the tile's records and cells (bulk prefetch)
-    // before the fields are staged; the threads' per-particle copies below then
-    // mostly hit L2 instead of waiting on DRAM
-    if (tid == 0) {
-        const unsigned long long rb = (unsigned long long)n * 32;
-        for (unsigned long long o = 0; o < rb; o += 32768)
-            l2_prefetch(reinterpret_cast<const char *>(recp) + o, (unsigned)min(rb - o, 32768ull));
-        const unsigned long long c0 = ((unsigned long long)begin * 4 + 15) & ~15ull;
-        const unsigned long long c1 = ((unsigned long long)end * 4) & ~15ull;
-        if (c1 > c0) l2_prefetch(reinterpret_cast<const char *>(P.cell) + c0, (unsigned)(c1 - c0));
-    }
     // ---- each thread pushes a run of consecutive particles; the next
     // particle's words are copied to shared memory while one is pushed (the
     // first copy overlaps the staging of the fields)

@@ -27,7 +27,7 @@ void set_solver_constants(qpic_ctx *c)
     for (int l = 0; l < c->L; l++) { h[l] = (float)c->cE[l]; h[MAX_L + l] = (float)c->cB[l]; }
     for (size_t q = 0; q < c->taps.size(); q++) h[2 * MAX_L + q] = (float)c->taps[q];
     cudaMemcpyAsync(c->coef, h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
-    static double h64[2 * MAX_L + MAX_TAPS];
+    double h64[2 * MAX_L + MAX_TAPS];
     for (int k = 0; k < 2 * MAX_L + MAX_TAPS; k++) h64[k] = 0.0;
     for (int l = 0; l < c->L; l++) { h64[l] = c->cE[l]; h64[MAX_L + l] = c->cB[l]; }
     for (size_t q = 0; q < c->taps.size(); q++) h64[2 * MAX_L + q] = c->taps[q];
@@ -123,6 +123,20 @@ __device__ __forceinline__ V zdiff(const V *f, const T *C, int L)
     return acc;
 }
 
+// The same difference in FP64 from FP32 samples and FP64 coefficients: the
+// axis (r = 0) rows of the FP32 path are advanced in FP64 (their mode terms
+// carry the 1/r limits), then rounded to the stored FP32 fields.
+template <typename V>
+__device__ __forceinline__ double2 zdiff64(const V *f, const double *C, int L)
+{
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 1; l <= L; l++) {
+        acc.x = fma(C[l - 1], (double)f[l].x - (double)f[1 - l].x, acc.x);
+        acc.y = fma(C[l - 1], (double)f[l].y - (double)f[1 - l].y, acc.y);
+    }
+    return acc;
+}
+
 // ---------------------------------------------------------------- Faraday
 // dB/dt = -curl E:  B_r: -(i m/r) E_z + D^E_z E_phi;  B_phi: -D^E_z E_r + d_r E_z;
 // B_z: -(1/r) d_r(r E_phi) + (i m/r) E_r.  Writes B^{n+1/2} and Bbar^n.  One
@@ -196,8 +210,17 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
         }
         {
             const size_t q = (size_t)(0 * P + p) * a.plane + base;
-            const T bn = gap ? (T)0 : br[p] + dt * d;
-            B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (br[p] + bn);
+            if (sizeof(T) == 4 && j == 0 && m == 1) {
+                // the axis term in FP64 on the FP32 path (dE_phi again from the staged row)
+                const double d64 = (double)(isim ? -ez1[pr] : ez1[pim]) * a.idr64 +
+                                   zdiff64(sE2 + p * W + s, a.coef64, a.L).x * a.idz64;
+                const double b64 = (double)br[p] + a.dt64 * d64;
+                B[q] = gap ? (T)0 : (T)b64;
+                Bb[q] = gap ? (T)0 : (T)(0.5 * ((double)br[p] + b64));
+            } else {
+                const T bn = gap ? (T)0 : br[p] + dt * d;
+                B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (br[p] + bn);
+            }
         }
         if (up) {
             // B_phi at (i+1/2, j+1/2)
@@ -432,6 +455,9 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
         {
             T v;
             if (j == a.nr || (j == 0 && m != 1)) v = 0;
+            else if (j == 0 && sizeof(T) == 4)          // the axis term in FP64
+                v = (T)((double)ep[p] + a.dt64 * (zdiff64(sB2 + p * W + s - 1, a.coef64 + MAX_L, a.L).y * a.idz64 -
+                                                  2.0 * (double)bz[p] * a.idr64 - (double)jp[p]));
             else if (j == 0) v = ep[p] + dt * (dBr - (T)2 * bz[p] * idr - jp[p]);
             else v = ep[p] + dt * (dBr - (bz[p] - bzm[p]) * idr - jp[p]);
             E[(size_t)(1 * P + p) * a.plane + base] = gap ? (T)0 : v;
@@ -442,8 +468,9 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
             T v;
             if (j == a.nr || (j == 0 && m != 0)) {
                 v = 0;
-            } else if (j == 0) {
-                v = ez[p] + dt * ((T)4 * bp0 * idr - jz[p]);
+            } else if (j == 0) {                       // the axis term in FP64 on the FP32 path
+                v = sizeof(T) == 4 ? (T)((double)ez[p] + a.dt64 * (4.0 * (double)bp0 * a.idr64 - (double)jz[p]))
+                                   : ez[p] + dt * ((T)4 * bp0 * idr - jz[p]);
             } else {
                 const T imr = m > 0 ? (isim ? sB2[pr * W + s].y : -sB2[pim * W + s].y) * ((T)m * irj) : (T)0;
                 const T d = (rh * bp0 - rl * bpm[p]) * irjdr - imr - jz[p];
