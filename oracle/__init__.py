@@ -129,13 +129,19 @@ class Oracle:
             self.h = None
 
     # fields
+    def _check_field(self, which, comp, mode):
+        if which not in FIELDS or comp not in COMPS or not 0 <= int(mode) < self.nm:
+            raise ValueError("no field %r %r mode %r in a box of %d modes" % (which, comp, mode, self.nm))
+
     def set_field(self, which, comp, mode, val):
+        self._check_field(which, comp, mode)
         val = np.asarray(val, dtype=np.complex128).reshape(self.nr + 1, self.nz)
         re = np.ascontiguousarray(val.real)
         im = np.ascontiguousarray(val.imag)
         self.L.or_set_field(self.h, FIELDS[which], COMPS[comp], mode, _p(re), _p(im))
 
     def get_field(self, which, comp, mode):
+        self._check_field(which, comp, mode)
         re = np.zeros((self.nr + 1, self.nz))
         im = np.zeros((self.nr + 1, self.nz))
         self.L.or_get_field(self.h, FIELDS[which], COMPS[comp], mode, _p(re), _p(im))

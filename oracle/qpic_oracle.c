@@ -140,6 +140,7 @@ static cplx *field_ptr(ostate *s, int which)
 /* copy one (comp, mode) plane, [nr+1][nz], in or out */
 void or_set_field(ostate *s, int which, int c, int m, const double *re, const double *im)
 {
+    if (c < 0 || c > 2 || m < 0 || m >= s->nm) return;     /* no such plane */
     cplx *f = field_ptr(s, which);
     for (int j = 0; j <= s->nr; j++)
         for (int i = 0; i < s->nz; i++) {
@@ -150,6 +151,7 @@ void or_set_field(ostate *s, int which, int c, int m, const double *re, const do
 
 void or_get_field(ostate *s, int which, int c, int m, double *re, double *im)
 {
+    if (c < 0 || c > 2 || m < 0 || m >= s->nm) return;     /* no such plane */
     cplx *f = field_ptr(s, which);
     for (int j = 0; j <= s->nr; j++)
         for (int i = 0; i < s->nz; i++) {

@@ -125,6 +125,8 @@ def add_laser(o, cE, cB, a0, w0, tau, z_c, z_f, psi=0.0):
     sqrt([k]_E/[k]_B) at k0 = 1 (the discrete B/E ratio of a wave, Eq. 9), with the
     discrete frequency from Eq. 10 for the time shift."""
     from .coeffs import symbol
+    if o.nm < 2:
+        raise ValueError("the laser is an m = 1 field: the box needs at least 2 modes")
     kE = symbol(cE, o.dz)[0] / o.dz
     kB = symbol(cB, o.dz)[0] / o.dz
     omega = 2.0 / o.dt * np.arcsin(0.5 * o.dt * np.sqrt(kE * kB))

@@ -190,3 +190,20 @@ def test_pulse_group_velocity(oracle_mod):
         assert abs(v_meas - vg) < 2e-3
         if solver == "dual":
             assert abs(vg - 1.0) < 1e-4
+
+
+def test_field_planes_out_of_range_are_refused(oracle_mod):
+    """a mode the box does not have is an error, never a write past the
+    arrays; the laser (an m = 1 field) needs at least two modes"""
+    from oracle import coeffs as C
+    from oracle import setup
+    cE, cB = C.solver_coefficients("dual", 0.13, 0.2)
+    o = oracle_mod.Oracle(32, 8, 1, 0.2, 0.5, 0.13, cE, cB, None, periodic=True)
+    with pytest.raises(ValueError):
+        o.set_field("E", "r", 1, np.zeros((9, 32)))
+    with pytest.raises(ValueError):
+        o.get_field("B", "x", 0)
+    with pytest.raises(ValueError):
+        setup.add_laser(o, cE, cB, 1.0, 2.0, 2.0, 3.2, 3.2)
+    o.set_field("E", "z", 0, np.ones((9, 32)))
+    assert np.all(o.get_field("E", "z", 0) == 1.0)
