@@ -238,22 +238,26 @@ def reduced_divergence(q, torch, stream, n, par, wp):
 def batch_scan(q, torch, stream, nruns, steps, seed=5):
     """Parameter scan of independent periodic runs (grids 256-1024 x 32-128,
     n 0.003-0.02, a0 1-4, ppc 8/16/32; run k draws from a generator seeded
-    (seed, k)).  The tile shape of each particles-per-cell class comes from the
-    autotuner (a 512 x 64 run of that class, sort period 2 for all).  The same
-    runs are stepped one after another, then together as one graph-launched
-    batch.  Returns aggregate particle-steps/s of both."""
+    (seed, k)).  The tile shape, sort period (2 or 4) and particles per
+    thread (4 or 8) of each particles-per-cell class come from the autotuner
+    (a batch of four 512 x 64 runs of that class).  The same runs are stepped one
+    after another, then together as one graph-launched batch whose particle
+    phase is one persistent launch per group of runs.  Returns aggregate
+    particle-steps/s of both."""
     from paper_2303_12874_gb300 import autotune
     tiles = {}
     for ppc_ in ((2, 2, 2), (2, 2, 4), (2, 2, 8)):
-        def make(tz, tr, sp):
-            return q.Sim(512, 64, 0.2, 0.5, stream=stream, tile_z=tz, tile_r=tr, sort_period=sp)
+        def make(tz, tr, sp, ppt):
+            return q.Sim(512, 64, 0.2, 0.5, stream=stream, tile_z=tz, tile_r=tr, sort_period=sp,
+                         particles_per_thread=ppt)
 
         def init(sim, ppc_=ppc_):
             sim.load_plasma(0.01, 0.0, 0.0, ppc_)
             sim.add_laser(2.0, 8.0, 15.0, 51.2, 51.2)
-        tz, tr, _, _ = autotune.tune(make, init, 512, 64, 2, int(np.prod(ppc_)), steps=4, warmup=2,
-                                     sort_periods=(2,))
-        tiles[ppc_] = (tz, tr)
+        tz, tr, sp, ppt, _ = autotune.tune(make, init, 512, 64, 2, int(np.prod(ppc_)), steps=8, warmup=4,
+                                           sort_periods=(2, 4), batch_copies=4,
+                                           particles_per_thread=(4, 8))
+        tiles[ppc_] = (tz, tr, sp, ppt)
     sims, npart = [], []
     for k in range(nruns):
         rng = np.random.default_rng([seed, k])
@@ -263,7 +267,7 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
         a0 = float(rng.uniform(1.0, 4.0))
         ppc = [(2, 2, 2), (2, 2, 4), (2, 2, 8)][int(rng.integers(0, 3))]
         sim = q.Sim(nz, nr, 0.2, 0.5, stream=stream, seed=seed * 1000 + k, tile_z=tiles[ppc][0],
-                    tile_r=tiles[ppc][1])
+                    tile_r=tiles[ppc][1], sort_period=tiles[ppc][2], particles_per_thread=tiles[ppc][3])
         sim.load_plasma(n0, 0.0, 0.0, ppc)
         zc = 0.5 * nz * 0.2
         sim.add_laser(a0, 8.0, 15.0, zc, zc)
@@ -281,10 +285,12 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
     batch = q.Batch(sims, stream=stream)
+    cycle = batch.cycle
     batch.step(batch.cycle)
     torch.cuda.synchronize()
     e0.record(stream)
-    batch.step(steps - steps % batch.cycle)
+    nb = max(cycle, steps - steps % cycle)
+    batch.step(nb)
     e1.record(stream)
     torch.cuda.synchronize()
     bat_ms = e0.elapsed_time(e1)
@@ -292,9 +298,11 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
     for sm in sims:
         sm.close()
     return {"runs": nruns, "particles": int(total), "steps": steps,
-            "tiles": {"ppc %d" % int(np.prod(k)): "%dx%d" % v for k, v in tiles.items()},
-            "sequential": total * steps / (seq_ms / 1e3), "batched_graph": total * steps / (bat_ms / 1e3),
-            "speedup": seq_ms / bat_ms, "unit": "particle-steps/s"}
+            "tiles": {"ppc %d" % int(np.prod(k)): "%dx%d sort %d, %d particles per thread" % v
+                      for k, v in tiles.items()},
+            "cycle": cycle,
+            "sequential": total * steps / (seq_ms / 1e3), "batched_graph": total * nb / (bat_ms / 1e3),
+            "speedup": (nb / bat_ms) / (steps / seq_ms), "unit": "particle-steps/s"}
 
 
 def oracle_sample(w, dt, nz_sample, steps, threads=1):

@@ -87,6 +87,11 @@ typedef struct {
     int32_t tile_z, tile_r;   /* particle tile in cells: 16x8 (default), 32x8, 8x8, 16x16, 32x4 */
     int32_t sort_period;      /* steps between particle sorts (0: default 2; a particle moves
                                  < 1 cell per step, so 2 keeps every one inside its tile halo) */
+    int32_t particles_per_thread; /* consecutive particles one thread of the particle kernel
+                                 takes in a chunk of 256 x this - 1 particles, 1..8 (0: 8).  A
+                                 tile's particles are sorted by cell, so about ppc / this many
+                                 threads share a cell (the "threads per cell" knob); smaller
+                                 values mean more threads per cell and more chunk drains */
     int32_t track_work;       /* per-particle work in W0, W1: 0 off; 1 modal (Eq. 16:
                                  W0 from m = 0, W1 from m >= 1); 2 directional (Eq. 17:
                                  W0 = W_z, W1 = W_perp, all modes) */
@@ -101,7 +106,7 @@ typedef struct {
 
 /* Fill *cfg with defaults (M = 1, dual solver, L = 16, band 0.8, cfl 0.9,
  * FP32 + int64 fixed point, filter on, tol 1e-16, periodic, 16 x 8 tiles, sort
- * every 2 steps). */
+ * every 2 steps, 8 particles per thread). */
 qpic_status qpic_default_config(qpic_config *cfg);
 
 /* Create a context: fit the z-operator coefficients on the host in FP64
@@ -339,25 +344,47 @@ qpic_status qpic_kernel_times(qpic_ctx *ctx, int32_t n, double *ms, int64_t *lau
                               const char **names, int32_t *n_classes);
 
 /* Batches (a systems feature; the paper has no counterpart): many independent
- * runs (for example a parameter scan) advanced by one CUDA graph launch per cycle.  qpic_batch_create captures one cycle of
- * 2 x `sort_period` full steps of every run (a sort swaps the particle
- * buffers, so a cycle holds two sorts and every replay starts from the
- * buffers the graph was recorded with) -- each run on its own stream, forked
- * from and joined to cuda_stream -- into a single graph; the runs are parallel
- * branches, so uneven runs overlap on the GPU and launch costs are paid once
- * per cycle.  cuda_stream NULL: the batch uses a stream of its own (the legacy
- * default stream cannot be captured).  Runs must use the FP32 path, a periodic box (no moving window),
- * one common sort period, and profiling off; each is first brought to a cycle
- * boundary.  The contexts stay owned by the caller and must outlive the batch;
- * do not step them individually while the batch exists.
+ * runs (for example a parameter scan) advanced by one CUDA graph launch per
+ * cycle of steps.  qpic_batch_create captures the cycle once.  Every step of
+ * it has three phases: (1) Faraday (Eq. 9) and the step's epoch on each run's
+ * own stream, forked from and joined to cuda_stream; (2) one persistent
+ * launch per group of up to 64 runs that share the mode count and the tile
+ * shape: its blocks (two per SM) take items from a work list -- first the
+ * gather, Boris push and charge-conserving deposit (Sec. II.B, Eqs. 10-11) of
+ * every (run, tile), then the current reduction of every (run, tile), each of
+ * which waits, for at most a bounded number of polls, until the deposits of
+ * the 3 x 3 tiles around it have been published; (3) the J filter (Sec. III),
+ * Ampere (Eq. 8) and, when due, the sort on the runs' own streams.  A sort
+ * swaps the particle buffers, so the cycle is twice the least common multiple
+ * of the runs' sort periods (at most 16 steps) and every replay starts from the
+ * buffers the graph was recorded with.  cuda_stream NULL: the batch uses a
+ * stream of its own (the legacy default stream cannot be captured).  Runs
+ * must use the FP32 fixed-point path, a periodic box (no moving window),
+ * profiling off, the device current at their creation, and a sort period of
+ * at most min(TZ, TR) - 3 (a particle then never deposits outside the 3 x 3
+ * tiles around the tile it was sorted into); QPIC_EINVAL otherwise.  Each run
+ * is first brought to a cycle boundary with its particles sorted (stepped on
+ * its own until then).  A batch is deterministic (the int64 deposit); it
+ * agrees with the same runs stepped one by one to FP32 rounding, the batched
+ * particle kernel being a separate compilation whose fused multiply-adds may
+ * differ.  The contexts stay owned by the caller and must outlive the batch;
+ * do not step them individually while it exists.
  * qpic_batch_step: nsteps must be a multiple of qpic_batch_cycle(); it first
  * waits for the runs' own streams, then synchronises cuda_stream and checks
- * every run's error word. */
+ * every run's error word: QPIC_ETIMEOUT when a wait of the particle phase gave
+ * up (that tile's current is left out of the step), QPIC_EOVERFLOW for a
+ * fixed-point overflow; qpic_batch_last_error names the run.
+ * qpic_batch_set_wait: the number of polls (each about 0.1 us or more) after
+ * which a wait gives up (default 2^24, above one second), and an item of the
+ * work list (-1: none; 0 .. tiles-1 are the particle items of the first group
+ * in run order) whose completion is never published -- a way to exercise the
+ * timeout path without a fault; polls >= 0, else QPIC_EINVAL. */
 typedef struct qpic_batch qpic_batch;
 qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_stream, qpic_batch **out);
 qpic_status qpic_batch_step(qpic_batch *batch, int32_t nsteps);
 int32_t qpic_batch_cycle(const qpic_batch *batch);
 const char *qpic_batch_last_error(const qpic_batch *batch);
+qpic_status qpic_batch_set_wait(qpic_batch *batch, int64_t polls, int32_t withheld_item);
 void qpic_batch_destroy(qpic_batch *batch);
 
 #ifdef __cplusplus

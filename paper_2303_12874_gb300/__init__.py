@@ -18,7 +18,7 @@ _lib = None
 
 # revision tag of the gather+push+deposit kernel; measured DRAM traffic stored
 # under profiles/ is only reported while it matches
-KERNEL_REV = "gpd-v12"
+KERNEL_REV = "gpd-v14"
 
 QPIC_YEE, QPIC_DUAL = 0, 1
 QPIC_FP64, QPIC_FP32_FIXED, QPIC_FP32_FATOMIC = 0, 1, 2
@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
         ("filter_tol", ctypes.c_double), ("periodic_z", ctypes.c_int32),
         ("moving_window", ctypes.c_int32), ("window_v", ctypes.c_double),
         ("tile_z", ctypes.c_int32), ("tile_r", ctypes.c_int32), ("sort_period", ctypes.c_int32),
-        ("track_work", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_particles", ctypes.c_int64),
+        ("particles_per_thread", ctypes.c_int32), ("track_work", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_particles", ctypes.c_int64),
         ("cuda_stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
     ]
@@ -112,6 +112,8 @@ def _declare(L):
     L.qpic_batch_cycle.restype = _I
     L.qpic_batch_last_error.argtypes = [_P]
     L.qpic_batch_last_error.restype = ctypes.c_char_p
+    L.qpic_batch_set_wait.argtypes = [_P, ctypes.c_int64, _I]
+    L.qpic_batch_set_wait.restype = ctypes.c_int
     L.qpic_batch_destroy.argtypes = [_P]
     L.qpic_batch_destroy.restype = None
     L.qpic_gauss_residual.argtypes = [_P, _D, _I]
@@ -239,7 +241,9 @@ def reduced_integrate_device(ptrs, n, a0, omega_p, k_perp, v_phi, t0, dt, nsteps
 
 
 class Batch:
-    """Independent runs advanced together by one CUDA graph launch per cycle."""
+    """Independent runs advanced together by one CUDA graph launch per cycle
+    (per step: Faraday per run, one persistent particle-phase launch per group
+    of runs, then filter, Ampere and sort per run)."""
 
     def __init__(self, sims, stream=None):
         self.L = load()
@@ -260,6 +264,11 @@ class Batch:
         if st != 0:
             raise QpicError("qpic_batch_step: %s %s" % (STATUS.get(st, st),
                                                        self.L.qpic_batch_last_error(self.h).decode()))
+
+    def set_wait(self, polls, withheld_item=-1):
+        st = self.L.qpic_batch_set_wait(self.h, int(polls), int(withheld_item))
+        if st != 0:
+            raise QpicError("qpic_batch_set_wait: %s" % STATUS.get(st, st))
 
     def close(self):
         if getattr(self, "h", None):
@@ -300,6 +309,7 @@ class Sim:
     def __init__(self, nz, nr, dz, dr, n_modes=2, dt=0.0, cfl_frac=0.9, solver="dual", n_coef=16,
                  fit_band=0.8, jz_filter=True, filter_tol=1e-16, periodic=True,
                  moving_window=False, window_v=1.0, tile_z=16, tile_r=8, sort_period=2,
+                 particles_per_thread=8,
                  track_work=False, seed=1, max_particles=0, stream=None, torch_alloc=False,
                  precision=QPIC_FP32_FIXED):
         self.L = load()
@@ -313,6 +323,7 @@ class Sim:
         cfg.jz_filter, cfg.filter_tol = int(jz_filter), filter_tol
         cfg.periodic_z, cfg.moving_window, cfg.window_v = int(periodic), int(moving_window), window_v
         cfg.tile_z, cfg.tile_r, cfg.sort_period = tile_z, tile_r, sort_period
+        cfg.particles_per_thread = particles_per_thread
         # track_work: False/0 off, True/1 modal work (Eq. 16), 2 directional work (Eq. 17)
         cfg.track_work, cfg.seed, cfg.max_particles = int(track_work), seed, max_particles
         if stream is not None:

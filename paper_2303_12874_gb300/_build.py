@@ -15,10 +15,15 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqpic.so")
 SOURCES = ["api.cu", "k_fields.cu", "k_particles.cu", "host_numerics.cpp", "noalloc.cu", "k_fp64.cu",
            "k_reduced.cu"]
-# the particle kernel, one object per (mode parts, float-atomic deposit) so that
-# the instantiations compile in parallel: (object name, defines)
-GPD_OBJECTS = [("gpd_np%d_fa%d" % (np_, fa), ["-DGPD_NP=%d" % np_, "-DGPD_FA=%d" % fa])
-               for np_ in (1, 3, 5, 7) for fa in (0, 1)]
+# the particle kernel, one object per (mode parts, deposit variant or batched
+# phase, group of tile shapes) so that the instantiations compile in parallel:
+# (object name, defines).  The kernels for 5 and 7 parts take about a minute
+# per tile shape, so they get one object per shape.
+_SHAPES = {1: (31,), 3: (31,), 5: (1, 2, 4, 8, 16), 7: (1, 2, 4, 8, 16)}
+GPD_OBJECTS = [("gpd_np%d_%s_s%d" % (np_, kind, m),
+                ["-DGPD_NP=%d" % np_, "-DGPD_FA=%d" % fa, "-DGPD_BATCH=%d" % bt, "-DGPD_SHAPES=%d" % m])
+               for np_ in (1, 3, 5, 7) for kind, fa, bt in (("fa0", 0, 0), ("fa1", 1, 0), ("batch", 0, 1))
+               for m in _SHAPES[np_]]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -57,7 +62,8 @@ def build(force=False, verbose=False, extra=()):
             print(r.stdout + r.stderr)
         return obj
 
-    jobs = [("gpd_inst.cu", name, defs) for name, defs in GPD_OBJECTS] + list(SOURCES)
+    # the longest translation units first
+    jobs = [("gpd_inst.cu", name, defs) for name, defs in GPD_OBJECTS[::-1]] + list(SOURCES)
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, jobs))
     tmp = LIB + ".tmp%d" % os.getpid()

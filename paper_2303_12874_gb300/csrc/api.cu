@@ -318,6 +318,7 @@ qpic_status qpic_default_config(qpic_config *cfg)
     cfg->tile_z = 16;
     cfg->tile_r = 8;
     cfg->sort_period = 2;
+    cfg->particles_per_thread = 8;
     cfg->seed = 1;
     return QPIC_OK;
 }
@@ -393,6 +394,8 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
         return bad(QPIC_EINVAL, "tile_z x tile_r: one of 16x8, 32x8, 8x8, 16x16, 32x4");
     c->halo = 1;
     c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 2;
+    c->ppt = cfg->particles_per_thread > 0 ? cfg->particles_per_thread : 8;
+    if (c->ppt > 8) return bad(QPIC_EINVAL, "particles_per_thread: 1..8");
     FieldGeom &g = c->g;
     g.nz = cfg->nz; g.nr = cfg->nr; g.nm = cfg->n_modes; g.nparts = 2 * cfg->n_modes - 1;
     g.periodic = cfg->periodic_z ? 1 : 0;
@@ -1162,9 +1165,13 @@ qpic_status qpic_kernel_times(qpic_ctx *c, int32_t n, double *ms, int64_t *launc
 
 // ---------------------------------------------------------------- batches
 // A batch advances many independent runs with one graph launch per cycle of
-// `period` steps (the sort period): at creation each run's cycle is captured
-// from its own stream, forked from and joined to the batch stream, so the runs
-// are parallel branches of a single CUDA graph.
+// steps.  At creation the cycle is captured once.  Each step has three
+// phases: Faraday and the step's epoch on each run's own stream (parallel
+// branches of the graph); then one persistent launch per group of runs with
+// the same mode count and tile shape, walking the (run, tile) work list of
+// the particle phase -- gather, push and deposit, then the current
+// reduction, with bounded waits between them (k_batch_particles); then the
+// J_z filter, Ampere and the sort again on the runs' own streams.
 
 }  // extern "C"
 
@@ -1179,13 +1186,28 @@ struct qpic_batch {
     int period = 2;
     bool own_main = false;
     std::vector<long long> kernels_per_cycle;
+    long long batch_kernels_per_cycle = 0;
+    // the batched particle phase: runs grouped by (mode parts, tile shape), at
+    // most BATCH_GROUP runs per group; per group the tile prefix over its runs,
+    // its work-list counter and one device run table per step of the cycle
+    struct Group {
+        int nparts = 0, tz = 0, tr = 0;
+        std::vector<int> members;      // indices into runs
+        int *d_prefix = nullptr, *d_head = nullptr;
+        std::vector<void *> d_tables;
+    };
+    std::vector<Group> groups;
+    std::vector<int *> gdone;          // per run: per tile, epoch of its last stored deposit
+    qpic::BatchCtlHost *d_ctl = nullptr;
+    int blocks = 304;
     std::string err;
 };
+
+static const int BATCH_GROUP = 64;   // runs per persistent launch (its constant-memory run table)
 
 static qpic_status batch_fail(qpic_batch *b, qpic_status s, const std::string &m)
 {
     b->err = m;
-    cudaGetLastError();               // leave no pending error for unrelated calls
     return s;
 }
 
@@ -1200,6 +1222,13 @@ void qpic_batch_destroy(qpic_batch *b)
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    for (auto &g : b->groups) {
+        cudaFree(g.d_prefix);
+        cudaFree(g.d_head);
+        for (void *t : g.d_tables) cudaFree(t);
+    }
+    for (int *p : b->gdone) cudaFree(p);
+    cudaFree(b->d_ctl);
     if (b->own_main && b->main) cudaStreamDestroy(b->main);
     delete b;
 }
@@ -1210,6 +1239,14 @@ int32_t qpic_batch_cycle(const qpic_batch *b)
 }
 
 const char *qpic_batch_last_error(const qpic_batch *b) { return b ? b->err.c_str() : "no batch"; }
+
+qpic_status qpic_batch_set_wait(qpic_batch *b, int64_t polls, int32_t withheld_item)
+{
+    if (!b || !b->d_ctl || polls < 0) return QPIC_EINVAL;
+    const qpic::BatchCtlHost h{(long long)polls, withheld_item < 0 ? -1 : (int)withheld_item, 0};
+    cudaStreamSynchronize(b->main);
+    return cudaMemcpy(b->d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice) == cudaSuccess ? QPIC_OK : QPIC_ECUDA;
+}
 
 qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_stream, qpic_batch **out)
 {
@@ -1225,28 +1262,107 @@ qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_strea
             return batch_fail(b, QPIC_ECUDA, "batch stream creation failed");
         b->own_main = true;
     }
-    const int all = QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE |
-                    QPIC_STAGE_WINDOW | QPIC_STAGE_SORT;
     // a sort swaps the particle buffers on the host; a captured cycle must hold
-    // an even number of sorts so that each replay starts from the buffers the
-    // graph was recorded with
-    b->period = 2 * (runs[0]->sort_period > 1 ? runs[0]->sort_period : 1);
+    // an even number of sorts of every run, so that each replay starts from the
+    // buffers the graph was recorded with: the cycle is twice the least common
+    // multiple of the runs' sort periods
+    long long lcm = 1;
     for (int k = 0; k < n; k++) {
         qpic_ctx *c = runs[k];
-        if (!c) { b->err = "null run"; return QPIC_EINVAL; }
-        if (c->fp64 || c->cfg.moving_window || c->profile) {
-            b->err = "batch runs: FP32 path, periodic box, profiling off";
-            return QPIC_EINVAL;
-        }
-        if (c->sort_period != runs[0]->sort_period) { b->err = "batch runs need one sort period"; return QPIC_EINVAL; }
-        if (check_device(c) != QPIC_OK) { b->err = "batch runs: " + c->err; return QPIC_ESTATE; }
+        if (!c) return batch_fail(b, QPIC_EINVAL, "null run");
+        if (c->fp64 || c->fatomic || c->cfg.moving_window || c->profile)
+            return batch_fail(b, QPIC_EINVAL, "batch runs: FP32 fixed-point path, periodic box, profiling off");
+        if (check_device(c) != QPIC_OK) return batch_fail(b, QPIC_ESTATE, "batch runs: " + c->err);
+        const long long sp = c->sort_period > 1 ? c->sort_period : 1;
+        // a particle drifts at most one cell per step from the tile it was
+        // sorted into, and its deposit reaches two nodes further: the current
+        // reduction of a tile then needs the particle items of the 3 x 3 tiles
+        // around it only while the sort period is below the tile size minus 2
+        if (sp + 3 > std::min(c->TZ, c->TR))
+            return batch_fail(b, QPIC_EINVAL, "batch runs: sort period must be at most min(TZ, TR) - 3");
+        long long a = lcm, bb = sp;
+        while (bb) { const long long t = a % bb; a = bb; bb = t; }
+        lcm = lcm / a * sp;
+        if (lcm > 8) return batch_fail(b, QPIC_EINVAL, "batch runs: sort periods whose cycle exceeds 16 steps");
         b->runs.push_back(c);
     }
-    // bring every run to a cycle boundary, then drain all work
+    b->period = (int)(2 * lcm);
+    const int all = QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE |
+                    QPIC_STAGE_WINDOW | QPIC_STAGE_SORT;
+    // bring every run to a cycle boundary with its particles sorted (a run
+    // stepped on its own does the same steps: a sort falls on every cycle
+    // boundary), then drain all work
     for (qpic_ctx *c : b->runs) {
-        while (c->nstep % b->period) run_one_step(c, all);
-        if (c->n_tail > 0) launch_sort(c);
+        for (int guard = 0; c->nstep % b->period || c->n_tail > 0; guard++) {
+            if (guard > 2 * b->period) return batch_fail(b, QPIC_ESTATE, "batch runs: particles stay unsorted");
+            run_one_step(c, all);
+        }
         cudaStreamSynchronize(c->stream);
+    }
+    // groups of the particle phase, per-tile publication flags, control word
+    int nsm = 152;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    b->blocks = 2 * nsm;                          // resident blocks: two per SM
+    b->gdone.assign(n, nullptr);
+    for (int k = 0; k < n; k++) {
+        qpic_ctx *c = b->runs[k];
+        const size_t nt = (size_t)c->ntz * c->ntr;
+        if (cudaMalloc(&b->gdone[k], nt * sizeof(int)) != cudaSuccess)
+            return batch_fail(b, QPIC_ENOMEM, "batch flags");
+        cudaMemset(b->gdone[k], 0xff, nt * sizeof(int));
+        bool placed = false;
+        for (auto &g : b->groups)
+            if (g.nparts == c->g.nparts && g.tz == c->TZ && g.tr == c->TR && (int)g.members.size() < BATCH_GROUP) {
+                g.members.push_back(k);
+                placed = true;
+                break;
+            }
+        if (!placed) {
+            qpic_batch::Group g;
+            g.nparts = c->g.nparts; g.tz = c->TZ; g.tr = c->TR;
+            g.members.push_back(k);
+            b->groups.push_back(g);
+        }
+    }
+    if (cudaMalloc(&b->d_ctl, sizeof(qpic::BatchCtlHost)) != cudaSuccess)
+        return batch_fail(b, QPIC_ENOMEM, "batch control word");
+    const qpic::BatchCtlHost ctl = qpic::batch_ctl_default();
+    cudaMemcpy(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice);
+    // the run tables hold each run's particle buffers at each step of the
+    // cycle: the buffers swap after every sort, which is due after step s
+    // when (nstep + s + 1) is a multiple of the run's period
+    const size_t rb = qpic::batch_run_bytes();
+    for (auto &g : b->groups) {
+        const int m = (int)g.members.size();
+        std::vector<int> prefix(m + 1, 0);
+        for (int i = 0; i < m; i++) {
+            qpic_ctx *c = b->runs[g.members[i]];
+            prefix[i + 1] = prefix[i] + c->ntz * c->ntr;
+        }
+        if (cudaMalloc(&g.d_prefix, (m + 1) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&g.d_head, sizeof(int)) != cudaSuccess)
+            return batch_fail(b, QPIC_ENOMEM, "batch work list");
+        cudaMemcpy(g.d_prefix, prefix.data(), (m + 1) * sizeof(int), cudaMemcpyHostToDevice);
+        std::vector<char> host((size_t)m * rb);
+        for (int s2 = 0; s2 < b->period; s2++) {
+            for (int i = 0; i < m; i++) {
+                const int k = g.members[i];
+                qpic_ctx *c = b->runs[k];
+                const long long sp = c->sort_period > 1 ? c->sort_period : 1;
+                long long sorts = 0;                  // sorts of this run before step s2 of the cycle
+                for (int q = 0; q < s2; q++)
+                    if ((c->nstep + q + 1) % sp == 0) sorts++;
+                qpic::batch_fill_run(c, (sorts & 1) ? c->ps : c->p, b->gdone[k], host.data() + (size_t)i * rb);
+            }
+            void *t = nullptr;
+            if (cudaMalloc(&t, (size_t)m * rb) != cudaSuccess) return batch_fail(b, QPIC_ENOMEM, "batch tables");
+            cudaMemcpy(t, host.data(), (size_t)m * rb, cudaMemcpyHostToDevice);
+            g.d_tables.push_back(t);
+        }
     }
     b->side.resize(n);
     b->ev_join.resize(n);
@@ -1259,32 +1375,72 @@ qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_strea
         return batch_fail(b, QPIC_ECUDA, "event creation failed");
     cudaError_t e = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-    cudaEventRecord(b->ev_fork, b->main);
-    b->kernels_per_cycle.resize(n);
+    b->kernels_per_cycle.assign(n, 0);
+    std::vector<long long> nk0(n), ns0(n);
+    std::vector<Particles> p0(n);
+    std::vector<cudaStream_t> old(n);
     for (int k = 0; k < n; k++) {
         qpic_ctx *c = b->runs[k];
-        cudaStream_t old = c->stream;
+        nk0[k] = c->n_kernels; ns0[k] = c->nstep; p0[k] = c->p; old[k] = c->stream;
         c->stream = b->side[k];
-        cudaStreamWaitEvent(c->stream, b->ev_fork, 0);
-        const long long nk0 = c->n_kernels, ns0 = c->nstep;
-        const Particles p0 = c->p;
-        for (int s2 = 0; s2 < b->period; s2++) run_one_step(c, all);
-        b->kernels_per_cycle[k] = c->n_kernels - nk0;
-        c->n_kernels = nk0;                 // captured, not executed
-        c->nstep = ns0;
-        cudaEventRecord(b->ev_join[k], c->stream);
-        cudaStreamWaitEvent(b->main, b->ev_join[k], 0);
-        c->stream = old;
-        if (c->p.cell != p0.cell) {         // odd number of sorts in the cycle
-            cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(b->main, &g);
-            if (g) cudaGraphDestroy(g);
-            Particles t = c->p; c->p = c->ps; c->ps = t;
-            return batch_fail(b, QPIC_EINVAL, "captured cycle holds an odd number of sorts");
+    }
+    // fork the runs' branches off the batch stream, then join them back
+    auto fork = [&]() {
+        cudaEventRecord(b->ev_fork, b->main);
+        for (int k = 0; k < n; k++) cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+    };
+    auto join = [&]() {
+        for (int k = 0; k < n; k++) {
+            cudaEventRecord(b->ev_join[k], b->side[k]);
+            cudaStreamWaitEvent(b->main, b->ev_join[k], 0);
         }
+    };
+    bool shape_ok = true;
+    for (int s2 = 0; s2 < b->period; s2++) {
+        fork();
+        for (qpic_ctx *c : b->runs) {
+            launch_faraday(c);
+            qpic::launch_epoch(c);
+        }
+        join();
+        for (auto &g : b->groups) {
+            cudaMemsetAsync(g.d_head, 0, sizeof(int), b->main);
+            if (!qpic::launch_batch_particles(g.nparts, g.tz, g.tr, g.d_tables[s2], g.d_prefix,
+                                              (int)g.members.size(), g.d_head, b->d_ctl, b->blocks, b->main))
+                shape_ok = false;
+        }
+        fork();
+        for (qpic_ctx *c : b->runs) {
+            c->j_filtered = false;
+            if (!c->taps.empty()) launch_jfilter(c);
+            c->j_filtered = !c->taps.empty();
+            launch_ampere(c);
+            c->nstep++;
+            const long long sp = c->sort_period > 1 ? c->sort_period : 1;
+            if (c->nstep % sp == 0) launch_sort(c);
+        }
+        join();
+    }
+    b->batch_kernels_per_cycle = (long long)b->period * (long long)b->groups.size();
+    bool odd = false;
+    for (int k = 0; k < n; k++) {
+        qpic_ctx *c = b->runs[k];
+        b->kernels_per_cycle[k] = c->n_kernels - nk0[k];
+        c->n_kernels = nk0[k];                  // captured, not executed
+        c->nstep = ns0[k];
+        c->stream = old[k];
+        if (c->p.cell != p0[k].cell) odd = true;
     }
     e = cudaStreamEndCapture(b->main, &b->graph);
+    if (odd) {
+        for (int k = 0; k < n; k++) {
+            qpic_ctx *c = b->runs[k];
+            if (c->p.cell != p0[k].cell) { Particles t = c->p; c->p = c->ps; c->ps = t; }
+        }
+        return batch_fail(b, QPIC_EINVAL, "captured cycle holds an odd number of sorts");
+    }
     if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    if (!shape_ok) return batch_fail(b, QPIC_EINVAL, "batch runs: tile shape without a batched particle kernel");
     e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
     return QPIC_OK;
@@ -1293,7 +1449,7 @@ qpic_status qpic_batch_create(qpic_ctx *const *runs, int32_t n, void *cuda_strea
 qpic_status qpic_batch_step(qpic_batch *b, int32_t nsteps)
 {
     if (!b || !b->exec || nsteps < 0) return QPIC_EINVAL;
-    if (nsteps % b->period) { b->err = "nsteps must be a multiple of the cycle (2 x sort period)"; return QPIC_EINVAL; }
+    if (nsteps % b->period) { b->err = "nsteps must be a multiple of the cycle (qpic_batch_cycle)"; return QPIC_EINVAL; }
     for (qpic_ctx *c : b->runs) cudaStreamSynchronize(c->stream);   // earlier work of the runs
     for (qpic_ctx *c : b->runs) cudaMemsetAsync(c->d_err, 0, sizeof(int), b->main);
     for (int r = 0; r < nsteps / b->period; r++) {
@@ -1302,15 +1458,21 @@ qpic_status qpic_batch_step(qpic_batch *b, int32_t nsteps)
     }
     cudaError_t e = cudaStreamSynchronize(b->main);
     if (e != cudaSuccess) return batch_fail(b, QPIC_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    qpic_status st = QPIC_OK;
     for (size_t k = 0; k < b->runs.size(); k++) {
         qpic_ctx *c = b->runs[k];
         c->nstep += nsteps;
         c->n_kernels += b->kernels_per_cycle[k] * (nsteps / b->period);
+        if (k == 0) c->n_kernels += b->batch_kernels_per_cycle * (nsteps / b->period);
         int err = 0;
         cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-        if (err & 1) { b->err = "fixed-point overflow in run " + std::to_string(k); return QPIC_EOVERFLOW; }
+        if ((err & 4) && st == QPIC_OK) {
+            b->err = "run " + std::to_string(k) + ": a dependency wait of the particle phase gave up";
+            st = QPIC_ETIMEOUT;
+        }
+        if ((err & 1) && st == QPIC_OK) { b->err = "fixed-point overflow in run " + std::to_string(k); st = QPIC_EOVERFLOW; }
     }
-    return QPIC_OK;
+    return st;
 }
 
 }  // extern "C"

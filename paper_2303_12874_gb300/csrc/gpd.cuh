@@ -39,6 +39,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "qpic_internal.h"
 
 namespace qpic {
@@ -52,6 +54,7 @@ struct PArgs {
     int TZ, TR, ntz, ntr, H, lTZ, lTR;
     float qscale;
     int track_work;
+    int chunk;       // particles per chunk of a tile: 256 x (particles per thread) - 1 (<= 2047)
 };
 
 static PArgs pargs(const qpic_ctx *c)
@@ -67,6 +70,7 @@ static PArgs pargs(const qpic_ctx *c)
     a.lTZ = __builtin_ctz(c->TZ); a.lTR = __builtin_ctz(c->TR);
     a.qscale = c->qscale;
     a.track_work = c->cfg.track_work;
+    a.chunk = 256 * c->ppt - 1;
     return a;
 }
 
@@ -149,8 +153,6 @@ struct TileGeom {
     static constexpr size_t SMEM = (size_t)JPAD * 8 /* hi, lo int32 planes */ + (size_t)JPAD * 8 /* int64 plane */ +
                                    (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
     static_assert((JPAD * 8) % 16 == 0, "float4 tile alignment");
-    // particles one thread handles between flushes of its register sums: the
-
 };
 
 template <int NP, int TZ, int TR>
@@ -645,23 +647,25 @@ struct FastSum {
 
 // ------------------------------------------------------------ the GPD kernel
 // Particle order inside a tile.  The n particles of a tile (sorted by cell) are
-// taken in chunks of at most GPD_C = 2047 (the int32 accumulator planes are
-// drained into int64 after each, FX_SHIFT).  In a chunk of rc particles every
-// thread takes kc = ceil(rc / GPD_T) consecutive particles (nt = rc / kc
+// taken in chunks of at most C = 256 p - 1 particles, p the particles per
+// thread (1..8, so C <= GPD_C = 2047: the int32 accumulator planes are drained
+// into int64 after each chunk, FX_SHIFT).  In a chunk of rc particles every
+// thread takes kc = ceil(rc / GPD_T) <= p consecutive particles (nt = rc / kc
 // threads take kc, thread nt the rem = rc - nt kc left), so one thread's moves
-// mostly share a cell (FastSum).  Thread t's k-th particle of a chunk is
-// q0 + t kc + k.
+// mostly share a cell (FastSum) and about ppc / kc threads work on one cell.
+// Thread t's k-th particle of a chunk is q0 + t kc + k.
 constexpr int GPD_T = 256, GPD_C = 2047;
+static_assert(GPD_T == 256 && GPD_C == 8 * GPD_T - 1, "chunk sizes assume 256 threads");
 
 struct Chunk { int q0, rc, kc, nt, rem; };
 
-__host__ __device__ __forceinline__ int tile_nchunks(int n) { return (n + GPD_C - 1) / GPD_C; }
+__host__ __device__ __forceinline__ int tile_nchunks(int n, int chunk) { return (n + chunk - 1) / chunk; }
 
-__host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c)
+__host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c, int chunk)
 {
     Chunk k;
-    k.q0 = c * GPD_C;
-    k.rc = n - k.q0 < GPD_C ? n - k.q0 : GPD_C;
+    k.q0 = c * chunk;
+    k.rc = n - k.q0 < chunk ? n - k.q0 : chunk;
     k.kc = (k.rc + GPD_T - 1) / GPD_T;
     k.nt = k.rc / k.kc;
     k.rem = k.rc - k.nt * k.kc;
@@ -760,39 +764,52 @@ __device__ __forceinline__ void gpd_global_one(const Particles &P, long long idx
 
 // FA: the FP32 float-atomic variant (every deposit goes to the global FP32
 // current Jfa with float atomics; the fixed-point accumulators are unused)
+// everything one run's particle kernel reads and writes
+struct GpdArgs {
+    Particles P;
+    const float *E, *Bb;
+    unsigned long long *J;
+    float *Jfa;
+    unsigned long long *Jtile;
+    int *tstamp, *jdirty;
+    const int *d_epoch;
+    const int32_t *offsets;
+    const long long *dcount;
+    PArgs a;
+};
+
+// One block of the particle kernel: tile bid (bid < ntiles) or a chunk of the
+// particles appended since the last sort (bid >= ntiles).  sraw: the block's
+// dynamic shared memory (TileGeom::SMEM bytes).
 template <int NP, int TZ, int TR, bool FA>
-__global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__restrict__ E,
-                                                 const float *__restrict__ Bb,
-                                                 unsigned long long *__restrict__ J,
-                                                 float *__restrict__ Jfa,
-                                                 unsigned long long *__restrict__ Jtile,
-                                                 int *__restrict__ tstamp, int *__restrict__ jdirty,
-                                                 const int *__restrict__ d_epoch,
-                                                 const int32_t *__restrict__ offsets,
-                                                 const long long *__restrict__ dcount, PArgs a,
-                                                 int ntiles, int tail_chunk)
+__device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, int tail_chunk,
+                                          unsigned long long *sraw)
 {
     using G = TileGeom<NP, TZ, TR>;
     constexpr int NM = (NP + 1) / 2;
-    extern __shared__ __align__(16) unsigned long long sraw[];
+    const Particles P = g.P;
+    const float *__restrict__ E = g.E;
+    const float *__restrict__ Bb = g.Bb;
+    const PArgs a = g.a;
+    const int32_t *__restrict__ offsets = g.offsets;
     long long begin, end;
-    const bool tile_mode = blockIdx.x < (unsigned)ntiles;
+    const bool tile_mode = bid < ntiles;
     int tz0 = 0, tr0 = 0;
     if (tile_mode) {
-        const int t = blockIdx.x;
+        const int t = bid;
         begin = offsets[(size_t)t * (TZ * TR)];
         end = offsets[(size_t)(t + 1) * (TZ * TR)];
         if (begin == end) return;
         tz0 = (t / a.ntr) * TZ;
         tr0 = (t % a.ntr) * TR;
     } else {
-        const long long nsorted = dcount[1], np = dcount[0];
-        begin = nsorted + (long long)(blockIdx.x - ntiles) * tail_chunk;
+        const long long nsorted = g.dcount[1], np = g.dcount[0];
+        begin = nsorted + (long long)(bid - ntiles) * tail_chunk;
         end = min(begin + tail_chunk, np);
         if (begin >= end) return;
     }
-    const GlobAcc<NP> gacc{E, Bb, J, jdirty, d_epoch, a};
-    const FloatAcc facc{Jfa, a};
+    const GlobAcc<NP> gacc{E, Bb, g.J, g.jdirty, g.d_epoch, a};
+    const FloatAcc facc{g.Jfa, a};
     if (!tile_mode || a.nzp < 2 * G::JW) {
         // particles appended since the last sort, or a box too short for the
         // staged tile: every access goes to global memory
@@ -828,8 +845,9 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
         }
         cp_async_commit();
     };
-    const int nch = tile_nchunks(n);
-    Chunk C = tile_chunk(n, 0);
+    const int chunk = a.chunk;
+    const int nch = tile_nchunks(n, chunk);
+    Chunk C = tile_chunk(n, 0, chunk);
     int cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
     int q = C.q0 + tid * C.kc;
     prefetch(0, cnt > 0 ? q : -1);
@@ -864,7 +882,7 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
     fs.clear();
     for (int ch = 0; ch < nch; ch++) {
         if (ch > 0) {                                              // chunks beyond the first
-            C = tile_chunk(n, ch);
+            C = tile_chunk(n, ch, chunk);
             cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
             q = C.q0 + tid * C.kc;
             prefetch(0, cnt > 0 ? q : -1);
@@ -951,10 +969,17 @@ __global__ void __launch_bounds__(GPD_T, 2) k_gpd(Particles P, const float *__re
     // the tile's accumulators (the int64 plane plus the queued moves' int32
     // parts) go to its own scratch block with plain stores; the reduction
     // kernel sums the tiles that cover each node
-    unsigned long long *dst = Jtile + (size_t)blockIdx.x * G::JWORDS;
+    unsigned long long *dst = g.Jtile + (size_t)bid * G::JWORDS;
     for (int k = tid; k < G::JWORDS; k += blockDim.x)
         dst[k] = sJ64[k] + (unsigned long long)(((long long)(int)sJh[k] << FX_SHIFT) + (long long)(int)sJl[k]);
-    if (tid == 0) tstamp[blockIdx.x] = *d_epoch;
+    if (tid == 0) g.tstamp[bid] = *g.d_epoch;
+}
+
+template <int NP, int TZ, int TR, bool FA>
+__global__ void __launch_bounds__(GPD_T, 2) k_gpd(GpdArgs g, int ntiles, int tail_chunk)
+{
+    extern __shared__ __align__(16) unsigned long long sraw[];
+    gpd_block<NP, TZ, TR, FA>(g, blockIdx.x, ntiles, tail_chunk, sraw);
 }
 
 template <int NP, int TZ, int TR, bool FA>
@@ -962,23 +987,12 @@ static void gpd_launch2(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int c
 {
     const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
     cudaFuncSetAttribute(k_gpd<NP, TZ, TR, FA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gpd<NP, TZ, TR, FA><<<grid, GPD_T, sm, c->stream>>>(c->p, c->E, c->Bb, c->Jacc, c->Jfa, c->Jtile,
-                                                    c->tstamp, c->jdirty, c->d_epoch, c->offsets, c->d_count, a,
-                                                    ntiles, chunk);
+    const GpdArgs g{c->p, c->E, c->Bb, c->Jacc, c->Jfa, c->Jtile, c->tstamp, c->jdirty, c->d_epoch,
+                    c->offsets, c->d_count, a};
+    k_gpd<NP, TZ, TR, FA><<<grid, GPD_T, sm, c->stream>>>(g, ntiles, chunk);
 }
 
 
-template <int NP, bool FA>
-static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk)
-{
-    if (c->TZ == 16 && c->TR == 8) gpd_launch2<NP, 16, 8, FA>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 32 && c->TR == 8) gpd_launch2<NP, 32, 8, FA>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 8 && c->TR == 8) gpd_launch2<NP, 8, 8, FA>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 16 && c->TR == 16) gpd_launch2<NP, 16, 16, FA>(c, a, grid, ntiles, chunk);
-    else if (c->TZ == 32 && c->TR == 4) gpd_launch2<NP, 32, 4, FA>(c, a, grid, ntiles, chunk);
-    else return false;
-    return true;
-}
 // ------------------------------------------------------------ current reduction + decode
 // One thread per node of a tile's core (its TZ x TR cells; the last tile row
 // also owns the wall row j = nr) and current component, all NP parts of that
@@ -988,30 +1002,58 @@ static bool gpd_dispatch_tile(qpic_ctx *c, const PArgs &a, int grid, int ntiles,
 // mark equals the step's epoch), the global accumulator (then cleared), summed
 // in a fixed order in int64 and turned into FP32 current with the per-row
 // finite-volume factor.
-// as many blocks per SM as its 2048 threads allow: the kernel is latency
-// bound, and occupancy matters more than the few registers it then spills
-template <int NP, int TZ, int TR>
-__global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(const unsigned long long *__restrict__ Jtile,
-                                                         const int *__restrict__ tstamp,
-                                                         const int *__restrict__ d_epoch,
-                                                         unsigned long long *__restrict__ Jacc,
-                                                         const int *__restrict__ jdirty,
-                                                         float *__restrict__ Jf,
-                                                         const float *__restrict__ rowf, PArgs a,
-                                                         long long tile_words, float inv_qscale,
-                                                         int tiles_ok, int *err)
+
+// everything one run's current reduction reads and writes
+struct JredArgs {
+    const unsigned long long *Jtile;
+    const int *tstamp, *d_epoch;
+    unsigned long long *Jacc;
+    const int *jdirty;
+    float *Jf;
+    const float *rowf;
+    PArgs a;
+    long long tile_words;
+    float inv_qscale;
+    int tiles_ok;
+    int *err;
+};
+
+// a load of a word that another block of the same launch may have stored
+// (COH: from L2, never through the non-coherent read-only path)
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_maybe_cg(const T *p)
 {
+    if constexpr (COH) return __ldcg(p);
+    else return *p;
+}
+
+// Work item w of tile t of the reduction: component w / (TZ TR) of node
+// w % (TZ TR) of the tile's core, every row of it that the tile owns.  COH:
+// the tile blocks and stamps were stored by other blocks of the same launch
+// (the batched particle phase), so they are read coherently.
+template <int NP, int TZ, int TR, bool COH = false>
+__device__ __forceinline__ void jreduce_work(const JredArgs g, int t, int w)
+{
+    const unsigned long long *__restrict__ Jtile = g.Jtile;
+    const int *__restrict__ tstamp = g.tstamp;
+    unsigned long long *__restrict__ Jacc = g.Jacc;
+    float *__restrict__ Jf = g.Jf;
+    const float *__restrict__ rowf = g.rowf;
+    const PArgs a = g.a;
+    const long long tile_words = g.tile_words;
+    const float inv_qscale = g.inv_qscale;
+    const int tiles_ok = g.tiles_ok;
+    int *err = g.err;
     constexpr int H = 1, JW = TZ + 2 * H + 3, JR = TR + 2 * H + 3, NN = TZ * TR;
-    const int t = blockIdx.x;
     const int tzi = t / a.ntr, tri = t - tzi * a.ntr;
     const int tz0 = tzi * TZ, tr0 = tri * TR;
-    const int comp = threadIdx.x / NN, node = threadIdx.x - comp * NN;
+    const int comp = w / NN, node = w - comp * NN;
     const int c = node % TZ, r0 = node / TZ;
     if (c >= a.nzp - tz0) return;                          // past the last (partial) column
     const int CR = (tri == a.ntr - 1) ? a.nr + 1 - tr0 : TR;
     const int i = tz0 + c;
-    const int epoch = *d_epoch;
-    const bool dirty = jdirty[t] == epoch;
+    const int epoch = *g.d_epoch;
+    const bool dirty = ld_maybe_cg<COH>(g.jdirty + t) == epoch;
     // candidate blocks: geometry first, per z neighbour and per r neighbour
     // (3 + 3), then combined; their words are loaded together with the stamps
     // that say whether they were written this step (no wait between)
@@ -1038,7 +1080,7 @@ __global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(c
         const int ez = d / 3, er = d % 3;
         kbase[d] = zpart[ez] + rpart[er];
         geo[d] = zok[ez] && rok[er];
-        ok[d] = geo[d] && tstamp[ztile[ez] + tri + er - 1] == epoch;
+        ok[d] = geo[d] && ld_maybe_cg<COH>(tstamp + ztile[ez] + tri + er - 1) == epoch;
     }
     int l = i - (int)a.zoff;
     l = l < 0 ? l + a.nzp : l;
@@ -1053,7 +1095,7 @@ __global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(c
 #pragma unroll
             for (int p = 0; p < NP; p++) {
                 const size_t q = (size_t)(comp * NP + p) * a.plane + q0;
-                v[p] = (long long)Jacc[q];
+                v[p] = (long long)ld_maybe_cg<COH>(Jacc + q);
                 Jacc[q] = 0ull;
             }
         }
@@ -1064,7 +1106,7 @@ __global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(c
                 const unsigned long long *src = Jtile + kbase[d] + lj * JW;
                 unsigned long long w[NP];
 #pragma unroll
-                for (int p = 0; p < NP; p++) w[p] = src[p * (JR * JW)];
+                for (int p = 0; p < NP; p++) w[p] = ld_maybe_cg<COH>(src + p * (JR * JW));
                 if (ok[d]) {
 #pragma unroll
                     for (int p = 0; p < NP; p++) v[p] += (long long)w[p];
@@ -1084,28 +1126,172 @@ __global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(c
     }
 }
 
+// as many blocks per SM as its 2048 threads allow: the kernel is latency
+// bound, and occupancy matters more than the few registers it then spills
+template <int NP, int TZ, int TR>
+__global__ void __launch_bounds__(3 * TZ * TR, 2048 / (3 * TZ * TR)) k_jreduce(JredArgs g)
+{
+    jreduce_work<NP, TZ, TR>(g, blockIdx.x, threadIdx.x);
+}
+
+// ------------------------------------------------------------ batched particle phase
+// One launch advances the particle phase of every run of a batch that shares
+// this mode count and tile shape.  Its work list holds first one particle
+// item per (run, tile) -- gather, push and deposit of the tile -- and then one
+// reduction item per (run, tile).  The blocks stay resident and take items in
+// list order from a counter.  A reduction item waits until the particle items
+// of the 3 x 3 tiles around it have published this step's epoch; every item
+// it waits on was taken earlier by a running block and waits on nothing, so
+// the waits end.  A wait gives up after ctl->spins polls: the run's error
+// word gets bit 2 (reported as QPIC_ETIMEOUT) and the item is skipped.
+struct BatchRun {
+    GpdArgs g;
+    JredArgs j;
+    int *gdone;      // per tile: epoch of its last stored deposit
+    int ntiles;
+};
+
+using BatchCtl = BatchCtlHost;     // spins: polls before a wait gives up; hold: item that publishes nothing
+
+template <int TZ, int TR>
+__device__ bool batch_wait(const BatchRun *R, int t, long long cap)
+{
+    const int ntr = R->g.a.ntr, ntz = R->g.a.ntz;
+    const int tzi = t / ntr, tri = t - (t / ntr) * ntr;
+    const int epoch = *R->g.d_epoch;
+    long long polls = 0;
+    for (int ez = -1; ez <= 1; ez++) {
+        int kz = tzi + ez;
+        kz = kz < 0 ? kz + ntz : (kz >= ntz ? kz - ntz : kz);
+        for (int er = -1; er <= 1; er++) {
+            const int kr = tri + er;
+            if (kr < 0 || kr >= ntr) continue;
+            const volatile int *f = R->gdone + kz * ntr + kr;
+            while (*f != epoch) {
+                if (++polls > cap) return false;
+                __nanosleep(100);
+            }
+        }
+    }
+    return true;
+}
+
+// the run table of the launch in flight, in constant memory so that the
+// kernel reads its fields like kernel parameters (copied in from a device
+// table by the launching stream right before the launch)
+constexpr int BATCH_MAX_RUNS = 64;
+static __constant__ __align__(16) unsigned char c_batch_runs[BATCH_MAX_RUNS * sizeof(BatchRun)];
+
+template <int NP, int TZ, int TR>
+__global__ void __launch_bounds__(GPD_T, 2) k_batch_particles(const int *__restrict__ tprefix, int nruns,
+                                                              int *__restrict__ head,
+                                                              const BatchCtl *__restrict__ ctl)
+{
+    const BatchRun *runs = reinterpret_cast<const BatchRun *>(c_batch_runs);
+    extern __shared__ __align__(16) unsigned long long sraw[];
+    __shared__ int s_item, s_ok;
+    const int total = tprefix[nruns];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= 2 * total) return;
+        const bool reduce = it >= total;
+        const int k = reduce ? it - total : it;
+        int lo = 0, hi = nruns;                    // tprefix[lo] <= k < tprefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tprefix[mid] <= k) lo = mid; else hi = mid;
+        }
+        const BatchRun *R = runs + lo;
+        const int t = k - tprefix[lo];
+        if (!reduce) {
+            gpd_block<NP, TZ, TR, false>(R->g, t, R->ntiles, 0, sraw);
+            __syncthreads();                        // every store of the tile is issued
+            if (threadIdx.x == 0 && it != ctl->hold) {
+                __threadfence();
+                atomicExch(R->gdone + t, *R->g.d_epoch);
+            }
+        } else {
+            if (threadIdx.x == 0) s_ok = batch_wait<TZ, TR>(R, t, ctl->spins);
+            __syncthreads();
+            if (s_ok) {
+                __threadfence();
+                for (int w = threadIdx.x; w < 3 * TZ * TR; w += blockDim.x)
+                    jreduce_work<NP, TZ, TR, true>(R->j, t, w);
+            } else if (threadIdx.x == 0) {
+                atomicOr(R->j.err, 4);
+            }
+        }
+        __syncthreads();                            // s_item and s_ok are reused
+    }
+}
+
+template <int NP, int TZ, int TR>
+static void batch_particles_launch2(const BatchRun *runs, const int *tprefix, int nruns, int *head,
+                                    const BatchCtl *ctl, int blocks, cudaStream_t st)
+{
+    const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
+    cudaFuncSetAttribute(k_batch_particles<NP, TZ, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaMemcpyToSymbolAsync(c_batch_runs, runs, (size_t)nruns * sizeof(BatchRun), 0, cudaMemcpyDeviceToDevice, st);
+    k_batch_particles<NP, TZ, TR><<<blocks, GPD_T, sm, st>>>(tprefix, nruns, head, ctl);
+}
+
+
 template <int NP, int TZ, int TR>
 static void jreduce_launch(qpic_ctx *c, const PArgs &a, int tiles_ok)
 {
-    k_jreduce<NP, TZ, TR><<<c->ntz * c->ntr, 3 * TZ * TR, 0, c->stream>>>(
-        c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
-        (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err);
+    const JredArgs g{c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
+                     (long long)gpd_tile_words(c->g.nparts, TZ, TR), 1.0f / c->qscale, tiles_ok, c->d_err};
+    k_jreduce<NP, TZ, TR><<<c->ntz * c->ntr, 3 * TZ * TR, 0, c->stream>>>(g);
 }
 
-template <int NP>
-static void jreduce_dispatch(qpic_ctx *c, const PArgs &a, int tiles_ok)
+
+// One launch per (mode parts, tile shape): defined and explicitly
+// instantiated in gpd_inst.cu, which the build compiles once per group of
+// instantiations so that they compile in parallel.
+template <int NP, int TZ, int TR, bool FA>
+void gpd_shape(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk);
+template <int NP, int TZ, int TR>
+void jreduce_shape(qpic_ctx *c, const PArgs &a, int tiles_ok);
+template <int NP, int TZ, int TR>
+void batch_shape(const BatchRun *runs, const int *tprefix, int nruns, int *head, const BatchCtl *ctl,
+                 int blocks, cudaStream_t st);
+
+// the supported tile shapes (TZ x TR): 16x8, 32x8, 8x8, 16x16, 32x4
+template <typename F>
+inline bool tile_dispatch(int tz, int tr, F &&f)
 {
-    if (c->TZ == 16 && c->TR == 8) jreduce_launch<NP, 16, 8>(c, a, tiles_ok);
-    else if (c->TZ == 32 && c->TR == 8) jreduce_launch<NP, 32, 8>(c, a, tiles_ok);
-    else if (c->TZ == 8 && c->TR == 8) jreduce_launch<NP, 8, 8>(c, a, tiles_ok);
-    else if (c->TZ == 16 && c->TR == 16) jreduce_launch<NP, 16, 16>(c, a, tiles_ok);
-    else jreduce_launch<NP, 32, 4>(c, a, tiles_ok);
+    if (tz == 16 && tr == 8) f(std::integral_constant<int, 16>(), std::integral_constant<int, 8>());
+    else if (tz == 32 && tr == 8) f(std::integral_constant<int, 32>(), std::integral_constant<int, 8>());
+    else if (tz == 8 && tr == 8) f(std::integral_constant<int, 8>(), std::integral_constant<int, 8>());
+    else if (tz == 16 && tr == 16) f(std::integral_constant<int, 16>(), std::integral_constant<int, 16>());
+    else if (tz == 32 && tr == 4) f(std::integral_constant<int, 32>(), std::integral_constant<int, 4>());
+    else return false;
+    return true;
 }
 
-// defined (explicitly instantiated) in gpd_inst.cu, one object per <NP, FA>
 template <int NP, bool FA>
-bool gpd_run(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk);
+inline bool gpd_run(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int chunk)
+{
+    return tile_dispatch(c->TZ, c->TR, [&](auto tz, auto tr) {
+        gpd_shape<NP, decltype(tz)::value, decltype(tr)::value, FA>(c, a, grid, ntiles, chunk);
+    });
+}
 template <int NP>
-void jreduce_run(qpic_ctx *c, const PArgs &a, int tiles_ok);
+inline bool jreduce_run(qpic_ctx *c, const PArgs &a, int tiles_ok)
+{
+    return tile_dispatch(c->TZ, c->TR, [&](auto tz, auto tr) {
+        jreduce_shape<NP, decltype(tz)::value, decltype(tr)::value>(c, a, tiles_ok);
+    });
+}
+template <int NP>
+inline bool batch_particles_run(int tz, int tr, const BatchRun *runs, const int *tprefix, int nruns, int *head,
+                                const BatchCtl *ctl, int blocks, cudaStream_t st)
+{
+    return tile_dispatch(tz, tr, [&](auto z, auto r) {
+        batch_shape<NP, decltype(z)::value, decltype(r)::value>(runs, tprefix, nruns, head, ctl, blocks, st);
+    });
+}
 
 }  // namespace qpic

@@ -47,6 +47,47 @@ void launch_gpd(qpic_ctx *c)
     prof_end(c, KC_GPD);
 }
 
+// ------------------------------------------------------------ batched particle phase
+size_t batch_run_bytes() { return sizeof(BatchRun); }
+
+BatchCtlHost batch_ctl_default() { return BatchCtlHost{1LL << 24, -1}; }
+
+// one run's entry of a batch table (a host copy), with the particle buffers
+// the run will hold at that step (p_cur)
+void batch_fill_run(qpic_ctx *c, const Particles &p_cur, int *gdone, void *out)
+{
+    const PArgs a = pargs(c);
+    BatchRun R;
+    R.g = GpdArgs{p_cur, c->E, c->Bb, c->Jacc, c->Jfa, c->Jtile, c->tstamp, c->jdirty, c->d_epoch,
+                  c->offsets, c->d_count, a};
+    const int JW = c->TZ + 2 * c->halo + 3;
+    R.j = JredArgs{c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
+                   (long long)gpd_tile_words(c->g.nparts, c->TZ, c->TR), 1.0f / c->qscale,
+                   c->g.nzp >= 2 * JW ? 1 : 0, c->d_err};
+    R.gdone = gdone;
+    R.ntiles = c->ntz * c->ntr;
+    memcpy(out, &R, sizeof(R));
+}
+
+void launch_epoch(qpic_ctx *c)
+{
+    k_next_epoch<<<1, 1, 0, c->stream>>>(c->d_epoch);
+    c->n_kernels += 1;
+}
+
+bool launch_batch_particles(int nparts, int tz, int tr, const void *d_table, const int *d_prefix, int nruns,
+                            int *d_head, const void *d_ctl, int blocks, cudaStream_t st)
+{
+    const BatchRun *runs = static_cast<const BatchRun *>(d_table);
+    const BatchCtl *ctl = static_cast<const BatchCtl *>(d_ctl);
+    switch (nparts) {
+    case 1: return batch_particles_run<1>(tz, tr, runs, d_prefix, nruns, d_head, ctl, blocks, st);
+    case 3: return batch_particles_run<3>(tz, tr, runs, d_prefix, nruns, d_head, ctl, blocks, st);
+    case 5: return batch_particles_run<5>(tz, tr, runs, d_prefix, nruns, d_head, ctl, blocks, st);
+    default: return batch_particles_run<7>(tz, tr, runs, d_prefix, nruns, d_head, ctl, blocks, st);
+    }
+}
+
 // ------------------------------------------------------------ current reduction + decode
 // FP32 float-atomic variant: the current was summed in FP32 in Jfa; apply the
 // per-row finite-volume factor, zero the gap of an open box, clear Jfa.

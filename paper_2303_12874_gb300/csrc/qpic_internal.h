@@ -137,6 +137,7 @@ struct qpic_ctx {
 
     // tiles and sort
     int TZ = 16, TR = 8, ntz = 0, ntr = 0, halo = 1;
+    int ppt = 8;                 // consecutive particles per thread in the particle kernel
     long long nkeys = 0;
     int32_t *counts = nullptr, *offsets = nullptr, *scan_tmp = nullptr;
     int sort_period = 1;
@@ -220,6 +221,21 @@ void fp64_particle_sums(qpic_ctx *c, double *out3);
 void fp64_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale, unsigned long long *out);
 void scale_buffer(qpic_ctx *c, double *buf, size_t n, double s);
 void fp64_field_energy(qpic_ctx *c, double *out_modes);
+
+// ---- batched particle phase (k_particles.cu): one persistent launch over the
+// (run, tile) work list of the runs of a batch that share mode count and tile
+// shape.  Table entries are opaque here (batch_run_bytes each).
+struct BatchCtlHost {
+    long long spins;   // polls of one dependency wait before it gives up (QPIC_ETIMEOUT)
+    int hold;          // particle item that publishes nothing (-1: none; tests of the bounded wait)
+    int pad;
+};
+size_t batch_run_bytes();
+BatchCtlHost batch_ctl_default();
+void batch_fill_run(qpic_ctx *c, const Particles &p_cur, int *gdone, void *out);
+void launch_epoch(qpic_ctx *c);
+bool launch_batch_particles(int nparts, int tz, int tr, const void *d_table, const int *d_prefix, int nruns,
+                            int *d_head, const void *d_ctl, int blocks, cudaStream_t st);
 
 // QPIC_OK when the context's device is the current one, else QPIC_ESTATE (or
 // QPIC_ECUDA) with the context's error text set (api.cu)

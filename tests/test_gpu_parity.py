@@ -119,15 +119,19 @@ def o_cB(o):
     return C.dual_coefficients(o.dt, o.dz)[1]
 
 
-@pytest.mark.parametrize("solver,sort_period", [("dual", 2), ("yee", 2), ("dual", 1), ("dual", 3)])
-def test_full_step_config1(solver, sort_period):
+@pytest.mark.parametrize("solver,sort_period,ppt", [("dual", 2, 8), ("yee", 2, 8), ("dual", 1, 8),
+                                                    ("dual", 3, 8), ("dual", 2, 1), ("dual", 2, 3)])
+def test_full_step_config1(solver, sort_period, ppt):
     """sort_period 3 leaves particles up to 2 cells outside their tile: those
-    take the global-memory path of the same kernel"""
+    take the global-memory path of the same kernel.  ppt: particles per thread
+    (1: chunks of 255 particles, so a 16 x 8 tile of this plasma (1024
+    particles) is deposited in several chunks with a drain between them)"""
     w = synth.workload("cfg1_small")
     nz, nr = w["nz"], w["nr"]
     from oracle import coeffs as C
     dt = 0.9 * C.cfl_dt(w["dz"], w["dr"], nr, 2, solver)
-    sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, solver=solver, sort_period=sort_period)
+    sim, o = make_pair(nz, nr, w["dz"], w["dr"], dt, solver=solver, sort_period=sort_period,
+                       particles_per_thread=ppt)
     oracle_config1_state(o, dict(w, solver=solver), dt)
     # the oracle builds up currents and plasma motion; its state goes to the GPU
     o.step(3)
@@ -138,6 +142,21 @@ def test_full_step_config1(solver, sort_period):
     o.step(nst)
     for which in ("E", "B", "J"):
         compare_fields(sim, o, which, TOL)
+
+
+def test_particles_per_thread_leaves_results_unchanged():
+    """the particles each thread takes in a row only regroup the exact
+    integer sums of the deposit: fields bit-identical for 1, 3 and 8"""
+    w = synth.workload("cfg1_small")
+    out = []
+    for ppt in (1, 3, 8):
+        sim, _o = make_pair(w["nz"], w["nr"], w["dz"], w["dr"], 0.13, particles_per_thread=ppt)
+        _config1_state(sim, _o)
+        sim.step(5)
+        out.append([sim.fields(f) for f in ("E", "B", "J")])
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
 
 
 def test_bit_reproducible():
