@@ -77,6 +77,7 @@ def _declare(L):
     L.or_shift_window.argtypes = [_VP]
     L.or_compact.argtypes = [_VP]
     L.or_set_partitions.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+    L.or_set_absorber.argtypes = [_VP, ctypes.c_int, ctypes.c_double]
     L.or_has_openmp.restype = ctypes.c_int
 
 
@@ -94,7 +95,8 @@ class Oracle:
     m >= 1); 2 the directional work of Eq. 17 (W0 = W_z, W1 = W_perp)."""
 
     def __init__(self, nz, nr, n_modes, dz, dr, dt, cE, cB, ktaps=None,
-                 periodic=True, track_work=False, partitions=1, threads=0):
+                 periodic=True, track_work=False, partitions=1, threads=0, absorb_cells=0,
+                 absorb_sigma=0.0):
         cE = np.ascontiguousarray(cE, dtype=np.float64)
         cB = np.ascontiguousarray(cB, dtype=np.float64)
         kt = np.ascontiguousarray(ktaps if ktaps is not None else np.zeros(1), dtype=np.float64)
@@ -110,6 +112,15 @@ class Oracle:
             raise ValueError("oracle: bad configuration")
         if partitions > 1 or threads > 0:
             self.set_partitions(partitions, threads)
+        if absorb_cells > 0:
+            self.set_absorber(absorb_cells, absorb_sigma)
+
+    def set_absorber(self, ncells, sigma_max=0.0):
+        """Absorbing layer of `ncells` cells next to the wall (0: none): both
+        fields multiplied after each update by exp(-sigma(r) dt), sigma rising
+        as the square of the depth to sigma_max (<= 0: 3 ln(1e4) / (2 ncells
+        dr)); see or_set_absorber."""
+        self.L.or_set_absorber(self.h, int(ncells), float(sigma_max))
 
     def set_partitions(self, partitions, threads=0):
         """Deposit the particles in `partitions` fixed ranges (in parallel when

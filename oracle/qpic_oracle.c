@@ -68,6 +68,8 @@ typedef struct {
     int periodic;              /* 1: z periodic; 0: open (zero outside) */
     int track_work;
     double zmin;               /* lab z of logical cell 0 */
+    int nabs;                  /* absorbing layer: cells next to the wall (0: none) */
+    double sigabs;             /* its peak conductivity sigma_max */
     cplx *E, *B, *Bb, *J;      /* [comp][mode][j=0..nr][i=0..nz-1] */
     int nparts;                /* particle ranges deposited separately (1: serial) */
     cplx *Jp;                  /* nparts current buffers when nparts > 1 */
@@ -97,6 +99,43 @@ ostate *or_create(int nz, int nr, int nm, double dz, double dr, double dt,
     s->Bb = (cplx *)calloc(n, sizeof(cplx)); s->J = (cplx *)calloc(n, sizeof(cplx));
     s->nparts = 1;
     return s;
+}
+
+/* Absorbing radial layer (an extension: the paper's runs end at a conducting
+ * wall and it describes no absorbing boundary).  The ncells cells next to the
+ * wall, r0 = R - ncells dr < r <= R, get the conductivity
+ *     sigma(r) = sigma_max ((r - r0) / (ncells dr))^2
+ * on both E and B (equal electric and magnetic conductivity: a layer matched
+ * to the vacuum at normal incidence).  In time the loss term -sigma F of
+ * dF/dt = rhs - sigma F is centred (the lossy leapfrog update):
+ *     F^{new} = alpha F^{old} + beta dt rhs,
+ *     alpha = (1 - sigma dt/2) / (1 + sigma dt/2),  beta = 1 / (1 + sigma dt/2),
+ * with sigma at the component's own radius (alpha = beta = 1 outside).
+ * sigma_max <= 0 takes 3 ln(1e4) / (2 ncells dr), the value at which a wave
+ * crossing the layer twice in the continuum is attenuated by 1e4. */
+void or_set_absorber(ostate *s, int ncells, double sigma_max)
+{
+    if (ncells < 0) ncells = 0;
+    if (ncells > s->nr) ncells = s->nr;
+    s->nabs = ncells;
+    s->sigabs = ncells == 0 ? 0.0
+              : (sigma_max > 0.0 ? sigma_max : 3.0 * log(1e4) / (2.0 * ncells * s->dr));
+}
+
+/* sigma(r) dt / 2 at radius r (0 outside the layer) */
+static double half_loss(const ostate *s, double r)
+{
+    if (s->nabs == 0) return 0.0;
+    const double width = s->nabs * s->dr, r0 = s->nr * s->dr - width;
+    if (r <= r0) return 0.0;
+    const double x = (r - r0) / width;
+    return 0.5 * s->sigabs * x * x * s->dt;
+}
+/* the lossy update F <- alpha F + beta dt rhs at radius r */
+static cplx lossy(const ostate *s, double r, cplx f, cplx dt_rhs)
+{
+    const double h = half_loss(s, r);
+    return ((1.0 - h) * f + dt_rhs) / (1.0 + h);
 }
 
 /* number of particle ranges deposited separately (1: serial, the default) and,
@@ -253,16 +292,16 @@ void or_faraday(ostate *s)
                 } else {
                     d = -I * (double)m / rj * s->E[fidx(s, CZ, m, j, i)] + dzE(s, s->E, CP, m, j, i);
                 }
-                Bn[fidx(s, CR, m, j, i)] += dt * d;
+                Bn[fidx(s, CR, m, j, i)] = lossy(s, rj, Bn[fidx(s, CR, m, j, i)], dt * d);
                 if (j < nr) {
                     /* B_phi at (i+1/2, j+1/2) */
                     d = -dzE(s, s->E, CR, m, j, i)
                         + (s->E[fidx(s, CZ, m, j + 1, i)] - s->E[fidx(s, CZ, m, j, i)]) / dr;
-                    Bn[fidx(s, CP, m, j, i)] += dt * d;
+                    Bn[fidx(s, CP, m, j, i)] = lossy(s, rh, Bn[fidx(s, CP, m, j, i)], dt * d);
                     /* B_z at (i, j+1/2) */
                     d = -((j + 1) * dr * s->E[fidx(s, CP, m, j + 1, i)] - rj * s->E[fidx(s, CP, m, j, i)]) / (rh * dr)
                         + I * (double)m / rh * s->E[fidx(s, CR, m, j, i)];
-                    Bn[fidx(s, CZ, m, j, i)] += dt * d;
+                    Bn[fidx(s, CZ, m, j, i)] = lossy(s, rh, Bn[fidx(s, CZ, m, j, i)], dt * d);
                 }
             }
         }
@@ -317,7 +356,7 @@ void or_ampere(ostate *s)
                     /* E_r at (i, j+1/2) */
                     cplx d = I * (double)m / rh * s->B[fidx(s, CZ, m, j, i)]
                              - dzB(s, s->B, CP, m, j, i) - s->J[fidx(s, CR, m, j, i)];
-                    s->E[fidx(s, CR, m, j, i)] += dt * d;
+                    s->E[fidx(s, CR, m, j, i)] = lossy(s, rh, s->E[fidx(s, CR, m, j, i)], dt * d);
                 }
                 /* E_phi at (i, j) */
                 if (j == nr || (j == 0 && m != 1)) {
@@ -325,23 +364,23 @@ void or_ampere(ostate *s)
                 } else if (j == 0) {
                     cplx d = dzB(s, s->B, CR, 1, 0, i) - 2.0 * s->B[fidx(s, CZ, 1, 0, i)] / dr
                              - s->J[fidx(s, CP, 1, 0, i)];
-                    s->E[fidx(s, CP, 1, 0, i)] += dt * d;
+                    s->E[fidx(s, CP, 1, 0, i)] = lossy(s, rj, s->E[fidx(s, CP, 1, 0, i)], dt * d);
                 } else {
                     cplx d = dzB(s, s->B, CR, m, j, i)
                              - (s->B[fidx(s, CZ, m, j, i)] - s->B[fidx(s, CZ, m, j - 1, i)]) / dr
                              - s->J[fidx(s, CP, m, j, i)];
-                    s->E[fidx(s, CP, m, j, i)] += dt * d;
+                    s->E[fidx(s, CP, m, j, i)] = lossy(s, rj, s->E[fidx(s, CP, m, j, i)], dt * d);
                 }
                 /* E_z at (i+1/2, j) */
                 if (j == nr || (j == 0 && m != 0)) {
                     s->E[fidx(s, CZ, m, j, i)] = 0.0;
                 } else if (j == 0) {
                     cplx d = 4.0 * s->B[fidx(s, CP, 0, 0, i)] / dr - s->J[fidx(s, CZ, 0, 0, i)];
-                    s->E[fidx(s, CZ, 0, 0, i)] += dt * d;
+                    s->E[fidx(s, CZ, 0, 0, i)] = lossy(s, rj, s->E[fidx(s, CZ, 0, 0, i)], dt * d);
                 } else {
                     cplx d = ((j + 0.5) * dr * s->B[fidx(s, CP, m, j, i)] - rl * s->B[fidx(s, CP, m, j - 1, i)]) / (rj * dr)
                              - I * (double)m / rj * s->B[fidx(s, CR, m, j, i)] - s->J[fidx(s, CZ, m, j, i)];
-                    s->E[fidx(s, CZ, m, j, i)] += dt * d;
+                    s->E[fidx(s, CZ, m, j, i)] = lossy(s, rj, s->E[fidx(s, CZ, m, j, i)], dt * d);
                 }
             }
         }
