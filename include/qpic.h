@@ -92,6 +92,14 @@ typedef struct {
                                  tile's particles are sorted by cell, so about ppc / this many
                                  threads share a cell (the "threads per cell" knob); smaller
                                  values mean more threads per cell and more chunk drains */
+    int32_t absorb_cells;     /* absorbing radial layer (an extension; the paper's runs end at a
+                                 conducting wall): the cells next to the wall, 0..nr (0: none).
+                                 On r0 = R - absorb_cells dr < r <= R, E and B get the
+                                 conductivity sigma(r) = absorb_sigma ((r - r0)/(R - r0))^2 with
+                                 the centred lossy update F = alpha F + beta dt rhs,
+                                 alpha = (1 - sigma dt/2)/(1 + sigma dt/2), beta = 1/(1 + sigma dt/2) */
+    double absorb_sigma;      /* peak conductivity (0: 3 ln(1e4) / (2 absorb_cells dr), a round-trip
+                                 attenuation of 1e4 in the continuum) */
     int32_t track_work;       /* per-particle work in W0, W1: 0 off; 1 modal (Eq. 16:
                                  W0 from m = 0, W1 from m >= 1); 2 directional (Eq. 17:
                                  W0 = W_z, W1 = W_perp, all modes) */

@@ -41,7 +41,8 @@ class Config(ctypes.Structure):
         ("filter_tol", ctypes.c_double), ("periodic_z", ctypes.c_int32),
         ("moving_window", ctypes.c_int32), ("window_v", ctypes.c_double),
         ("tile_z", ctypes.c_int32), ("tile_r", ctypes.c_int32), ("sort_period", ctypes.c_int32),
-        ("particles_per_thread", ctypes.c_int32), ("track_work", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_particles", ctypes.c_int64),
+        ("particles_per_thread", ctypes.c_int32), ("absorb_cells", ctypes.c_int32),
+        ("absorb_sigma", ctypes.c_double), ("track_work", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_particles", ctypes.c_int64),
         ("cuda_stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
     ]
@@ -309,7 +310,7 @@ class Sim:
     def __init__(self, nz, nr, dz, dr, n_modes=2, dt=0.0, cfl_frac=0.9, solver="dual", n_coef=16,
                  fit_band=0.8, jz_filter=True, filter_tol=1e-16, periodic=True,
                  moving_window=False, window_v=1.0, tile_z=16, tile_r=8, sort_period=2,
-                 particles_per_thread=8,
+                 particles_per_thread=8, absorb_cells=0, absorb_sigma=0.0,
                  track_work=False, seed=1, max_particles=0, stream=None, torch_alloc=False,
                  precision=QPIC_FP32_FIXED):
         self.L = load()
@@ -324,6 +325,7 @@ class Sim:
         cfg.periodic_z, cfg.moving_window, cfg.window_v = int(periodic), int(moving_window), window_v
         cfg.tile_z, cfg.tile_r, cfg.sort_period = tile_z, tile_r, sort_period
         cfg.particles_per_thread = particles_per_thread
+        cfg.absorb_cells, cfg.absorb_sigma = absorb_cells, absorb_sigma
         # track_work: False/0 off, True/1 modal work (Eq. 16), 2 directional work (Eq. 17)
         cfg.track_work, cfg.seed, cfg.max_particles = int(track_work), seed, max_particles
         if stream is not None:

@@ -319,6 +319,8 @@ qpic_status qpic_default_config(qpic_config *cfg)
     cfg->tile_r = 8;
     cfg->sort_period = 2;
     cfg->particles_per_thread = 8;
+    cfg->absorb_cells = 0;
+    cfg->absorb_sigma = 0.0;
     cfg->seed = 1;
     return QPIC_OK;
 }
@@ -396,6 +398,12 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 2;
     c->ppt = cfg->particles_per_thread > 0 ? cfg->particles_per_thread : 8;
     if (c->ppt > 8) return bad(QPIC_EINVAL, "particles_per_thread: 1..8");
+    if (cfg->absorb_cells < 0 || cfg->absorb_cells > cfg->nr || !(cfg->absorb_sigma >= 0.0) ||
+        !std::isfinite(cfg->absorb_sigma))
+        return bad(QPIC_EINVAL, "absorb_cells: 0..nr; absorb_sigma: finite, >= 0");
+    c->nabs = cfg->absorb_cells;
+    c->sigabs = c->nabs == 0 ? 0.0
+              : (cfg->absorb_sigma > 0 ? cfg->absorb_sigma : 3.0 * std::log(1e4) / (2.0 * c->nabs * cfg->dr));
     FieldGeom &g = c->g;
     g.nz = cfg->nz; g.nr = cfg->nr; g.nm = cfg->n_modes; g.nparts = 2 * cfg->n_modes - 1;
     g.periodic = cfg->periodic_z ? 1 : 0;
@@ -475,6 +483,30 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
         rf[3 * (g.nr + 1) + j] = (float)(dr / (V * dt));
     }
     cudaMemcpy(c->rowf, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    // absorbing radial layer: sigma(r) = sigma_max ((r - r0) / (n_abs dr))^2 on
+    // r0 < r <= R, and the lossy leapfrog update F = alpha F + beta dt rhs with
+    // alpha = (1 - sigma dt/2) / (1 + sigma dt/2), beta = 1 / (1 + sigma dt/2),
+    // per row at r_j and r_{j+1/2}
+    if (c->nabs > 0) {
+        const size_t nl = (size_t)4 * (g.nr + 1);
+        if (!alloc_arr(c, &c->lossf, nl) || !alloc_arr(c, &c->loss64, nl))
+            return bad(QPIC_ENOMEM, "absorbing layer: device allocation failed");
+        std::vector<double> l64(nl);
+        std::vector<float> l32(nl);
+        const double width = c->nabs * dr, r0 = R - width;
+        for (int j = 0; j <= g.nr; j++) {
+            for (int k = 0; k < 2; k++) {
+                const double r = (j + 0.5 * k) * dr;
+                const double x = r > r0 ? (r - r0) / width : 0.0;
+                const double h = 0.5 * c->sigabs * x * x * dt;
+                l64[(size_t)(2 * k) * (g.nr + 1) + j] = (1.0 - h) / (1.0 + h);
+                l64[(size_t)(2 * k + 1) * (g.nr + 1) + j] = 1.0 / (1.0 + h);
+            }
+        }
+        for (size_t k = 0; k < nl; k++) l32[k] = (float)l64[k];
+        cudaMemcpy(c->loss64, l64.data(), nl * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->lossf, l32.data(), nl * sizeof(float), cudaMemcpyHostToDevice);
+    }
     set_solver_constants(c);
     set_qscale(c, 1.0);
     qpic_status st = cuda_check(c, "init");

@@ -42,6 +42,12 @@ struct GridArgs {
     double dz64, dr64, dt64, idz64, idr64;
     const float *coef;     // [cE | cB | taps] FP32
     const double *coef64;  // the same in FP64 (plain FP64 path)
+    // absorbing layer: rows j >= loss_row0 take F = alpha F + beta dt rhs with
+    // [alpha(r_j), beta(r_j), alpha(r_{j+1/2}), beta(r_{j+1/2})] at
+    // loss[k (nr + 1) + j] (FP32) and loss64 (FP64); loss_row0 > nr: no layer
+    int loss_row0;
+    const float *loss;
+    const double *loss64;
 };
 
 static GridArgs grid_args(const qpic_ctx *c)
@@ -55,7 +61,18 @@ static GridArgs grid_args(const qpic_ctx *c)
     a.idz = (float)a.idz64; a.idr = (float)a.idr64;
     a.coef = c->coef;
     a.coef64 = c->coef64;
+    a.loss_row0 = c->nabs > 0 ? c->g.nr - c->nabs : c->g.nr + 1;
+    a.loss = c->lossf;
+    a.loss64 = c->loss64;
     return a;
+}
+
+// factor k (0, 1: alpha, beta at r_j; 2, 3: at r_{j+1/2}) of row j of the layer
+template <typename T>
+__device__ __forceinline__ T loss_at(const GridArgs &a, int k, int j)
+{
+    if constexpr (sizeof(T) == 8) return a.loss64[k * (a.nr + 1) + j];
+    else return a.loss[k * (a.nr + 1) + j];
 }
 
 __device__ __forceinline__ int wrapz(int i, int nzp)
@@ -191,6 +208,10 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
     // the row's reciprocals, once per thread (divisions are long sequences)
     const T irh = (T)1 / rh, irj = j > 0 ? (T)1 / rj : (T)0, irhdr = irh * idr;
     const int s = threadIdx.x + a.L;   // smem index of column i
+    // absorbing layer (block-uniform): lossy update factors at r_j and r_{j+1/2}
+    const bool lossy = j >= a.loss_row0;
+    T aI = 1, bI = 1, aH = 1, bH = 1;
+    if (lossy) { aI = loss_at<T>(a, 0, j); bI = loss_at<T>(a, 1, j); aH = loss_at<T>(a, 2, j); bH = loss_at<T>(a, 3, j); }
 #pragma unroll
     for (int p = 0; p < P; p++) {
         const int m = part_mode(p);
@@ -214,11 +235,12 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
                 // the axis term in FP64 on the FP32 path (dE_phi again from the staged row)
                 const double d64 = (double)(isim ? -ez1[pr] : ez1[pim]) * a.idr64 +
                                    zdiff64(sE2 + p * W + s, a.coef64, a.L).x * a.idz64;
-                const double b64 = (double)br[p] + a.dt64 * d64;
+                const double b64 = lossy ? a.loss64[j] * (double)br[p] + a.loss64[(a.nr + 1) + j] * (a.dt64 * d64)
+                                         : (double)br[p] + a.dt64 * d64;
                 B[q] = gap ? (T)0 : (T)b64;
                 Bb[q] = gap ? (T)0 : (T)(0.5 * ((double)br[p] + b64));
             } else {
-                const T bn = gap ? (T)0 : br[p] + dt * d;
+                const T bn = gap ? (T)0 : (lossy ? aI * br[p] + bI * (dt * d) : br[p] + dt * d);
                 B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (br[p] + bn);
             }
         }
@@ -226,13 +248,13 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_far
             // B_phi at (i+1/2, j+1/2)
             d = -dEr + (ez1[p] - ez[p]) * idr;
             size_t q = (size_t)(1 * P + p) * a.plane + base;
-            T bn = gap ? (T)0 : bp[p] + dt * d;
+            T bn = gap ? (T)0 : (lossy ? aH * bp[p] + bH * (dt * d) : bp[p] + dt * d);
             B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bp[p] + bn);
             // B_z at (i, j+1/2); E_phi(j) and E_r(j) from the staged row
             const T imr = m > 0 ? (isim ? sE2[pr * W + s].y : -sE2[pim * W + s].y) * ((T)m * irh) : (T)0;
             d = -(rj1 * ep1[p] - rj * sE2[p * W + s].x) * irhdr + imr;
             q = (size_t)(2 * P + p) * a.plane + base;
-            bn = gap ? (T)0 : bz[p] + dt * d;
+            bn = gap ? (T)0 : (lossy ? aH * bz[p] + bH * (dt * d) : bz[p] + dt * d);
             B[q] = bn; Bb[q] = gap ? (T)0 : (T)0.5 * (bz[p] + bn);
         } else {
             // half-r row beyond the wall: not advanced; its average is the value itself
@@ -437,6 +459,11 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
     const T rj = j * dr, rh = (j + (T)0.5) * dr, rl = (j - (T)0.5) * dr;
     const T irh = (T)1 / rh, irj = j > 0 ? (T)1 / rj : (T)0, irjdr = irj * idr;
     const int s = threadIdx.x + a.L;
+    const bool lossy = j >= a.loss_row0;           // absorbing layer (block-uniform)
+    T aI = 1, bI = 1, aH = 1, bH = 1;
+    if (lossy) { aI = loss_at<T>(a, 0, j); bI = loss_at<T>(a, 1, j); aH = loss_at<T>(a, 2, j); bH = loss_at<T>(a, 3, j); }
+    // the lossy update of an FP64 axis term on the FP32 path
+    const double aI64 = lossy ? a.loss64[j] : 1.0, bI64 = lossy ? a.loss64[(a.nr + 1) + j] : 1.0;
 #pragma unroll
     for (int p = 0; p < P; p++) {
         const int m = part_mode(p);
@@ -449,17 +476,23 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
         if (j < a.nr) {
             const T imr = m > 0 ? (isim ? bz[pr] : -bz[pim]) * ((T)m * irh) : (T)0;
             const T d = imr - dBphi - jr[p];
-            E[(size_t)(0 * P + p) * a.plane + base] = gap ? (T)0 : er[p] + dt * d;
+            E[(size_t)(0 * P + p) * a.plane + base] = gap ? (T)0 : (lossy ? aH * er[p] + bH * (dt * d) : er[p] + dt * d);
         }
         // E_phi at (i, j)
         {
             T v;
             if (j == a.nr || (j == 0 && m != 1)) v = 0;
-            else if (j == 0 && sizeof(T) == 4)          // the axis term in FP64
-                v = (T)((double)ep[p] + a.dt64 * (zdiff64(sB2 + p * W + s - 1, a.coef64 + MAX_L, a.L).y * a.idz64 -
-                                                  2.0 * (double)bz[p] * a.idr64 - (double)jp[p]));
-            else if (j == 0) v = ep[p] + dt * (dBr - (T)2 * bz[p] * idr - jp[p]);
-            else v = ep[p] + dt * (dBr - (bz[p] - bzm[p]) * idr - jp[p]);
+            else if (j == 0 && sizeof(T) == 4) {        // the axis term in FP64
+                const double dtd = a.dt64 * (zdiff64(sB2 + p * W + s - 1, a.coef64 + MAX_L, a.L).y * a.idz64 -
+                                             2.0 * (double)bz[p] * a.idr64 - (double)jp[p]);
+                v = (T)(lossy ? aI64 * (double)ep[p] + bI64 * dtd : (double)ep[p] + dtd);
+            } else if (j == 0) {
+                const T d = dBr - (T)2 * bz[p] * idr - jp[p];
+                v = lossy ? aI * ep[p] + bI * (dt * d) : ep[p] + dt * d;
+            } else {
+                const T d = dBr - (bz[p] - bzm[p]) * idr - jp[p];
+                v = lossy ? aI * ep[p] + bI * (dt * d) : ep[p] + dt * d;
+            }
             E[(size_t)(1 * P + p) * a.plane + base] = gap ? (T)0 : v;
         }
         // E_z at (i+1/2, j); B_phi(j) and B_r(j) from the staged row
@@ -469,12 +502,17 @@ __global__ void __launch_bounds__(FTILE, sizeof(T) == 4 && P <= 3 ? 6 : 1) k_amp
             if (j == a.nr || (j == 0 && m != 0)) {
                 v = 0;
             } else if (j == 0) {                       // the axis term in FP64 on the FP32 path
-                v = sizeof(T) == 4 ? (T)((double)ez[p] + a.dt64 * (4.0 * (double)bp0 * a.idr64 - (double)jz[p]))
-                                   : ez[p] + dt * ((T)4 * bp0 * idr - jz[p]);
+                if (sizeof(T) == 4) {
+                    const double dtd = a.dt64 * (4.0 * (double)bp0 * a.idr64 - (double)jz[p]);
+                    v = (T)(lossy ? aI64 * (double)ez[p] + bI64 * dtd : (double)ez[p] + dtd);
+                } else {
+                    const T d = (T)4 * bp0 * idr - jz[p];
+                    v = lossy ? aI * ez[p] + bI * (dt * d) : ez[p] + dt * d;
+                }
             } else {
                 const T imr = m > 0 ? (isim ? sB2[pr * W + s].y : -sB2[pim * W + s].y) * ((T)m * irj) : (T)0;
                 const T d = (rh * bp0 - rl * bpm[p]) * irjdr - imr - jz[p];
-                v = ez[p] + dt * d;
+                v = lossy ? aI * ez[p] + bI * (dt * d) : ez[p] + dt * d;
             }
             E[(size_t)(2 * P + p) * a.plane + base] = gap ? (T)0 : v;
         }

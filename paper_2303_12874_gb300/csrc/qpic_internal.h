@@ -138,6 +138,10 @@ struct qpic_ctx {
     // tiles and sort
     int TZ = 16, TR = 8, ntz = 0, ntr = 0, halo = 1;
     int ppt = 8;                 // consecutive particles per thread in the particle kernel
+    int nabs = 0;                // absorbing radial layer: cells next to the wall (0: none)
+    double sigabs = 0;           // its peak conductivity
+    float *lossf = nullptr;      // lossy update factors per row (4 (nr + 1)), FP32 and FP64
+    double *loss64 = nullptr;
     long long nkeys = 0;
     int32_t *counts = nullptr, *offsets = nullptr, *scan_tmp = nullptr;
     int sort_period = 1;
