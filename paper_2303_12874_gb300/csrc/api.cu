@@ -585,13 +585,13 @@ qpic_status qpic_load_plasma(qpic_ctx *c, double n0, double z_start, double ramp
     if (!c) return QPIC_EINVAL;
     if (ppc_z < 1 || ppc_r < 1 || ppc_phi < 1 || !(n0 >= 0)) return fail(c, QPIC_EINVAL, "plasma parameters");
     QPIC_REQUIRE_DEVICE(c);
-    c->have_plasma = true;
-    c->n0 = n0; c->z_start = z_start; c->ramp_len = ramp_len;
-    c->ppc_z = ppc_z; c->ppc_r = ppc_r; c->ppc_phi = ppc_phi; c->jitter = phi_jitter ? 1 : 0;
     long long n = (long long)c->g.nz * c->g.nr * ppc_z * ppc_r * ppc_phi;
     long long per_col = (long long)c->g.nr * ppc_z * ppc_r * ppc_phi;
     qpic_status s = ensure_capacity(c, n + (c->cfg.moving_window ? 64 * per_col : 0));
-    if (s != QPIC_OK) return s;
+    if (s != QPIC_OK) return s;           // refused: the context keeps its previous state
+    c->have_plasma = true;
+    c->n0 = n0; c->z_start = z_start; c->ramp_len = ramp_len;
+    c->ppc_z = ppc_z; c->ppc_r = ppc_r; c->ppc_phi = ppc_phi; c->jitter = phi_jitter ? 1 : 0;
     // largest weight: density n0 at the outermost sub-particle radius
     double rmax = (c->g.nr - 1 + (ppc_r - 0.5) / ppc_r) * c->dr;
     set_qscale(c, n0 * 2.0 * kPi * rmax * (c->dr / ppc_r) * (c->dz / ppc_z) / ppc_phi);
