@@ -84,7 +84,11 @@ def reduced_bunch(seed, n, v_g=0.993583, wp=1.0 / (1.002565 * 12.14), R_over_lp=
     0.836/w_p] shifted by +R (the model's bubble is centred on zeta = 0), x
     uniform in [-r_b, r_b] with r_b = sqrt(R^2 - zeta^2), gamma uniform in
     [gamma_g, 2 gamma_g] with gamma_g = 1/sqrt(1 - v_g^2), and the velocity at
-    a random angle to the x axis with v_z >= v_g.  Returns (x, zeta, u_x, u_z)."""
+    a random angle to the x axis with v_z >= v_g.  Returns (x, zeta, u_x, u_z):
+    the state at injection.  The injection times (the appendix spreads them
+    over 200/w_p) are not drawn here; the caller passes each electron's start
+    step to the integrator (`start`), as the benchmark's staggering leg and
+    the reduced-model tests do."""
     rng = np.random.default_rng([seed, 7])
     R = R_over_lp / wp
     zeta = rng.uniform(-2 * R + 0.286 / wp, -2 * R + 0.836 / wp, n) + R
