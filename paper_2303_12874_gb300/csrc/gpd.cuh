@@ -549,7 +549,7 @@ __device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, 
 }
 
 // Same-cell deposits summed in registers.  A thread takes consecutive particles
-// of its tile (see tile_slot), so successive moves mostly stay in one cell and
+// of its tile (see chunk_slot), so successive moves mostly stay in one cell and
 // go to the same 8*NP accumulator words (J_z at 2 faces, J_r at 2 faces, J_phi
 // at 4 nodes, each per part).  Each contribution is rounded to the int64 fixed
 // point exactly as fx() does, kept as hi 2^21 + lo, and the two halves are
@@ -670,6 +670,18 @@ __host__ __device__ __forceinline__ Chunk tile_chunk(int n, int c, int chunk)
     k.nt = k.rc / k.kc;
     k.rem = k.rc - k.nt * k.kc;
     return k;
+}
+
+// Storage slot, inside its chunk, of thread t's k-th particle.  The sort
+// stores each chunk column by column: the k-th particles of all threads that
+// have one lie in consecutive slots (k (nt + 1) + t while every thread up to
+// nt has a k-th particle, rem (nt + 1) + (k - rem) nt + t after), so at every
+// iteration the block's threads read and write consecutive records
+// (coalesced), while each thread still walks consecutive particles of the
+// cell-sorted order (u = t kc + k).
+__host__ __device__ __forceinline__ int chunk_slot(const Chunk &C, int t, int k)
+{
+    return k < C.rem ? k * (C.nt + 1) + t : C.rem * (C.nt + 1) + (k - C.rem) * C.nt + t;
 }
 
 // Ampere-style asynchronous 4-byte global -> shared copies (one per thread and
@@ -849,8 +861,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     const int nch = tile_nchunks(n, chunk);
     Chunk C = tile_chunk(n, 0, chunk);
     int cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
-    int q = C.q0 + tid * C.kc;
-    prefetch(0, cnt > 0 ? q : -1);
+    prefetch(0, cnt > 0 ? C.q0 + chunk_slot(C, tid, 0) : -1);
     // ---- stage E and Bbar of the tile and its halo; clear the accumulators
     const int col0 = tz0 - G::H - 1;
     const int row0 = tr0 - G::H - 1;
@@ -884,15 +895,14 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
         if (ch > 0) {                                              // chunks beyond the first
             C = tile_chunk(n, ch, chunk);
             cnt = tid < C.nt ? C.kc : (tid == C.nt ? C.rem : 0);
-            q = C.q0 + tid * C.kc;
-            prefetch(0, cnt > 0 ? q : -1);
+            prefetch(0, cnt > 0 ? C.q0 + chunk_slot(C, tid, 0) : -1);
         }
         int buf = 0;
         for (int k = 0; k < C.kc; k++) {                           // block-uniform trip count
-            prefetch(buf ^ 1, k + 1 < cnt ? q + k + 1 : -1);
+            prefetch(buf ^ 1, k + 1 < cnt ? C.q0 + chunk_slot(C, tid, k + 1) : -1);
             cp_async_wait_prev();                                  // this particle's words have landed
             if (k < cnt) {
-                const int qi = q + k;
+                const int qi = C.q0 + chunk_slot(C, tid, k);
                 const float *pb = pbuf + buf * G::PB;
                 const float4 *pr = reinterpret_cast<const float4 *>(pb + GPD_T);
                 const int cell = __float_as_int(pb[tid]);

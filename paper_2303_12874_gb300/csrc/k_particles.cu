@@ -263,7 +263,15 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
         if ((int)lane == leader) top = atomicSub(&counts[k], n);      // slots [top-n, top)
         top = __shfl_sync(grp, top, leader);
         const int rank = __popc(grp & ((1u << lane) - 1u));
-        const long long d = (long long)offsets[k] + top - n + rank;
+        // position in the cell-sorted order of the tile, then its storage slot
+        // (chunks stored column by column, chunk_slot)
+        const int tile = k >> (a.lTZ + a.lTR);
+        const long long t0 = offsets[(long long)tile << (a.lTZ + a.lTR)];
+        const int ntile = (int)(offsets[(long long)(tile + 1) << (a.lTZ + a.lTR)] - t0);
+        const int u = (int)((long long)offsets[k] + top - n + rank - t0);
+        const Chunk C = tile_chunk(ntile, u / a.chunk, a.chunk);
+        const int w = u - C.q0, th = w / C.kc;
+        const long long d = t0 + C.q0 + chunk_slot(C, th, w - th * C.kc);
         dst.cell[d] = c;
         float4 ra, rb;
         ld_rec(src.rec + 2 * i, ra, rb);
