@@ -257,6 +257,12 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
         const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
         if (c < 0) continue;
         const int k = sort_key(c, a);
+        // the key's offset and its tile's extent, loaded before the atomic so
+        // that their latencies overlap
+        const int tile = k >> (a.lTZ + a.lTR);
+        const int ok = offsets[k];
+        const int t0 = offsets[(long long)tile << (a.lTZ + a.lTR)];
+        const int t1 = offsets[(long long)(tile + 1) << (a.lTZ + a.lTR)];
         const unsigned grp = __match_any_sync(act, k);
         const int leader = __ffs(grp) - 1, n = __popc(grp);
         int top = 0;
@@ -265,13 +271,11 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
         const int rank = __popc(grp & ((1u << lane) - 1u));
         // position in the cell-sorted order of the tile, then its storage slot
         // (chunks stored column by column, chunk_slot)
-        const int tile = k >> (a.lTZ + a.lTR);
-        const long long t0 = offsets[(long long)tile << (a.lTZ + a.lTR)];
-        const int ntile = (int)(offsets[(long long)(tile + 1) << (a.lTZ + a.lTR)] - t0);
-        const int u = (int)((long long)offsets[k] + top - n + rank - t0);
+        const int ntile = t1 - t0;
+        const int u = ok + top - n + rank - t0;
         const Chunk C = tile_chunk(ntile, u / a.chunk, a.chunk);
         const int w = u - C.q0, th = w / C.kc;
-        const long long d = t0 + C.q0 + chunk_slot(C, th, w - th * C.kc);
+        const long long d = (long long)t0 + C.q0 + chunk_slot(C, th, w - th * C.kc);
         dst.cell[d] = c;
         float4 ra, rb;
         ld_rec(src.rec + 2 * i, ra, rb);
