@@ -65,8 +65,9 @@ enum { QPIC_STAGE_FARADAY = 1, QPIC_STAGE_PARTICLES = 2, QPIC_STAGE_AMPERE = 4,
        QPIC_STAGE_WINDOW = 8, QPIC_STAGE_SORT = 16 };
 
 typedef struct {
-    int32_t nz, nr;        /* logical grid: nz cells along z (< ~32000), nr cells in r (wall
-                              at nr dr) */
+    int32_t nz, nr;        /* logical grid: nz cells along z, nr cells in r (wall at nr dr);
+                              nz plus the open box's gap below 32768, nr below 65535
+                              (QPIC_EINVAL otherwise) */
     int32_t n_modes;       /* M + 1 azimuthal modes (1..4) */
     double dz, dr;
     double dt;             /* <= 0: dt = cfl_frac x the solver's stability limit */

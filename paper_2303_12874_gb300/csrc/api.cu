@@ -410,8 +410,9 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     int reach = std::max({2 * c->L + 2, (int)c->taps.size() + 2, 2 * (c->TZ + 2 * c->halo + 3)});
     g.gap = g.periodic ? 0 : ((reach + c->TZ - 1) / c->TZ) * c->TZ;
     g.nzp = g.nz + g.gap;
-    if (g.nzp >= 32768 || g.nr >= 65536)
-        return bad(QPIC_EINVAL, "grid too large for the packed cell index (nz + gap < 32768, nr < 65536)");
+    if (g.nzp >= 32768 || g.nr >= 65535)
+        return bad(QPIC_EINVAL, "grid too large: nz + gap < 32768 (packed cell index), nr < 65535 "
+                                "(packed cell index; one block row per grid row, nr + 1 <= 65535)");
     g.zoff = 0;
     g.plane = (size_t)(g.nr + 1) * g.nzp;
     g.dz = (float)c->dz; g.dr = (float)c->dr; g.dt = (float)c->dt;

@@ -152,3 +152,28 @@ def test_batch_refuses_what_it_cannot_run():
     s = q.Sim(r["nz"], r["nr"], 0.2, 0.5, dt=0.12, precision=q.QPIC_FP64)
     with pytest.raises(q.QpicError, match="EINVAL"):
         q.Batch([s])
+
+
+def test_more_runs_than_one_launch_holds():
+    """70 runs of one shape need two persistent launches per step (at most 64
+    runs each); one run holds no particles at all"""
+    specs = [dict(nz=32, nr=8, n0=0.01 * (1 + k % 5), a0=1.0, ppc=(1, 1, 2), tile=(16, 8)) for k in range(70)]
+
+    def make(k):
+        if k == 17:
+            return q.Sim(32, 8, 0.2, 0.5, dt=0.12)
+        return _make(specs[k])
+
+    solo = [make(k) for k in range(70)]
+    for s in solo:
+        s.step(8)
+    batched = [make(k) for k in range(70)]
+    b = q.Batch(batched)
+    assert 8 % b.cycle == 0
+    b.step(8)
+    assert batched[17].num_particles() == 0
+    for s, t in zip(solo, batched):
+        assert t.diag()["steps"] == 8
+        for which in ("E", "J"):
+            assert _rel(t.fields(which), s.fields(which)) <= 1e-4, which
+    b.close()
