@@ -16,6 +16,7 @@ import json
 import os
 
 from . import _build
+from . import QpicError
 
 TILES = [(16, 8), (32, 8), (8, 8), (16, 16), (32, 4)]
 SORT_PERIODS = [1, 2]
@@ -103,7 +104,12 @@ def tune(make_sim, init_state, nz, nr, n_modes, ppc, periodic=True, steps=8, war
             if batch and not batch_ok(tz, tr, sp):
                 continue
             for ppt in ppts:
-                ms = _time_one(make_sim, init_state, tz, tr, sp, ppt, steps, warmup, batch_copies)
+                try:
+                    ms = _time_one(make_sim, init_state, tz, tr, sp, ppt, steps, warmup, batch_copies)
+                except QpicError as e:
+                    if "EINVAL" not in str(e):
+                        raise
+                    continue                    # a shape this run cannot take (e.g. too much shared memory)
                 if best is None or ms < best[4]:
                     best = (tz, tr, sp, ppt, ms)
     if best is None:

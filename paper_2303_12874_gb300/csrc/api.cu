@@ -404,6 +404,17 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->nabs = cfg->absorb_cells;
     c->sigabs = c->nabs == 0 ? 0.0
               : (cfg->absorb_sigma > 0 ? cfg->absorb_sigma : 3.0 * std::log(1e4) / (2.0 * c->nabs * cfg->dr));
+    if (cfg->precision != QPIC_FP64) {
+        // the tile's staged fields and accumulators must fit one block's shared memory
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t need = gpd_tile_smem(2 * cfg->n_modes - 1, c->TZ, c->TR);
+        if (optin > 0 && need > (size_t)optin)
+            return bad(QPIC_EINVAL, "tile_z x tile_r too large for n_modes: the particle kernel needs " +
+                                        std::to_string(need) + " B of shared memory per block, the device has " +
+                                        std::to_string(optin) + " B (take a smaller tile)");
+    }
     FieldGeom &g = c->g;
     g.nz = cfg->nz; g.nr = cfg->nr; g.nm = cfg->n_modes; g.nparts = 2 * cfg->n_modes - 1;
     g.periodic = cfg->periodic_z ? 1 : 0;

@@ -23,6 +23,25 @@ size_t gpd_tile_words(int nparts, int tz, int tr)
     return (size_t)3 * nparts * (FW + 1) * (FR + 1);
 }
 
+// dynamic shared memory of one particle-kernel block for this mode count and
+// tile shape (the tile's staged fields, accumulators, queue and prefetch buffers)
+size_t gpd_tile_smem(int nparts, int tz, int tr)
+{
+    size_t out = 0;
+    auto pick = [&](auto np) {
+        tile_dispatch(tz, tr, [&](auto z, auto r) {
+            out = TileGeom<decltype(np)::value, decltype(z)::value, decltype(r)::value>::SMEM;
+        });
+    };
+    switch (nparts) {
+    case 1: pick(std::integral_constant<int, 1>()); break;
+    case 3: pick(std::integral_constant<int, 3>()); break;
+    case 5: pick(std::integral_constant<int, 5>()); break;
+    default: pick(std::integral_constant<int, 7>()); break;
+    }
+    return out;
+}
+
 __global__ void k_next_epoch(int *e) { *e += 1; }
 
 void launch_gpd(qpic_ctx *c)

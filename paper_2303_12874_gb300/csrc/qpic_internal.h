@@ -197,6 +197,7 @@ void launch_spectrum(qpic_ctx *c, const double *edges, int nb, double wscale,
 void launch_gpd(qpic_ctx *c);
 bool gpd_tile_supported(int tile_z, int tile_r);
 size_t gpd_tile_words(int nparts, int tile_z, int tile_r);   // accumulator words per tile
+size_t gpd_tile_smem(int nparts, int tile_z, int tile_r);    // shared memory of one particle-kernel block
 double launch_absmax(qpic_ctx *c, const double *w, long long n);  // max |w[i]| (device array; syncs)
 void launch_sort(qpic_ctx *c);
 int launch_load_plasma(qpic_ctx *c, long long first_logical_col, int ncols, bool append);

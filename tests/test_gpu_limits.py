@@ -40,3 +40,12 @@ def test_largest_grid_steps(nz, nr):
 def test_grid_at_the_limit_is_refused(nz, nr):
     with pytest.raises(q.QpicError, match="EINVAL"):
         q.Sim(nz, nr, 0.2, 0.5)
+
+
+@pytest.mark.parametrize("n_modes,tile", [(3, (32, 8)), (4, (32, 8)), (4, (16, 16))])
+def test_tile_too_large_for_the_modes_is_refused(n_modes, tile):
+    """the particle kernel's block (staged fields, accumulators) must fit the
+    device's shared memory: these mode counts and tiles would not"""
+    with pytest.raises(q.QpicError, match="EINVAL"):
+        q.Sim(64, 16, 0.2, 0.5, n_modes=n_modes, tile_z=tile[0], tile_r=tile[1])
+    q.Sim(64, 16, 0.2, 0.5, n_modes=n_modes, tile_z=8, tile_r=8, precision=q.QPIC_FP64)   # no tiles: fine
