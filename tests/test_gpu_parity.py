@@ -246,3 +246,16 @@ def test_set_field_takes_re_im_pairs():
     assert np.array_equal(got.real, re.astype(np.float32).astype(np.float64))
     with pytest.raises(ValueError):
         sim.set_field("B", "phi", 1, (re[:-1], im[:-1]))
+
+
+def test_box_shorter_than_two_staged_tiles():
+    """nz = 24 < 2 x (16 + 5): the staged tile would overlap its own wrap, so
+    every particle takes the global-memory path of the same kernel"""
+    nz, nr = 24, 19
+    sim, o = make_pair(nz, nr, DZ, DR, 0.13)
+    set_same_random_fields(sim, o, 21, amp=0.5)
+    load_same_particles(sim, o, _random_particles(6000, nz, nr, 22))
+    sim.step(1)
+    o.step(1)
+    for which in ("E", "B", "J"):
+        compare_fields(sim, o, which, TOL)
