@@ -1065,33 +1065,30 @@ __device__ __forceinline__ void jreduce_work(const JredArgs g, int t, int w)
     const int epoch = *g.d_epoch;
     const bool dirty = ld_maybe_cg<COH>(g.jdirty + t) == epoch;
     // candidate blocks: geometry first, per z neighbour and per r neighbour
-    // (3 + 3), then combined; their words are loaded together with the stamps
-    // that say whether they were written this step (no wait between)
-    long long zpart[3], rpart[3];
-    int ztile[3], ljb[3];
-    bool zok[3], rok[3];
+    // (3 + 3), then combined into bit masks (geo: the node lies in the
+    // candidate's staged block; ok: the block was written this step); the
+    // words are loaded together with the stamps (no wait between).  Offsets
+    // stay 32-bit inside a block; the block's base is formed per load.
+    int ztile[3], zli[3];
+    unsigned zok = 0u;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
         int kz = tzi + e - 1;
         kz = kz < 0 ? kz + a.ntz : (kz >= a.ntz ? kz - a.ntz : kz);
-        const int li = wrapn(i - (kz * TZ - H - 1), a.nzp);
+        zli[e] = wrapn(i - (kz * TZ - H - 1), a.nzp);
         ztile[e] = kz * a.ntr;
-        zpart[e] = (long long)ztile[e] * tile_words + li;
-        zok[e] = tiles_ok && li < JW;
-        const int kr = tri + e - 1;
-        ljb[e] = tr0 - (kr * TR - H - 1);
-        rpart[e] = (long long)kr * tile_words + (long long)(comp * NP) * (JR * JW);
-        rok[e] = kr >= 0 && kr < a.ntr;
+        if (tiles_ok && zli[e] < JW) zok |= 1u << e;
     }
-    long long kbase[9];
-    bool geo[9], ok[9];
+    unsigned geo = 0u, ok = 0u;
 #pragma unroll
     for (int d = 0; d < 9; d++) {
-        const int ez = d / 3, er = d % 3;
-        kbase[d] = zpart[ez] + rpart[er];
-        geo[d] = zok[ez] && rok[er];
-        ok[d] = geo[d] && ld_maybe_cg<COH>(tstamp + ztile[ez] + tri + er - 1) == epoch;
+        const int ez = d / 3, er = d % 3, kr = tri + er - 1;
+        if (((zok >> ez) & 1u) && kr >= 0 && kr < a.ntr) {
+            geo |= 1u << d;
+            if (ld_maybe_cg<COH>(tstamp + ztile[ez] + kr) == epoch) ok |= 1u << d;
+        }
     }
+    const int cbase = comp * NP * (JR * JW);
     int l = i - (int)a.zoff;
     l = l < 0 ? l + a.nzp : l;
     const bool gap = l >= a.nz;
@@ -1111,13 +1108,15 @@ __device__ __forceinline__ void jreduce_work(const JredArgs g, int t, int w)
         }
 #pragma unroll
         for (int d = 0; d < 9; d++) {
-            const int lj = ljb[d % 3] + r;
-            if (geo[d] && lj >= 0 && lj < JR) {
-                const unsigned long long *src = Jtile + kbase[d] + lj * JW;
+            const int ez = d / 3, er = d % 3;
+            const int lj = r + (1 - er) * TR + H + 1;          // row of the node in candidate d's block
+            if (((geo >> d) & 1u) && lj >= 0 && lj < JR) {
+                const unsigned long long *src = Jtile + (size_t)(ztile[ez] + tri + er - 1) * tile_words +
+                                                (cbase + lj * JW + zli[ez]);
                 unsigned long long w[NP];
 #pragma unroll
                 for (int p = 0; p < NP; p++) w[p] = ld_maybe_cg<COH>(src + p * (JR * JW));
-                if (ok[d]) {
+                if ((ok >> d) & 1u) {
 #pragma unroll
                     for (int p = 0; p < NP; p++) v[p] += (long long)w[p];
                 }
