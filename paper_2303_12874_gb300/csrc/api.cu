@@ -395,9 +395,11 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     if (!gpd_tile_supported(c->TZ, c->TR))
         return bad(QPIC_EINVAL, "tile_z x tile_r: one of 16x8, 32x8, 8x8, 16x16, 32x4");
     c->halo = 1;
+    if (cfg->sort_period < 0) return bad(QPIC_EINVAL, "sort_period: >= 1 (0: 2)");
     c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 2;
+    if (cfg->particles_per_thread < 0 || cfg->particles_per_thread > 8)
+        return bad(QPIC_EINVAL, "particles_per_thread: 1..8 (0: 8)");
     c->ppt = cfg->particles_per_thread > 0 ? cfg->particles_per_thread : 8;
-    if (c->ppt > 8) return bad(QPIC_EINVAL, "particles_per_thread: 1..8");
     if (cfg->absorb_cells < 0 || cfg->absorb_cells > cfg->nr || !(cfg->absorb_sigma >= 0.0) ||
         !std::isfinite(cfg->absorb_sigma))
         return bad(QPIC_EINVAL, "absorb_cells: 0..nr; absorb_sigma: finite, >= 0");
