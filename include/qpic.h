@@ -54,7 +54,8 @@ typedef enum {
     QPIC_ETIMEOUT = -6,    /* a bounded device-side wait gave up */
     QPIC_ENONFINITE = -7,  /* NaN/Inf found by the diagnostics */
     QPIC_ESTATE = -8,      /* call not valid in the current state */
-    QPIC_ECAPACITY = -9    /* particle buffer capacity exceeded */
+    QPIC_ECAPACITY = -9,   /* particle buffer capacity exceeded */
+    QPIC_ECHECK = -10      /* a kernel's invariant check failed (checked build, QPIC_CHECK, only) */
 } qpic_status;
 
 enum { QPIC_YEE = 0, QPIC_DUAL = 1 };

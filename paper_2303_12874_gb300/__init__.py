@@ -26,7 +26,7 @@ FIELD = {"E": 0, "B": 1, "Bbar": 2, "J": 3, "rho": 4}
 COMP = {"r": 0, "phi": 1, "z": 2}
 STAGE_FARADAY, STAGE_PARTICLES, STAGE_AMPERE, STAGE_WINDOW, STAGE_SORT = 1, 2, 4, 8, 16
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ECFL", -5: "EOVERFLOW",
-          -6: "ETIMEOUT", -7: "ENONFINITE", -8: "ESTATE", -9: "ECAPACITY"}
+          -6: "ETIMEOUT", -7: "ENONFINITE", -8: "ESTATE", -9: "ECAPACITY", -10: "ECHECK"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -52,16 +52,21 @@ class QpicError(RuntimeError):
     pass
 
 
+def _checked():
+    return os.environ.get("QPIC_CHECKED") == "1"
+
+
 def library_path():
-    return _build.LIB
+    return _build.LIB_CHECK if _checked() else _build.LIB
 
 
 def load(build_if_needed=True):
-    """Load libqpic.so (building it with nvcc first when stale)."""
+    """Load libqpic.so (building it with nvcc first when stale); with
+    QPIC_CHECKED=1 in the environment, the checked build (QPIC_CHECK)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_needed else _build.LIB
+    path = _build.build(check=_checked()) if build_if_needed else library_path()
     if not os.path.exists(path):
         raise QpicError("libqpic.so not found at %s (run __graft_entry__.build())" % path)
     L = ctypes.CDLL(path)
@@ -295,7 +300,10 @@ class _TorchAllocator:
         self.free_cb = FREE_FN(self._free)
 
     def _alloc(self, nbytes, user):
-        t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device="cuda:%d" % self.device)
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device="cuda:%d" % self.device)
+        except RuntimeError:
+            return 0                      # out of memory: the library reports QPIC_ENOMEM
         p = t.data_ptr()
         self.live[p] = t
         return p
@@ -332,7 +340,9 @@ class Sim:
             cfg.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
         self._alloc = None
         if torch_alloc:
-            self._alloc = _TorchAllocator()
+            # True: PyTorch's caching allocator; or an allocator object with
+            # alloc_cb / free_cb callbacks (as _TorchAllocator has)
+            self._alloc = torch_alloc if hasattr(torch_alloc, "alloc_cb") else _TorchAllocator()
             cfg.dev_alloc, cfg.dev_free = self._alloc.alloc_cb, self._alloc.free_cb
         self.cfg = cfg
         h = _P()

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qpic_internal.h"
 
 using namespace qpic;
@@ -184,10 +186,21 @@ void do_shift(qpic_ctx *c)
     }
 }
 
+// an NVTX range for the phases of a step (a no-op unless a profiler is attached)
+struct PhaseRange {
+    explicit PhaseRange(const char *name) { nvtxRangePushA(name); }
+    ~PhaseRange() { nvtxRangePop(); }
+};
+
 qpic_status run_one_step(qpic_ctx *c, int stages)
 {
-    if (stages & QPIC_STAGE_FARADAY) launch_faraday(c);
+    PhaseRange step_range("qpic step");
+    if (stages & QPIC_STAGE_FARADAY) {
+        PhaseRange r("faraday");
+        launch_faraday(c);
+    }
     if (stages & QPIC_STAGE_PARTICLES) {
+        PhaseRange r("gather push deposit");
         if (c->fp64) {
             fp64_push_deposit(c);
         } else {
@@ -197,6 +210,7 @@ qpic_status run_one_step(qpic_ctx *c, int stages)
         c->j_filtered = false;
     }
     if (stages & QPIC_STAGE_AMPERE) {
+        PhaseRange r("filter ampere");
         if (!c->taps.empty()) launch_jfilter(c);
         c->j_filtered = !c->taps.empty();
         launch_ampere(c);
@@ -205,6 +219,7 @@ qpic_status run_one_step(qpic_ctx *c, int stages)
                 (QPIC_STAGE_FARADAY | QPIC_STAGE_PARTICLES | QPIC_STAGE_AMPERE);
     if (full) c->nstep++;
     if ((stages & QPIC_STAGE_WINDOW) && c->cfg.moving_window) {
+        PhaseRange r("window");
         while (c->cfg.window_v * ((double)c->nstep * c->dt) >= (double)(c->shifts + 1) * c->dz)
             do_shift(c);
     }
@@ -212,7 +227,10 @@ qpic_status run_one_step(qpic_ctx *c, int stages)
     if (stages & QPIC_STAGE_SORT) {
         bool due = c->sort_period <= 1 || (c->nstep % c->sort_period) == 0 ||
                    c->n_tail > c->cap / 64;
-        if (due) launch_sort(c);
+        if (due) {
+            PhaseRange r("sort");
+            launch_sort(c);
+        }
     }
     return QPIC_OK;
 }
@@ -225,6 +243,7 @@ qpic_status check_device_error(qpic_ctx *c)
     if (ce != cudaSuccess) return fail(c, QPIC_ECUDA, std::string("step: ") + cudaGetErrorString(ce));
     if (e & 1) return fail(c, QPIC_EOVERFLOW, "fixed-point current accumulator overflow");
     if (e & 2) return fail(c, QPIC_ECAPACITY, "particle capacity exceeded during injection");
+    if (e & 8) return fail(c, QPIC_ECHECK, "a kernel invariant check failed (checked build)");
     return QPIC_OK;
 }
 

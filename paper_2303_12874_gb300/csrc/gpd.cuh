@@ -788,6 +788,7 @@ struct GpdArgs {
     const int32_t *offsets;
     const long long *dcount;
     PArgs a;
+    int *err;        // the run's error word (the checked build's invariant checks)
 };
 
 // One block of the particle kernel: tile bid (bid < ntiles) or a chunk of the
@@ -943,6 +944,12 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
                     const int niz = wrapn(iz + s.diz, a.nzp);
                     const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
                     const int ncell = dead ? -1 : make_cell(niz, jr + s.djr);
+                    // at most one cell per step (the stability limit), a cell inside the
+                    // grid, a slot inside the tile
+                    QPIC_DCHECK(fabsf(d.dzc) < 1.f && fabsf(d.drc) < 1.f && s.diz >= -1 && s.diz <= 1 &&
+                                    s.djr >= -1 && s.djr <= 1 && niz >= 0 && niz < a.nzp && jr + s.djr >= 0 &&
+                                    jr + s.djr < a.nr && qi >= 0 && qi < n && li + 1 < G::JW && lj + 1 < G::JR,
+                                g.err);
                     if (ncell != cell) cellp[qi] = ncell;   // most particles keep their cell
                     st_rec(recp + 2 * qi, make_float4(s.oz, s.orr, s.cph, s.sph),
                            make_float4(s.ux, s.uy, s.uz, s.w));
@@ -998,7 +1005,7 @@ static void gpd_launch2(qpic_ctx *c, const PArgs &a, int grid, int ntiles, int c
     const size_t sm = TileGeom<NP, TZ, TR>::SMEM;
     cudaFuncSetAttribute(k_gpd<NP, TZ, TR, FA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const GpdArgs g{c->p, c->E, c->Bb, c->Jacc, c->Jfa, c->Jtile, c->tstamp, c->jdirty, c->d_epoch,
-                    c->offsets, c->d_count, a};
+                    c->offsets, c->d_count, a, c->d_err};
     k_gpd<NP, TZ, TR, FA><<<grid, GPD_T, sm, c->stream>>>(g, ntiles, chunk);
 }
 
@@ -1111,6 +1118,8 @@ __device__ __forceinline__ void jreduce_work(const JredArgs g, int t, int w)
             const int ez = d / 3, er = d % 3;
             const int lj = r + (1 - er) * TR + H + 1;          // row of the node in candidate d's block
             if (((geo >> d) & 1u) && lj >= 0 && lj < JR) {
+                QPIC_DCHECK(cbase + lj * JW + zli[ez] + (NP - 1) * (JR * JW) < tile_words &&
+                                ztile[ez] + tri + er - 1 < a.ntz * a.ntr, err);
                 const unsigned long long *src = Jtile + (size_t)(ztile[ez] + tri + er - 1) * tile_words +
                                                 (cbase + lj * JW + zli[ez]);
                 unsigned long long w[NP];

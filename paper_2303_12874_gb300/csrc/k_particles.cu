@@ -78,7 +78,7 @@ void batch_fill_run(qpic_ctx *c, const Particles &p_cur, int *gdone, void *out)
     const PArgs a = pargs(c);
     BatchRun R;
     R.g = GpdArgs{p_cur, c->E, c->Bb, c->Jacc, c->Jfa, c->Jtile, c->tstamp, c->jdirty, c->d_epoch,
-                  c->offsets, c->d_count, a};
+                  c->offsets, c->d_count, a, c->d_err};
     const int JW = c->TZ + 2 * c->halo + 3;
     R.j = JredArgs{c->Jtile, c->tstamp, c->d_epoch, c->Jacc, c->jdirty, c->Jf, c->rowf, a,
                    (long long)gpd_tile_words(c->g.nparts, c->TZ, c->TR), 1.0f / c->qscale,
@@ -265,7 +265,7 @@ __global__ void k_scan_add(int32_t *out, const int32_t *bsum, long long n)
 }
 
 __global__ void k_scatter(Particles src, Particles dst, const long long *dcount, int32_t *counts,
-                          const int32_t *offsets, PArgs a)
+                          const int32_t *offsets, PArgs a, int *err)
 {
     const long long np = dcount[0];
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -295,6 +295,7 @@ __global__ void k_scatter(Particles src, Particles dst, const long long *dcount,
         const Chunk C = tile_chunk(ntile, u / a.chunk, a.chunk);
         const int w = u - C.q0, th = w / C.kc;
         const long long d = (long long)t0 + C.q0 + chunk_slot(C, th, w - th * C.kc);
+        QPIC_DCHECK(u >= 0 && u < ntile && d >= t0 && d < t1 && th <= C.nt, err);   // a slot of this tile
         dst.cell[d] = c;
         float4 ra, rb;
         ld_rec(src.rec + 2 * i, ra, rb);
@@ -333,7 +334,7 @@ void launch_sort(qpic_ctx *c)
     k_scan_local<<<nb, SCAN_B, 0, c->stream>>>(c->counts, c->offsets, c->scan_tmp, n + 1);
     k_scan_sums<<<1, SCAN_B, 0, c->stream>>>(c->scan_tmp, nb, c->scan_tmp + nb);
     k_scan_add<<<nb, SCAN_B, 0, c->stream>>>(c->offsets, c->scan_tmp, n + 1);
-    k_scatter<<<nblk, 256, 0, c->stream>>>(c->p, c->ps, dcount, c->counts, c->offsets, a);
+    k_scatter<<<nblk, 256, 0, c->stream>>>(c->p, c->ps, dcount, c->counts, c->offsets, a, c->d_err);
     k_set_counts<<<1, 1, 0, c->stream>>>(dcount, c->offsets + n);
     prof_end(c, KC_SORT, 6);
     Particles t = c->p; c->p = c->ps; c->ps = t;

@@ -253,6 +253,19 @@ void prof_end(qpic_ctx *c, int kclass, int nkernels = 1);
 }  // namespace qpic
 
 // return early from an entry point whose context belongs to another device
+// Device-side invariant checks of the checked build (QPIC_CHECK defined):
+// a violation sets bit 3 of the error word (reported as QPIC_ECHECK); no trap.
+#ifdef QPIC_CHECK
+#define QPIC_DCHECK(cond, errp)                                    \
+    do {                                                           \
+        if (!(cond)) atomicOr((errp), 8);                          \
+    } while (0)
+#else
+#define QPIC_DCHECK(cond, errp) \
+    do {                        \
+    } while (0)
+#endif
+
 #define QPIC_REQUIRE_DEVICE(c)                                                         \
     do {                                                                               \
         qpic_status _s = qpic::check_device(c);                                        \
