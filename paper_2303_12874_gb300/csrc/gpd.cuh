@@ -2,9 +2,10 @@
 // templates, instantiated per mode count and deposit variant in gpd_inst.cu.
 //
 // k_gpd: one CTA per particle tile (TZ x TR cells, particles sorted by tile).
-//   1. E^n and Bbar^n of the tile plus a halo are staged in shared memory
-//      (mode-parity images below the axis, even images beyond the wall, zeros
-//      in the gap of an open box), so the gather never branches on boundaries.
+//   1. E^n and Bbar^n of the tile plus a halo are staged in shared memory by
+//      asynchronous copies, all in flight at once (mode-parity images below the
+//      axis, even images beyond the wall, zeros in the gap of an open box), so
+//      the gather never branches on boundaries.
 //   2. per particle: bilinear gather of every mode at each component's own
 //      staggered point, modal sum F_0 + 2 Re(F_m e^{i m phi}) (Sec. III.B),
 //      rotation to x, y; relativistic Boris push with E^n and Bbar^n
@@ -696,6 +697,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// 4-byte copy that reads src_bytes (4 or 0) from global memory and zero-fills the rest
+__device__ __forceinline__ void cp_async4_zfill(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // one particle record (two float4 words, 32-byte aligned) in a single 256-bit access
 __device__ __forceinline__ void ld_rec(const float4 *p, float4 &a, float4 &b)
@@ -866,10 +874,15 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     // ---- stage E and Bbar of the tile and its halo; clear the accumulators
     const int col0 = tz0 - G::H - 1;
     const int row0 = tr0 - G::H - 1;
-    for (int k = tid; k < 2 * G::JPAD; k += blockDim.x) sJ64[k] = 0ull;    // int64 plane and both int32 planes
+    for (int k = tid; k < G::JPAD; k += blockDim.x)               // int64 plane and both int32 planes
+        reinterpret_cast<uint4 *>(sJ64)[k] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) *qcount = 0;
-    // one float4 word (up to 4 mode parts of one node) per thread and pass
-    // (compile-time trip count: the loop unrolls and its global loads overlap)
+    // one float4 word (up to 4 mode parts of one node) per thread and pass, each
+    // part copied asynchronously from its plane (zero-filled outside the grid),
+    // so that all the block's copies are in flight at once (compile-time trip
+    // count).  Half-r rows below the axis are copied from their mirror rows and
+    // take the mode parity's sign afterwards; rows beyond the wall are copied
+    // from their even image.
 #pragma unroll
     for (int it = 0; it < (G::FVEC + GPD_T - 1) / GPD_T; it++) {
         const int k = it * GPD_T + (int)threadIdx.x;
@@ -879,13 +892,41 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
         const int c = fc % 3, fb = fc / 3;
         int col = col0 + li;
         col = col < 0 ? col + a.nzp : (col >= a.nzp ? col - a.nzp : col);
-        float w4[4];
+        int j = row0 + lj;
+        const bool half = hr_of(fb, c);
+        if (half) {
+            if (j < 0) j = -1 - j;
+            if (j >= a.nr) j = 2 * a.nr - 1 - j;
+        }
+        const bool inside = j >= 0 && (half ? j < a.nr : j <= a.nr);
+        const float *F = (fb == 0 ? E : Bb) + (size_t)(c * a.nparts + 4 * v) * a.plane +
+                         (size_t)(inside ? j : 0) * a.nzp + col;
+        float *dst = reinterpret_cast<float *>(sf + k);
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            const int p = 4 * v + e;
-            w4[e] = p < NP ? gsample_at(E, Bb, a, fb, c, p, row0 + lj, col) : 0.f;
+            if (4 * v + e < NP) cp_async4_zfill(dst + e, F + (size_t)e * a.plane, inside ? 4 : 0);
+            else dst[e] = 0.f;
         }
-        sf[k] = make_float4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    cp_async_wait_all();
+    if (row0 < 0) {
+        // a tile on the axis: each thread signs its own words of the rows below it
+#pragma unroll
+        for (int it = 0; it < (G::FVEC + GPD_T - 1) / GPD_T; it++) {
+            const int k = it * GPD_T + (int)threadIdx.x;
+            if (k >= G::FVEC) break;
+            const int v = k % G::V, t1 = k / G::V;
+            const int t2 = t1 / G::FW, lj = t2 % G::FR, fc = t2 / G::FR;
+            const int c = fc % 3, fb = fc / 3;
+            if (row0 + lj >= 0 || !hr_of(fb, c)) continue;
+            const bool longitudinal = (fb == 1 && c == 2);
+            float *dst = reinterpret_cast<float *>(sf + k);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int p = 4 * v + e, m = (p + 1) >> 1;
+                if (p < NP && (((m & 1) != 0) != !longitudinal)) dst[e] = -dst[e];   // radial: (-1)^(m+1); z: (-1)^m
+            }
+        }
     }
     __syncthreads();
     const SmemAcc<NP, TZ, TR> sacc{sf, sJh, sJl, a.qscale};
