@@ -256,7 +256,7 @@ def batch_scan(q, torch, stream, nruns, steps, seed=5):
             sim.add_laser(2.0, 8.0, 15.0, 51.2, 51.2)
         tz, tr, sp, ppt, _ = autotune.tune(make, init, 512, 64, 2, int(np.prod(ppc_)), steps=8, warmup=4,
                                            sort_periods=(2, 4), batch_copies=4,
-                                           particles_per_thread=(4, 8))
+                                           particles_per_thread=(8, 16))
         tiles[ppc_] = (tz, tr, sp, ppt)
     sims, npart = [], []
     for k in range(nruns):

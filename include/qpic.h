@@ -90,7 +90,7 @@ typedef struct {
     int32_t sort_period;      /* steps between particle sorts (0: default 2; a particle moves
                                  < 1 cell per step, so 2 keeps every one inside its tile halo) */
     int32_t particles_per_thread; /* consecutive particles one thread of the particle kernel
-                                 takes in a chunk of 256 x this - 1 particles, 1..8 (0: 8).  A
+                                 takes in a chunk of 256 x this particles, 1..16 (0: 16).  A
                                  tile's particles are sorted by cell, so about ppc / this many
                                  threads share a cell (the "threads per cell" knob); smaller
                                  values mean more threads per cell and more chunk drains */

@@ -18,7 +18,7 @@ _lib = None
 
 # revision tag of the gather+push+deposit kernel; measured DRAM traffic stored
 # under profiles/ is only reported while it matches
-KERNEL_REV = "gpd-v17"
+KERNEL_REV = "gpd-v18"
 
 QPIC_YEE, QPIC_DUAL = 0, 1
 QPIC_FP64, QPIC_FP32_FIXED, QPIC_FP32_FATOMIC = 0, 1, 2
@@ -318,7 +318,7 @@ class Sim:
     def __init__(self, nz, nr, dz, dr, n_modes=2, dt=0.0, cfl_frac=0.9, solver="dual", n_coef=16,
                  fit_band=0.8, jz_filter=True, filter_tol=1e-16, periodic=True,
                  moving_window=False, window_v=1.0, tile_z=16, tile_r=8, sort_period=2,
-                 particles_per_thread=8, absorb_cells=0, absorb_sigma=0.0,
+                 particles_per_thread=16, absorb_cells=0, absorb_sigma=0.0,
                  track_work=False, seed=1, max_particles=0, stream=None, torch_alloc=False,
                  precision=QPIC_FP32_FIXED):
         self.L = load()

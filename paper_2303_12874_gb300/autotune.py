@@ -4,7 +4,7 @@ cell: the threads-per-cell knob).
 
 For a run configuration it times a few steps of every supported tile shape
 (16x8, 32x8, 8x8, 16x16, 32x4), sort period (1, 2 by default) and particles
-per thread (8 by default) on the GPU and keeps the fastest, caching the choice
+per thread (16 by default) on the GPU and keeps the fastest, caching the choice
 in a JSON file next to the built library keyed by (nz, nr, n_modes, particles
 per cell, periodic, the candidates, batch).
 Timing uses CUDA events; the state is the run's own plasma and laser.  With
@@ -20,7 +20,7 @@ from . import QpicError
 
 TILES = [(16, 8), (32, 8), (8, 8), (16, 16), (32, 4)]
 SORT_PERIODS = [1, 2]
-PARTICLES_PER_THREAD = [8]
+PARTICLES_PER_THREAD = [16]
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 
 

@@ -159,10 +159,10 @@ float *field_base(qpic_ctx *c, int which)
 void set_qscale(qpic_ctx *c, double qmax)
 {
     c->qref = qmax > 0 ? qmax : 1.0;
-    // per-particle contributions stay below 2 qref, i.e. 2^41 units: the exact
-    // FP32 hi 2^21 + lo split of the deposit handles them, and int64 keeps
-    // 2^21 contributions of the largest size per accumulator
-    c->qscale = (float)(1099511627776.0 / c->qref);        // 2^40 / qref
+    // per-particle contributions stay below 2 qref, i.e. 2^39 - 2^29 units: the
+    // particle kernel's 32-bit planes hold chunks of 4096 of them (FX_SCALE),
+    // and int64 keeps 2^24 contributions of the largest size per accumulator
+    c->qscale = (float)(FX_SCALE / c->qref);
 }
 
 void do_shift(qpic_ctx *c)
@@ -337,7 +337,7 @@ qpic_status qpic_default_config(qpic_config *cfg)
     cfg->tile_z = 16;
     cfg->tile_r = 8;
     cfg->sort_period = 2;
-    cfg->particles_per_thread = 8;
+    cfg->particles_per_thread = 16;
     cfg->absorb_cells = 0;
     cfg->absorb_sigma = 0.0;
     cfg->seed = 1;
@@ -416,9 +416,9 @@ qpic_status qpic_init(const qpic_config *cfg, qpic_ctx **out)
     c->halo = 1;
     if (cfg->sort_period < 0) return bad(QPIC_EINVAL, "sort_period: >= 1 (0: 2)");
     c->sort_period = cfg->sort_period > 0 ? cfg->sort_period : 2;
-    if (cfg->particles_per_thread < 0 || cfg->particles_per_thread > 8)
-        return bad(QPIC_EINVAL, "particles_per_thread: 1..8 (0: 8)");
-    c->ppt = cfg->particles_per_thread > 0 ? cfg->particles_per_thread : 8;
+    if (cfg->particles_per_thread < 0 || cfg->particles_per_thread > GPD_PPT_MAX)
+        return bad(QPIC_EINVAL, "particles_per_thread: 1..16 (0: 16)");
+    c->ppt = cfg->particles_per_thread > 0 ? cfg->particles_per_thread : 16;
     if (cfg->absorb_cells < 0 || cfg->absorb_cells > cfg->nr || !(cfg->absorb_sigma >= 0.0) ||
         !std::isfinite(cfg->absorb_sigma))
         return bad(QPIC_EINVAL, "absorb_cells: 0..nr; absorb_sigma: finite, >= 0");

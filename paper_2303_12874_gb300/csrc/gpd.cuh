@@ -13,11 +13,12 @@
 //      (r, cos phi, sin phi) written with cancellation-free differences;
 //      optional modal work (Eq. 16).
 //   3. charge-conserving deposit per mode into fixed-point shared
-//      accumulators: each int64 contribution v is added as two int32 parts,
-//      hi = round(v 2^-21) and lo = v - hi 2^21, to two int32 planes (32-bit
-//      shared atomics are several times faster than 64-bit ones); after every
-//      chunk of at most 2047 particles the planes are drained into an int64
-//      plane, so their sums never leave the int32 range.  The modal charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
+//      accumulators: each integer contribution v is added as two 32-bit parts,
+//      hi 2^20 + lo with 0 <= lo < 2^20, to two 32-bit planes (32-bit shared
+//      atomics are several times faster than 64-bit ones); after every chunk of
+//      at most 4096 particles the planes are drained into an int64 plane, so
+//      their sums never leave the 32-bit range (FX_SHIFT, FX_SCALE).  The modal
+//      charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
 //      splits into (S1 - S0)(e0 + e1)/2, carried by 2D Esirkepov r/z fluxes,
 //      and (S0 + S1)/2 (e1 - e0), carried by J_phi through (i m / r) J_phi.
 //      Each thread takes runs of consecutive particles of the tile (sorted by
@@ -25,7 +26,7 @@
 //      and added once per cell; moves across cells are queued and deposited
 //      once per tile.
 //   4. the tile's accumulators are stored to its own block of global memory
-//      as int64 (hi 2^21 + lo);
+//      as int64 (hi 2^20 + lo);
 //      k_jreduce sums the blocks that cover each node.  Integer addition makes
 //      the step independent of particle order (bit-reproducible).
 //   Particles beyond the staged halo (drift between sorts, or injected by the
@@ -55,7 +56,7 @@ struct PArgs {
     int TZ, TR, ntz, ntr, H, lTZ, lTR;
     float qscale;
     int track_work;
-    int chunk;       // particles per chunk of a tile: 256 x (particles per thread) - 1 (<= 2047)
+    int chunk;       // particles per chunk of a tile: 256 x (particles per thread) (<= 4096)
 };
 
 static PArgs pargs(const qpic_ctx *c)
@@ -71,7 +72,7 @@ static PArgs pargs(const qpic_ctx *c)
     a.lTZ = __builtin_ctz(c->TZ); a.lTR = __builtin_ctz(c->TR);
     a.qscale = c->qscale;
     a.track_work = c->cfg.track_work;
-    a.chunk = 256 * c->ppt - 1;
+    a.chunk = 256 * c->ppt;
     return a;
 }
 
@@ -123,15 +124,18 @@ __device__ __forceinline__ float gsample_at(const float *E, const float *Bb, con
 }
 
 // Fixed point of the current: a contribution x becomes v = round(x qscale)
-// with qscale = 2^40 / (largest particle charge), so |v| < 2^41 (the largest
-// factor of a charge in the deposit is 2).  v is split as hi 2^21 + lo with
-// |hi|, |lo| <= 2^20: two int32 sums hold 2^11 contributions of the largest
-// size without wrapping: a particle contributes at most once to a node, so
-// the planes are drained into int64 after every chunk of at most 2047
-// particles (GPD_C) and after the queued moves (at most QCAP).
-constexpr int FX_SHIFT = 21;
-constexpr float FX_DOWN = 4.76837158203125e-07f;  // 2^-21
-constexpr float FX_UP = 2097152.0f;               // 2^21
+// with qscale = FX_SCALE / (largest particle charge), so |v| < 2^39 - 2^29
+// (the largest factor of a charge in the deposit is 2).  v is rounded as
+// hi 2^20 + lo with |hi| <= 2^19 - 511 and |lo| <= 2^19; when the parts are
+// added to the shared planes, lo is carried into hi so that it lies in
+// [0, 2^20): the hi plane (signed) and the lo plane (unsigned) then hold the
+// sums of 4096 contributions of the largest size without wrapping.  A particle
+// contributes at most once to a node, so the planes are drained into int64
+// after every chunk of at most 4096 particles (GPD_C) and after the queued
+// moves (at most QCAP).
+constexpr float FX_DOWN = 1.0f / (float)(1 << FX_SHIFT);   // 2^-20
+constexpr float FX_UP = (float)(1 << FX_SHIFT);            // 2^20
+constexpr unsigned FX_LOMASK = (1u << FX_SHIFT) - 1u;
 
 // ------------------------------------------------------------ accessors
 // Staged tile of E and Bbar: per (field, component, row, column) node the NP
@@ -177,8 +181,10 @@ struct SmemAcc {
     __device__ __forceinline__ void jadd2(int c, int p, int lj, int li, int hi, int lo) const
     {
         const int k = ((c * NP + p) * G::JR + lj) * G::JW + li;
-        if (hi) atomicAdd(&sJh[k], (unsigned)hi);
-        if (lo) atomicAdd(&sJl[k], (unsigned)lo);
+        const int h = hi + (lo >> FX_SHIFT);              // lo < 0 borrows one from hi
+        const unsigned l = (unsigned)lo & FX_LOMASK;
+        if (h) atomicAdd(&sJh[k], (unsigned)h);
+        if (l) atomicAdd(&sJl[k], l);
     }
     __device__ __forceinline__ void put(int c, int p, int lj, int li, float x) const;
 };
@@ -222,18 +228,18 @@ struct FloatAcc {
 };
 
 
-// Exact round-to-nearest of a scaled contribution |v| < 2^42 into hi 2^21 + lo
+// Exact round-to-nearest of a scaled contribution |v| < 2^41 into hi 2^20 + lo
 // using only FP32 adds: t + 1.5*2^23 has unit spacing, so its bit pattern minus
 // that of 1.5*2^23 is round(t).  (A float->int64 conversion would run on the
 // FP64 pipe, which is narrow on this part.)
 __device__ __forceinline__ void fx_split(float v, int &hi, int &lo)
 {
     const float M = 12582912.0f;                       // 1.5 * 2^23
-    const float t = __fmul_rn(v, FX_DOWN);              // v 2^-18 (exact)
+    const float t = __fmul_rn(v, FX_DOWN);              // v 2^-20 (exact)
     const float tm = __fadd_rn(t, M);
     hi = __float_as_int(tm) - 0x4B400000;
     const float hf = __fsub_rn(tm, M);                  // round(t), exact
-    const float r = __fmaf_rn(-hf, FX_UP, v);           // v - hi 2^18, exact
+    const float r = __fmaf_rn(-hf, FX_UP, v);           // v - hi 2^20, exact
     lo = __float_as_int(__fadd_rn(r, M)) - 0x4B400000;
 }
 
@@ -553,7 +559,7 @@ __device__ __forceinline__ void deposit_general(const Acc &acc, const PArgs &a, 
 // of its tile (see chunk_slot), so successive moves mostly stay in one cell and
 // go to the same 8*NP accumulator words (J_z at 2 faces, J_r at 2 faces, J_phi
 // at 4 nodes, each per part).  Each contribution is rounded to the int64 fixed
-// point exactly as fx() does, kept as hi 2^21 + lo, and the two halves are
+// point exactly as fx() does, kept as hi 2^20 + lo, and the two halves are
 // summed in 32-bit registers; the biased bit patterns of the rounding sums
 // (1.5*2^23 + hi) are added directly and the bias is removed once per flush.
 // Integer sums make the result independent of particle order.  A flush adds
@@ -586,7 +592,7 @@ struct FastSum {
              : e == 3 ? p * PL + 1
                       : (NP + p) * PL + ((e - 4) & 1) + ((e - 4) >> 1) * G::JW;
     }
-    // two contributions t = value * qscale * 2^-21 (|t| < 2^21) at once, on the
+    // two contributions t = value * qscale * 2^-20 (|t| < 2^19) at once, on the
     // paired FP32 units: the same roundings as fx() for each lane
     __device__ __forceinline__ void put2(int i, float2 t)
     {
@@ -629,8 +635,9 @@ struct FastSum {
         }
         n += 1u;
     }
-    // the sums go to the hi and lo planes with 32-bit shared atomics (the
-    // planes hold the int32 sums exactly: see FX_SHIFT)
+    // the sums go to the hi and lo planes with 32-bit shared atomics, the lo
+    // sum L (|L| <= 16 2^19) carried into hi so that the lo plane receives
+    // L mod 2^20 (the planes hold their sums exactly: see FX_SCALE)
     __device__ __forceinline__ void flush(unsigned *sJh, unsigned *sJl)
     {
         if (n == 0u) return;
@@ -638,8 +645,9 @@ struct FastSum {
         const unsigned bias = 0x4B400000u * n;
 #pragma unroll
         for (int i = 0; i < NV; i++) {
-            atomicAdd(sJh + base + off(i), hs[i] - bias);
-            atomicAdd(sJl + base + off(i), ls[i] - bias);
+            const int L = (int)(ls[i] - bias);
+            atomicAdd(sJh + base + off(i), hs[i] - bias + (unsigned)(L >> FX_SHIFT));
+            atomicAdd(sJl + base + off(i), (unsigned)L & FX_LOMASK);
             hs[i] = 0u; ls[i] = 0u;
         }
         n = 0u;
@@ -648,15 +656,15 @@ struct FastSum {
 
 // ------------------------------------------------------------ the GPD kernel
 // Particle order inside a tile.  The n particles of a tile (sorted by cell) are
-// taken in chunks of at most C = 256 p - 1 particles, p the particles per
-// thread (1..8, so C <= GPD_C = 2047: the int32 accumulator planes are drained
-// into int64 after each chunk, FX_SHIFT).  In a chunk of rc particles every
+// taken in chunks of at most C = 256 p particles, p the particles per thread
+// (1..16, so C <= GPD_C = 4096: the 32-bit accumulator planes are drained into
+// int64 after each chunk, FX_SCALE).  In a chunk of rc particles every
 // thread takes kc = ceil(rc / GPD_T) <= p consecutive particles (nt = rc / kc
 // threads take kc, thread nt the rem = rc - nt kc left), so one thread's moves
 // mostly share a cell (FastSum) and about ppc / kc threads work on one cell.
 // Thread t's k-th particle of a chunk is q0 + t kc + k.
-constexpr int GPD_T = 256, GPD_C = 2047;
-static_assert(GPD_T == 256 && GPD_C == 8 * GPD_T - 1, "chunk sizes assume 256 threads");
+constexpr int GPD_T = 256, GPD_C = GPD_PPT_MAX * GPD_T;
+static_assert(GPD_T == 256 && GPD_C == 4096 && FX_SHIFT == 20, "chunk sizes assume 256 threads and the 2^20 split");
 
 struct Chunk { int q0, rc, kc, nt, rem; };
 
@@ -843,7 +851,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     const int zoff = (int)a.zoff;
     // ---- shared memory: accumulator planes, staged fields, crossing queue, particle buffers
     unsigned long long *sJ64 = sraw;                          // int64 sums of drained chunks
-    unsigned *sJh = reinterpret_cast<unsigned *>(sraw + G::JPAD);   // int32 hi, lo planes of the chunk
+    unsigned *sJh = reinterpret_cast<unsigned *>(sraw + G::JPAD);   // 32-bit hi, lo planes of the chunk
     unsigned *sJl = sJh + G::JPAD;
     float4 *sf = reinterpret_cast<float4 *>(sJh + 2 * G::JPAD);
     float *queue = reinterpret_cast<float *>(sf + G::FVEC);
@@ -874,7 +882,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     // ---- stage E and Bbar of the tile and its halo; clear the accumulators
     const int col0 = tz0 - G::H - 1;
     const int row0 = tr0 - G::H - 1;
-    for (int k = tid; k < G::JPAD; k += blockDim.x)               // int64 plane and both int32 planes
+    for (int k = tid; k < G::JPAD; k += blockDim.x)               // int64 plane and both 32-bit planes
         reinterpret_cast<uint4 *>(sJ64)[k] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) *qcount = 0;
     // one float4 word (up to 4 mode parts of one node) per thread and pass, each
@@ -930,7 +938,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     }
     __syncthreads();
     const SmemAcc<NP, TZ, TR> sacc{sf, sJh, sJl, a.qscale};
-    const float q20 = a.qscale * FX_DOWN;                         // qscale 2^-21
+    const float q20 = a.qscale * FX_DOWN;                         // qscale 2^-20
     FastSum<NP, TZ, TR> fs;
     fs.clear();
     for (int ch = 0; ch < nch; ch++) {
@@ -1002,11 +1010,11 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
         if constexpr (!FA) {
             fs.flush(sJh, sJl);
             fs.key = -1;
-            // drain the chunk's int32 planes into the int64 plane (each thread its
+            // drain the chunk's 32-bit planes into the int64 plane (each thread its
             // own words: no atomics), so the next chunk starts from zero
             __syncthreads();
             for (int w = tid; w < G::JWORDS; w += blockDim.x) {
-                sJ64[w] += (unsigned long long)(((long long)(int)sJh[w] << FX_SHIFT) + (long long)(int)sJl[w]);
+                sJ64[w] += (unsigned long long)(((long long)(int)sJh[w] << FX_SHIFT) + (long long)sJl[w]);
                 sJh[w] = 0u;
                 sJl[w] = 0u;
             }
@@ -1029,7 +1037,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     // kernel sums the tiles that cover each node
     unsigned long long *dst = g.Jtile + (size_t)bid * G::JWORDS;
     for (int k = tid; k < G::JWORDS; k += blockDim.x)
-        dst[k] = sJ64[k] + (unsigned long long)(((long long)(int)sJh[k] << FX_SHIFT) + (long long)(int)sJl[k]);
+        dst[k] = sJ64[k] + (unsigned long long)(((long long)(int)sJh[k] << FX_SHIFT) + (long long)sJl[k]);
     if (tid == 0) g.tstamp[bid] = *g.d_epoch;
 }
 

@@ -29,6 +29,19 @@ constexpr int MAX_L = 64;      // max coefficients per z-operator
 constexpr int MAX_TAPS = 512;  // max J_z filter half-length
 constexpr int MAX_MODES = 4;
 
+// Fixed point of the current (FP32 path).  A deposit contribution X (at most
+// 2 qref in magnitude, qref the largest particle charge) becomes the integer
+// v = round(X qscale), qscale = FX_SCALE / qref, so |v| < 2^39 - 2^29.  Inside
+// the particle kernel v is carried as hi 2^FX_SHIFT + lo in two 32-bit shared
+// planes (hi signed, |hi| <= 2^19 - 511 per contribution; lo made non-negative,
+// below 2^FX_SHIFT, by a carry into hi when it is added), so a chunk of up to
+// GPD_PPT_MAX x 256 = 4096 particles, each adding at most once to a node, keeps
+// both planes inside 32 bits.  The resolution, 2^-38 qref, is far below the
+// FP32 rounding of the contributions themselves.
+constexpr int FX_SHIFT = 20;
+constexpr double FX_SCALE = 274877906944.0 * (1023.0 / 1024.0);   // 2^38 (1 - 2^-10)
+constexpr int GPD_PPT_MAX = 16;
+
 struct FieldGeom {
     int nz, nr, nzp, gap, nparts, nm;
     long long zoff;            // physical column of logical 0 (mod nzp)
@@ -128,7 +141,7 @@ struct qpic_ctx {
     qpic::Particles64 p64, ps64;  // plain FP64 path: live buffers and compaction target
     int32_t *scan_flag = nullptr, *scan_pos = nullptr, *scan_tmp64 = nullptr;
     double qref = 0.0;            // max |charge| of a particle
-    float qscale = 0.f;           // fixed-point scale 2^40 / qref
+    float qscale = 0.f;           // fixed-point scale FX_SCALE / qref
 
     // plasma (for the moving-window injection)
     bool have_plasma = false;
@@ -137,7 +150,7 @@ struct qpic_ctx {
 
     // tiles and sort
     int TZ = 16, TR = 8, ntz = 0, ntr = 0, halo = 1;
-    int ppt = 8;                 // consecutive particles per thread in the particle kernel
+    int ppt = 16;                // consecutive particles per thread in the particle kernel
     int nabs = 0;                // absorbing radial layer: cells next to the wall (0: none)
     double sigabs = 0;           // its peak conductivity
     float *lossf = nullptr;      // lossy update factors per row (4 (nr + 1)), FP32 and FP64

@@ -16,7 +16,7 @@ COMPS = ("r", "phi", "z")
 
 def make_pair(nz, nr, dz, dr, dt, n_modes=2, solver="dual", periodic=True, jz_filter=True,
               track_work=False, tile=(16, 8), sort_period=2, moving_window=False,
-              precision=q.QPIC_FP32_FIXED, particles_per_thread=8, absorb_cells=0, absorb_sigma=0.0):
+              precision=q.QPIC_FP32_FIXED, particles_per_thread=16, absorb_cells=0, absorb_sigma=0.0):
     sim = q.Sim(nz, nr, dz, dr, n_modes=n_modes, dt=dt, solver=solver, periodic=periodic,
                 jz_filter=jz_filter, track_work=track_work, tile_z=tile[0], tile_r=tile[1],
                 sort_period=sort_period, moving_window=moving_window, precision=precision,

@@ -35,15 +35,15 @@ def test_loads_beyond_capacity_are_refused():
 
 
 def test_fixed_point_overflow_is_reported():
-    # charge units at scale 2^40 / (largest charge): each particle adds
-    # 2^40 x 0.4 (cells moved) x 0.5 (r weight) to each of its two J_z nodes
-    n = 28 * 2 ** 20
+    # charge units at scale 2^38 (1 - 2^-10) / (largest charge): each particle
+    # adds that scale x 0.6 (cells moved) x 1 (r weight) to one J_z node
+    n = 36 * 2 ** 20
     nz, nr, dz, dr, dt = 32, 8, 0.2, 0.5, 0.13
-    assert 1.2 * 2 ** 62 < n * 0.2 * 2 ** 40 < 1.5 * 2 ** 62
+    assert 1.2 * 2 ** 62 < n * 0.6 * 2 ** 38 * (1023 / 1024) < 1.5 * 2 ** 62
     rng = np.random.default_rng(7)
     z = (10 + 0.1 + 0.2 * rng.random(n)) * dz          # cell 10, offsets 0.1-0.3
-    r = np.full(n, 3.5 * dr)                            # mid-cell in r: weights 1/2, 1/2
-    vz = 0.4 * dz / dt                                  # 0.4 cell per step
+    r = np.full(n, 3.0 * dr)                            # on the node row: r weights 1, 0
+    vz = 0.6 * dz / dt                                  # 0.6 cell per step
     uz = np.full(n, vz / np.sqrt(1.0 - vz * vz))
     zeros = np.zeros(n)
     sim = q.Sim(nz, nr, dz, dr, dt=dt, max_particles=n)

@@ -51,7 +51,7 @@ def test_tile_too_large_for_the_modes_is_refused(n_modes, tile):
     q.Sim(64, 16, 0.2, 0.5, n_modes=n_modes, tile_z=8, tile_r=8, precision=q.QPIC_FP64)   # no tiles: fine
 
 
-@pytest.mark.parametrize("kw", [dict(particles_per_thread=9), dict(particles_per_thread=-1),
+@pytest.mark.parametrize("kw", [dict(particles_per_thread=17), dict(particles_per_thread=-1),
                                 dict(tile_z=16, tile_r=4), dict(tile_z=7), dict(sort_period=-3)])
 def test_invalid_particle_settings_are_refused(kw):
     with pytest.raises(q.QpicError, match="EINVAL"):

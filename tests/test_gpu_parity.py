@@ -120,12 +120,14 @@ def o_cB(o):
 
 
 @pytest.mark.parametrize("solver,sort_period,ppt", [("dual", 2, 8), ("yee", 2, 8), ("dual", 1, 8),
-                                                    ("dual", 3, 8), ("dual", 2, 1), ("dual", 2, 3)])
+                                                    ("dual", 3, 8), ("dual", 2, 1), ("dual", 2, 3),
+                                                    ("dual", 2, 16)])
 def test_full_step_config1(solver, sort_period, ppt):
     """sort_period 3 leaves particles up to 2 cells outside their tile: those
     take the global-memory path of the same kernel.  ppt: particles per thread
-    (1: chunks of 255 particles, so a 16 x 8 tile of this plasma (1024
-    particles) is deposited in several chunks with a drain between them)"""
+    (1: chunks of 256 particles, so a 16 x 8 tile of this plasma (1024
+    particles) is deposited in several chunks with a drain between them;
+    16: chunks of 4096, the largest the 32-bit planes allow)"""
     w = synth.workload("cfg1_small")
     nz, nr = w["nz"], w["nr"]
     from oracle import coeffs as C
@@ -146,10 +148,10 @@ def test_full_step_config1(solver, sort_period, ppt):
 
 def test_particles_per_thread_leaves_results_unchanged():
     """the particles each thread takes in a row only regroup the exact
-    integer sums of the deposit: fields bit-identical for 1, 3 and 8"""
+    integer sums of the deposit: fields bit-identical for 1, 3, 8 and 16"""
     w = synth.workload("cfg1_small")
     out = []
-    for ppt in (1, 3, 8):
+    for ppt in (1, 3, 8, 16):
         sim, _o = make_pair(w["nz"], w["nr"], w["dz"], w["dr"], 0.13, particles_per_thread=ppt)
         _config1_state(sim, _o)
         sim.step(5)
