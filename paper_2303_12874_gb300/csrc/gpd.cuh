@@ -16,8 +16,8 @@
 //      accumulators: each integer contribution v is added as two 32-bit parts,
 //      hi 2^20 + lo with 0 <= lo < 2^20, to two 32-bit planes (32-bit shared
 //      atomics are several times faster than 64-bit ones); after every chunk of
-//      at most 4096 particles the planes are drained into an int64 plane, so
-//      their sums never leave the 32-bit range (FX_SHIFT, FX_SCALE).  The modal
+//      at most 4096 particles but the last the planes are drained into an int64
+//      plane, so their sums never leave the 32-bit range (FX_SHIFT, FX_SCALE).  The modal
 //      charge change Q (S1 e1 - S0 e0), e = e^{-i m phi},
 //      splits into (S1 - S0)(e0 + e1)/2, carried by 2D Esirkepov r/z fluxes,
 //      and (S0 + S1)/2 (e1 - e0), carried by J_phi through (i m / r) J_phi.
@@ -131,8 +131,8 @@ __device__ __forceinline__ float gsample_at(const float *E, const float *Bb, con
 // [0, 2^20): the hi plane (signed) and the lo plane (unsigned) then hold the
 // sums of 4096 contributions of the largest size without wrapping.  A particle
 // contributes at most once to a node, so the planes are drained into int64
-// after every chunk of at most 4096 particles (GPD_C) and after the queued
-// moves (at most QCAP).
+// after every chunk of at most 4096 particles (GPD_C) but the last; the queued
+// moves go to the int64 plane directly.
 constexpr float FX_DOWN = 1.0f / (float)(1 << FX_SHIFT);   // 2^-20
 constexpr float FX_UP = (float)(1 << FX_SHIFT);            // 2^20
 constexpr unsigned FX_LOMASK = (1u << FX_SHIFT) - 1u;
@@ -263,6 +263,20 @@ __device__ __forceinline__ void GlobAcc<NP>::put(int c, int p, int j, int i, flo
 {
     jadd(c, p, j, i, fx(x, a.qscale));
 }
+
+// The tile's int64 shared plane, for the queued cell-crossing moves deposited
+// after the last chunk (64-bit shared atomics: at most QCAP moves per tile)
+template <int NP, int TZ, int TR>
+struct SmemAcc64 {
+    using G = TileGeom<NP, TZ, TR>;
+    unsigned long long *sJ64;    // [3][NP][JR][JW]
+    float qs;
+    __device__ __forceinline__ void put(int c, int p, int lj, int li, float x) const
+    {
+        const long long v = fx(x, qs);
+        if (v) atomicAdd(&sJ64[((c * NP + p) * G::JR + lj) * G::JW + li], (unsigned long long)v);
+    }
+};
 
 __device__ __forceinline__ int wrapn(int i, int n)      // for i in [-n, 2n)
 {
@@ -1010,6 +1024,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
         if constexpr (!FA) {
             fs.flush(sJh, sJl);
             fs.key = -1;
+            if (ch + 1 == nch) break;                              // the last chunk stays in its planes
             // drain the chunk's 32-bit planes into the int64 plane (each thread its
             // own words: no atomics), so the next chunk starts from zero
             __syncthreads();
@@ -1022,17 +1037,19 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
         }
     }
     if constexpr (FA) return;
-    // the queued cell-crossing moves, spread over all threads
+    // the queued cell-crossing moves, spread over all threads, into the int64
+    // plane (the last chunk's sums stay in the 32-bit planes)
     __syncthreads();
     const int nq = imin(*qcount, G::QCAP);
+    const SmemAcc64<NP, TZ, TR> sacc64{sJ64, a.qscale};
     for (int qq = tid; qq < nq; qq += blockDim.x) {
         int qi, qj;
         DepIn<NM> dq;
         queue_get<NM>(queue + G::QW * qq, qi, qj, dq);
-        deposit_general<NP>(sacc, a, qi, qj, dq);
+        deposit_general<NP>(sacc64, a, qi, qj, dq);
     }
     __syncthreads();
-    // the tile's accumulators (the int64 plane plus the queued moves' int32
+    // the tile's accumulators (the int64 plane plus the last chunk's 32-bit
     // parts) go to its own scratch block with plain stores; the reduction
     // kernel sums the tiles that cover each node
     unsigned long long *dst = g.Jtile + (size_t)bid * G::JWORDS;
