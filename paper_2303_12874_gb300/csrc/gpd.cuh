@@ -952,6 +952,10 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     }
     __syncthreads();
     const SmemAcc<NP, TZ, TR> sacc{sf, sJh, sJl, a.qscale};
+    // can a particle of this tile be, or move, behind the moving window?  The
+    // tile's staged columns are logical L0 ... L0 + FW - 1 (mod nzp); they avoid
+    // the gap [nz, nzp) when L0 + FW - 1 < nz
+    const bool near_gap = !a.periodic && pwrap(col0 - zoff, a.nzp) + G::FW - 1 >= a.nz;
     const float q20 = a.qscale * FX_DOWN;                         // qscale 2^-20
     FastSum<NP, TZ, TR> fs;
     fs.clear();
@@ -962,23 +966,23 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
             prefetch(0, cnt > 0 ? C.q0 + chunk_slot(C, tid, 0) : -1);
         }
         int buf = 0;
+        int qi = C.q0 + chunk_slot(C, tid, 0);                     // slot of this thread's k-th particle
         for (int k = 0; k < C.kc; k++) {                           // block-uniform trip count
-            prefetch(buf ^ 1, k + 1 < cnt ? C.q0 + chunk_slot(C, tid, k + 1) : -1);
+            const int qn = qi + C.nt + (k < C.rem ? 1 : 0);         // chunk_slot(C, tid, k + 1)
+            prefetch(buf ^ 1, k + 1 < cnt ? qn : -1);
             cp_async_wait_prev();                                  // this particle's words have landed
             if (k < cnt) {
-                const int qi = C.q0 + chunk_slot(C, tid, k);
                 const float *pb = pbuf + buf * G::PB;
                 const float4 *pr = reinterpret_cast<const float4 *>(pb + GPD_T);
                 const int cell = __float_as_int(pb[tid]);
                 const int iz = cell_iz(cell), jr = cell_jr(cell);
                 bool act = cell >= 0;
-                if (act && !a.periodic && wrapn(iz - zoff, a.nzp) >= a.nz) {
-                    cellp[qi] = -1;                    // behind the moving window
-                    act = false;
-                }
                 const int li = wrapn(iz - col0, a.nzp), lj = jr - row0;
                 if (act && !(li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2)) {
                     gpd_global_one<NP, FA>(P, begin + qi, cell, a, gacc, facc);   // drifted beyond the halo
+                    act = false;
+                } else if (act && near_gap && wrapn(iz - zoff, a.nzp) >= a.nz) {
+                    cellp[qi] = -1;                    // behind the moving window
                     act = false;
                 }
                 if (act) {
@@ -1005,7 +1009,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
                         else deposit_general<NP>(sacc, a, li, lj, d);
                     }
                     const int niz = wrapn(iz + s.diz, a.nzp);
-                    const bool dead = !a.periodic && wrapn(niz - zoff, a.nzp) >= a.nz;
+                    const bool dead = near_gap && wrapn(niz - zoff, a.nzp) >= a.nz;
                     const int ncell = dead ? -1 : make_cell(niz, jr + s.djr);
                     // at most one cell per step (the stability limit), a cell inside the
                     // grid, a slot inside the tile
@@ -1020,6 +1024,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
                 }
             }
             buf ^= 1;
+            qi = qn;
         }
         if constexpr (!FA) {
             fs.flush(sJh, sJl);
