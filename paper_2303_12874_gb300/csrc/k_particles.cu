@@ -3,6 +3,7 @@
 //
 // k_count / scan / k_scatter: counting sort of live particles by a tile-major
 // cell key; dead particles are dropped.
+#include <limits.h>
 #include <string.h>
 
 #include "gpd.cuh"
@@ -161,32 +162,64 @@ __device__ __forceinline__ int sort_key(int cell, const PArgs &a)
     return ((((tzi * a.ntr + tri) << a.lTR) + (jr & (a.TR - 1))) << a.lTZ) + (iz & (a.TZ - 1));
 }
 
-// histogram of live particles per key; lanes of a warp that share a key (the
-// buffer is nearly sorted) add their count with one atomic
-__global__ void k_count(const int32_t *__restrict__ cell, const long long *dcount, int32_t *counts,
-                        PArgs a)
+// histogram of live particles per key.  Each block takes ranges of
+// KCOUNT_R consecutive particles.  The buffer is sorted by key since the last
+// sort (up to the drift of a few steps and the particles appended since), so
+// the keys of a range mostly lie in a window of 4 tiles from the tile of its
+// smallest key among its first 256 particles: those are counted in a shared
+// histogram, added to the global counts once per range.  Keys outside the
+// window are added directly, lanes of a warp that share a key with one atomic.
+constexpr int KCOUNT_R = 4096, KCOUNT_W = 1024;   // particles per range; window keys (4 tiles of <= 256 cells)
+__global__ void __launch_bounds__(256) k_count(const int32_t *__restrict__ cell, const long long *dcount,
+                                               int32_t *counts, PArgs a)
 {
+    __shared__ int hist[KCOUNT_W];
+    __shared__ int s_kmin;
     const long long np = dcount[0];
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const unsigned lane = threadIdx.x & 31;
-    // four warp-wide passes per iteration, their loads issued first
-    for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < np; i0 += 4 * stride) {
-        int cu[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const long long i = i0 + u * stride + threadIdx.x;
-            cu[u] = i < np ? cell[i] : -1;
+    const int tid = threadIdx.x;
+    const unsigned lane = tid & 31;
+    const int tt = a.TZ * a.TR, W = 4 * tt;
+    for (long long r0 = (long long)blockIdx.x * KCOUNT_R; r0 < np; r0 += (long long)gridDim.x * KCOUNT_R) {
+        const long long r1 = min(r0 + KCOUNT_R, np);
+        if (tid == 0) s_kmin = INT_MAX;
+        for (int w = tid; w < W; w += blockDim.x) hist[w] = 0;
+        __syncthreads();
+        {
+            const long long i = r0 + tid;
+            const int c = i < r1 ? cell[i] : -1;
+            if (c >= 0) atomicMin(&s_kmin, sort_key(c, a));
         }
+        __syncthreads();
+        const int kmin = s_kmin;
+        const int kb = kmin == INT_MAX ? 0 : kmin - kmin % tt;      // window [kb, kb + W)
+        const int wn = kmin == INT_MAX ? 0 : W;
+        for (long long i0 = r0; i0 < r1; i0 += 4 * (long long)blockDim.x) {
+            int cu[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int c = cu[u];
-            const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
-            if (c >= 0) {
-                const int k = sort_key(c, a);
-                const unsigned grp = __match_any_sync(act, k);
-                if (lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&counts[k], __popc(grp));
+            for (int u = 0; u < 4; u++) {                          // the loads first
+                const long long i = i0 + u * (long long)blockDim.x + tid;
+                cu[u] = i < r1 ? cell[i] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int c = cu[u];
+                const int k = c >= 0 ? sort_key(c, a) : 0;
+                const bool inw = c >= 0 && k >= kb && k - kb < wn;
+                if (inw) atomicAdd(&hist[k - kb], 1);
+                const bool out = c >= 0 && !inw;
+                const unsigned m = __ballot_sync(0xffffffffu, out);
+                if (out) {
+                    const unsigned grp = __match_any_sync(m, k);
+                    if (lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&counts[k], __popc(grp));
+                }
             }
         }
+        __syncthreads();
+        for (int w = tid; w < wn; w += blockDim.x) {
+            const int h = hist[w];
+            if (h) atomicAdd(&counts[kb + w], h);
+        }
+        __syncthreads();                                           // hist and s_kmin are reused
     }
 }
 
