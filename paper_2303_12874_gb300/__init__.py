@@ -18,7 +18,7 @@ _lib = None
 
 # revision tag of the gather+push+deposit kernel; measured DRAM traffic stored
 # under profiles/ is only reported while it matches
-KERNEL_REV = "gpd-v20"
+KERNEL_REV = "gpd-v21"
 
 QPIC_YEE, QPIC_DUAL = 0, 1
 QPIC_FP64, QPIC_FP32_FIXED, QPIC_FP32_FATOMIC = 0, 1, 2

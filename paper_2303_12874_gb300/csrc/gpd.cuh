@@ -956,6 +956,9 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
     // tile's staged columns are logical L0 ... L0 + FW - 1 (mod nzp); they avoid
     // the gap [nz, nzp) when L0 + FW - 1 < nz
     const bool near_gap = !a.periodic && pwrap(col0 - zoff, a.nzp) + G::FW - 1 >= a.nz;
+    // the tile's staged columns do not cross the end of the circular z buffer:
+    // column offsets need no wrap
+    const bool flat = col0 >= 0 && col0 + G::FW <= a.nzp;
     const float q20 = a.qscale * FX_DOWN;                         // qscale 2^-20
     FastSum<NP, TZ, TR> fs;
     fs.clear();
@@ -977,7 +980,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
                 const int cell = __float_as_int(pb[tid]);
                 const int iz = cell_iz(cell), jr = cell_jr(cell);
                 bool act = cell >= 0;
-                const int li = wrapn(iz - col0, a.nzp), lj = jr - row0;
+                const int li = flat ? iz - col0 : wrapn(iz - col0, a.nzp), lj = jr - row0;
                 if (act && !(li >= 1 && li <= G::FW - 2 && lj >= 1 && lj <= G::FR - 2)) {
                     gpd_global_one<NP, FA>(P, begin + qi, cell, a, gacc, facc);   // drifted beyond the halo
                     act = false;
@@ -1008,7 +1011,7 @@ __device__ __forceinline__ void gpd_block(const GpdArgs g, int bid, int ntiles, 
                         if (slot < G::QCAP) queue_put<NM>(queue + G::QW * slot, li, lj, d);
                         else deposit_general<NP>(sacc, a, li, lj, d);
                     }
-                    const int niz = wrapn(iz + s.diz, a.nzp);
+                    const int niz = flat ? iz + s.diz : wrapn(iz + s.diz, a.nzp);
                     const bool dead = near_gap && wrapn(niz - zoff, a.nzp) >= a.nz;
                     const int ncell = dead ? -1 : make_cell(niz, jr + s.djr);
                     // at most one cell per step (the stability limit), a cell inside the
