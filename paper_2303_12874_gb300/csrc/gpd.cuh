@@ -149,13 +149,13 @@ struct TileGeom {
     static constexpr int JW = FW + 1, JR = FR + 1;                   // accumulators
     static constexpr int V = (NP + 3) / 4;
     static constexpr int JWORDS = 3 * NP * JW * JR;                   // accumulated values (int64 each)
-    static constexpr int JPAD = (JWORDS + 3) & ~3;                    // per int32 plane; keeps the float4 tile 16-B aligned
+    static constexpr int JPAD = (JWORDS + 3) & ~3;                    // per 32-bit plane; keeps the float4 tile 16-B aligned
     static constexpr int FVEC = 2 * 3 * FR * FW * V;                  // float4 words
     static constexpr int NM = (NP + 1) / 2;
     static constexpr int QW = 8 + 4 * (NM - 1);                       // words per queued move
     static constexpr int QCAP = 256;                                  // queued cell-crossing moves
     static constexpr int PB = 9 * 256;      // prefetched words per buffer: 256 cells, 2 x 256 float4
-    static constexpr size_t SMEM = (size_t)JPAD * 8 /* hi, lo int32 planes */ + (size_t)JPAD * 8 /* int64 plane */ +
+    static constexpr size_t SMEM = (size_t)JPAD * 8 /* hi, lo 32-bit planes */ + (size_t)JPAD * 8 /* int64 plane */ +
                                    (size_t)FVEC * 16 + (size_t)QCAP * QW * 4 + (size_t)2 * PB * 4 + 16;
     static_assert((JPAD * 8) % 16 == 0, "float4 tile alignment");
 };

@@ -41,6 +41,13 @@ constexpr int MAX_MODES = 4;
 constexpr int FX_SHIFT = 20;
 constexpr double FX_SCALE = 274877906944.0 * (1023.0 / 1024.0);   // 2^38 (1 - 2^-10)
 constexpr int GPD_PPT_MAX = 16;
+// the bounds above: a contribution of 2 qref (times 1 + 2^-20 for its FP32
+// rounding) gives a high part of at most 2^19 - 511; with the carry of the
+// low part (at most 1 per contribution) a chunk's hi sums stay below 2^31, and
+// its non-negative lo sums (each below 2^FX_SHIFT) below 2^32
+constexpr double FX_HI_MAX = 2.0 * FX_SCALE * (1.0 + 1.0 / 1048576.0) / (double)(1 << FX_SHIFT) + 0.5;
+static_assert((double)(GPD_PPT_MAX * 256) * (FX_HI_MAX + 1.0) < 2147483648.0, "hi plane of a chunk");
+static_assert((double)(GPD_PPT_MAX * 256) * (double)((1 << FX_SHIFT) - 1) < 4294967296.0, "lo plane of a chunk");
 
 struct FieldGeom {
     int nz, nr, nzp, gap, nparts, nm;
