@@ -77,7 +77,8 @@ typedef struct {
     int32_t n_coef;        /* L coefficients per z-operator for QPIC_DUAL (Appendix A: 16) */
     double fit_band;       /* fit range k dz in (0, fit_band*pi] (a reading; default 0.8) */
     int32_t precision;     /* QPIC_FP32_FIXED (default): FP32 push and solve, int64 fixed-point
-                              current sums (bit-reproducible);
+                              current sums (bit-reproducible; each contribution rounded to
+                              units of the largest particle charge / (2^38 (1 - 2^-10)));
                               QPIC_FP32_FATOMIC: the same with the current summed by FP32
                               float atomics in global memory (order-dependent rounding);
                               QPIC_FP64: plain FP64 path, one thread per particle */
